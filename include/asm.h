@@ -1,0 +1,181 @@
+/*
+ * asm.h -- C ABI of the GB300 (sm_103a) two-level additive Schwarz library.
+ *
+ * The library implements the fully algebraic two-level additive Schwarz
+ * preconditioner of Al Daas, Jolivet, Nataf and Tournier ("A robust
+ * two-level Schwarz preconditioner for sparse matrices"):
+ *
+ *   M^{-1} = sum_{i=1}^N R_i^T A_ii^{-1} R_i  +  Z E^{-1} Z^T,   E = Z^T A Z,
+ *
+ * (Remark in Section 4.3 with the coarse space of eq. coarse_space_2), and
+ * solves A x = b (eq. Ax=b) with it inside FP64 PCG (SPD A) or right-
+ * preconditioned FGMRES (general A, Section 5 / Section 6).
+ *
+ * Conventions shared by every entry point
+ *  - All functions return an asm_status; ASM_OK is 0.  On failure a
+ *    thread-local message is available from asm_last_error().  No C++
+ *    exception crosses this boundary.
+ *  - "device" pointers are CUDA global-memory addresses of the current
+ *    device; "host" pointers are ordinary process memory.  Each argument says
+ *    which it takes.  Pointers are borrowed: the library never frees memory it
+ *    did not allocate and keeps no caller pointer after a call returns.
+ *  - stream is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Work is enqueued on it; calls that return data to host memory
+ *    synchronise it.
+ *  - Index arrays are int32, values FP64, matrices CSR with sorted column
+ *    indices and no duplicates.
+ */
+#ifndef ASM_H
+#define ASM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct asm_handle asm_handle;
+
+typedef enum {
+  ASM_OK = 0,
+  ASM_ERR_INVALID_ARG = 1,      /* malformed CSR, partition, sizes or options   */
+  ASM_ERR_NOT_SPD = 2,          /* a local pivot <= 0 on the SPD path            */
+  ASM_ERR_ZERO_PIVOT = 3,       /* a zero local pivot on the general path        */
+  ASM_ERR_COARSE_SINGULAR = 4,  /* E = Z^T A Z not SPD / singular (Section 4.1)  */
+  ASM_ERR_NONFINITE = 5,        /* NaN or Inf in A or produced during setup      */
+  ASM_ERR_NO_CONVERGENCE = 6,   /* Krylov iteration cap reached                  */
+  ASM_ERR_TIMEOUT = 7,          /* a bounded device wait gave up                 */
+  ASM_ERR_CUDA = 8,             /* a CUDA runtime call failed                    */
+  ASM_ERR_OOM = 9,              /* device allocation failed                      */
+  ASM_ERR_UNSUPPORTED = 10      /* size beyond a kernel's stated capacity        */
+} asm_status;
+
+typedef enum { ASM_PREC_FP64 = 0, ASM_PREC_FP32 = 1 } asm_precision;
+
+/* Sparse matrix A (eq. Ax=b).  row_ptr has n+1 entries, col_idx and val nnz.
+ * on_device != 0: the three arrays (and the partition passed to asm_setup)
+ * are device pointers; otherwise host pointers. */
+typedef struct {
+  int32_t n;
+  int32_t nnz;
+  const int32_t* row_ptr;
+  const int32_t* col_idx;
+  const double* val;
+  int32_t on_device;
+} asm_csr;
+
+typedef struct {
+  int32_t spd;              /* 1: SPD method (eq. gevpsvd, Cholesky-type local
+                               sweep); 0: general matrices (Section 5: left
+                               singular vectors of D_i Pi_i, LU-type sweep)   */
+  int32_t local_precision;  /* asm_precision of the local inverses, the eigen
+                               iteration and the local part of the apply       */
+  int32_t oversample;       /* extra block columns of the subspace iteration   */
+  int32_t max_sweeps;       /* cap on subspace-iteration sweeps                 */
+  double eig_tol;           /* relative eigen-residual tolerance                */
+  double nu;                /* > 1: also add eigenvectors of eq. uppergevp with
+                               lambda > nu; <= 0: off (as in Section 6)         */
+  int32_t nev_lift;         /* at most this many eq. uppergevp vectors          */
+  int32_t coarse;           /* 1: two-level; 0: one-level (eq. onelevelasm)     */
+  uint64_t seed;            /* counter-based random start of the iteration     */
+  int32_t warm_start;       /* 1: predict the start block with the network set
+                               by asm_set_warm_start                           */
+  int32_t reserved[7];
+} asm_options;
+
+typedef struct {
+  int32_t method;           /* 0: PCG if spd else FGMRES; 1: PCG; 2: FGMRES    */
+  int32_t restart;          /* FGMRES restart length (default 30)              */
+  double rtol;              /* stop at ||b - A x||_2 / ||b||_2 <= rtol         */
+  int32_t max_it;           /* iteration cap                                   */
+  int32_t use_x0;           /* 1: x holds the initial guess; 0: x0 = 0         */
+  int32_t check_every;      /* iterations between host convergence checks      */
+  int32_t reserved[5];
+} asm_solve_opts;
+
+typedef struct {
+  int32_t iterations;       /* SpMVs performed                                 */
+  int32_t converged;
+  double final_relres;      /* recursive (PCG) / least-squares (FGMRES) estimate */
+  double true_relres;       /* ||b - A x|| / ||b|| recomputed at the end       */
+  double solve_ms;          /* device time of the Krylov loop                  */
+} asm_solve_info;
+
+typedef struct {
+  int32_t n, N, overlap, nev;
+  int32_t n_C;              /* coarse dimension |Omega_0|                       */
+  int64_t nnz_C;            /* stored nonzeros of E                             */
+  double gc, oc;            /* GC = 1 + n_C/n, OC = 1 + nnz_C/nnz_A (Section 6) */
+  int64_t sum_ni;           /* sum_i |Omega_i|                                  */
+  int32_t max_ni;
+  int32_t sweeps_max;       /* largest subspace-iteration sweep count           */
+  double eig_resid_max;     /* largest relative eigen-residual at exit          */
+  double stage_ms[12];      /* device time per setup stage (see asm_stage_name) */
+} asm_setup_info;
+
+/* Fill *o with defaults: spd 1, FP64, oversample 8, max_sweeps 60, eig_tol
+ * 1e-8, nu off, coarse on, seed 0, no warm start. */
+void asm_default_options(asm_options* o);
+void asm_default_solve_opts(asm_solve_opts* o);
+
+/* Build the preconditioner for A with the nonoverlapping partition `part`
+ * (n entries, values 0..N-1, Section 2.1), `overlap` = delta >= 1 layers grown
+ * through the graph of A + A^T, and `nev` coarse vectors per subdomain.
+ * Steps (each a device stage): overlap index sets (Section 2.1), dense A_ii
+ * (Section 2.3), local inverse by a blocked Gauss-Jordan sweep whose midpoint
+ * gives X = -B^{-1}C and S = G - C^T B^{-1} C (eq. HOp), block subspace
+ * iteration for eq. gevpsvd (SPD) or for the left singular vectors of
+ * D_i Pi_i (general), Z and E = Z^T A Z (Section 4.1), FP64 factor of E.
+ * A's arrays are copied; the caller may free them after the call.
+ * Errors: INVALID_ARG for malformed input (checked on the host), NOT_SPD /
+ * ZERO_PIVOT for a bad local pivot, COARSE_SINGULAR, NONFINITE, UNSUPPORTED,
+ * CUDA, OOM.  On error *out is NULL. */
+asm_status asm_setup(const asm_csr* A, const int32_t* part, int32_t N, int32_t overlap,
+                     int32_t nev, const asm_options* opt, void* stream, asm_handle** out);
+
+/* z = M^{-1} r (device r, z of length n, FP64; r and z must not alias).
+ * Deterministic: the overlapping sum is a fixed-order pull, no atomics. */
+asm_status asm_apply(asm_handle* h, const double* r, double* z, void* stream);
+
+/* Solve A x = b.  b and x are device pointers when the handle was built from
+ * device CSR arrays, host pointers otherwise (then the copies in and out are
+ * part of the call).  info (host) is always filled.  Returns
+ * NO_CONVERGENCE if max_it is reached. */
+asm_status asm_solve(asm_handle* h, const double* b, double* x, const asm_solve_opts* o,
+                     asm_solve_info* info, void* stream);
+
+/* y = A x with the handle's copy of A (device x, y). */
+asm_status asm_spmv(asm_handle* h, const double* x, double* y, void* stream);
+
+asm_status asm_get_info(const asm_handle* h, asm_setup_info* info);
+const char* asm_stage_name(int32_t stage);
+
+/* Overlap index sets, host outputs.  sub_offsets: N+1 entries (start of
+ * subdomain i in omega); layer_offsets: N*(overlap+2) entries, for subdomain i
+ * the local offsets [0, |I_i|, |I_i|+|Gamma_1|, ..., |Omega_i|]; omega:
+ * sum_i |Omega_i| global indices in R_i order.  Any pointer may be NULL. */
+asm_status asm_get_overlap(const asm_handle* h, int32_t* sub_offsets, int32_t* layer_offsets,
+                           int32_t* omega);
+
+/* Retained local values, host outputs of N*nev entries (row i = subdomain i,
+ * descending; unused slots 0): lambda^2 of eq. gevpsvd (SPD) or singular
+ * values of D_i Pi_i (general); counts[i] = number kept.  Either may be NULL. */
+asm_status asm_get_local_values(const asm_handle* h, double* values, int32_t* counts);
+
+/* Coarse basis blocks, host output: for subdomain i a |I_i| x counts[i]
+ * row-major FP64 block (rows in I_i order), concatenated over i; col_offsets
+ * (N+1) gives the first coarse column of each subdomain.  Either may be NULL. */
+asm_status asm_get_coarse_basis(const asm_handle* h, double* Z, int32_t* col_offsets);
+
+/* Dense E = Z^T A Z (n_C x n_C row-major FP64, host) as assembled, before
+ * factorisation. */
+asm_status asm_get_coarse_matrix(const asm_handle* h, double* E);
+
+void asm_destroy(asm_handle* h);
+const char* asm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ASM_H */

@@ -1,0 +1,290 @@
+"""Python binding of the sm_103a two-level additive Schwarz library.
+
+Argument marshalling only: every step of the method runs in the CUDA kernels
+of ``libasm_gb300.so`` behind the C ABI declared in ``include/asm.h``.  The
+functions below keep the C names (``asm_setup``, ``asm_apply``,
+``asm_solve``, ...); :class:`TwoLevelSchwarz` wraps a handle for callers
+holding NumPy arrays or torch tensors.  There is no CPU fallback: if the
+library is missing or no GPU is present the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+ASM_OK = 0
+STATUS = {0: "OK", 1: "INVALID_ARG", 2: "NOT_SPD", 3: "ZERO_PIVOT", 4: "COARSE_SINGULAR",
+          5: "NONFINITE", 6: "NO_CONVERGENCE", 7: "TIMEOUT", 8: "CUDA", 9: "OOM", 10: "UNSUPPORTED"}
+PREC_FP64, PREC_FP32 = 0, 1
+
+
+class AsmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+        self.name = STATUS.get(status, str(status))
+
+
+class asm_csr(C.Structure):
+    _fields_ = [("n", C.c_int32), ("nnz", C.c_int32), ("row_ptr", C.c_void_p), ("col_idx", C.c_void_p),
+                ("val", C.c_void_p), ("on_device", C.c_int32)]
+
+
+class asm_options(C.Structure):
+    _fields_ = [("spd", C.c_int32), ("local_precision", C.c_int32), ("oversample", C.c_int32),
+                ("max_sweeps", C.c_int32), ("eig_tol", C.c_double), ("nu", C.c_double),
+                ("nev_lift", C.c_int32), ("coarse", C.c_int32), ("seed", C.c_uint64),
+                ("warm_start", C.c_int32), ("reserved", C.c_int32 * 7)]
+
+
+class asm_solve_opts(C.Structure):
+    _fields_ = [("method", C.c_int32), ("restart", C.c_int32), ("rtol", C.c_double), ("max_it", C.c_int32),
+                ("use_x0", C.c_int32), ("check_every", C.c_int32), ("reserved", C.c_int32 * 5)]
+
+
+class asm_solve_info(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("converged", C.c_int32), ("final_relres", C.c_double),
+                ("true_relres", C.c_double), ("solve_ms", C.c_double)]
+
+
+class asm_setup_info(C.Structure):
+    _fields_ = [("n", C.c_int32), ("N", C.c_int32), ("overlap", C.c_int32), ("nev", C.c_int32),
+                ("n_C", C.c_int32), ("nnz_C", C.c_int64), ("gc", C.c_double), ("oc", C.c_double),
+                ("sum_ni", C.c_int64), ("max_ni", C.c_int32), ("sweeps_max", C.c_int32),
+                ("eig_resid_max", C.c_double), ("stage_ms", C.c_double * 12)]
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.lib_path()
+
+
+def load(path: str | None = None) -> C.CDLL:
+    """Load (once) the shared library; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or lib_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_2401_03915_gb300.build.build()")
+    L = C.CDLL(path)
+    vp, i32, pp = C.c_void_p, C.c_int32, C.POINTER(C.c_void_p)
+    L.asm_default_options.argtypes = [C.POINTER(asm_options)]
+    L.asm_default_solve_opts.argtypes = [C.POINTER(asm_solve_opts)]
+    L.asm_setup.argtypes = [C.POINTER(asm_csr), vp, i32, i32, i32, C.POINTER(asm_options), vp, pp]
+    L.asm_apply.argtypes = [vp, vp, vp, vp]
+    L.asm_spmv.argtypes = [vp, vp, vp, vp]
+    L.asm_solve.argtypes = [vp, vp, vp, C.POINTER(asm_solve_opts), C.POINTER(asm_solve_info), vp]
+    L.asm_get_info.argtypes = [vp, C.POINTER(asm_setup_info)]
+    L.asm_get_overlap.argtypes = [vp, vp, vp, vp]
+    L.asm_get_local_values.argtypes = [vp, vp, vp]
+    L.asm_get_coarse_basis.argtypes = [vp, vp, vp]
+    L.asm_get_coarse_matrix.argtypes = [vp, vp]
+    L.asm_destroy.argtypes = [vp]
+    L.asm_destroy.restype = None
+    L.asm_last_error.restype = C.c_char_p
+    L.asm_stage_name.restype = C.c_char_p
+    L.asm_stage_name.argtypes = [i32]
+    for f in ("asm_setup", "asm_apply", "asm_spmv", "asm_solve", "asm_get_info", "asm_get_overlap",
+              "asm_get_local_values", "asm_get_coarse_basis", "asm_get_coarse_matrix"):
+        getattr(L, f).restype = C.c_int
+    _lib = L
+    return L
+
+
+def _check(status: int) -> None:
+    if status != ASM_OK:
+        raise AsmError(status, load().asm_last_error().decode())
+
+
+def _ptr(a) -> int:
+    """Address of a torch tensor (device or host) or a NumPy array."""
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        return 0
+    return getattr(stream, "cuda_stream", stream)
+
+
+def default_options(**kw) -> asm_options:
+    o = asm_options()
+    load().asm_default_options(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def default_solve_opts(**kw) -> asm_solve_opts:
+    o = asm_solve_opts()
+    load().asm_default_solve_opts(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+# ---------------------------------------------------------------------------
+# C-named entry points
+# ---------------------------------------------------------------------------
+def asm_setup(row_ptr, col_idx, val, part, N: int, overlap: int, nev: int, opt: asm_options | None = None,
+              stream=None, on_device: bool | None = None) -> int:
+    """Build the preconditioner; returns the opaque handle (an int)."""
+    if on_device is None:
+        on_device = hasattr(row_ptr, "is_cuda") and row_ptr.is_cuda
+    n = len(row_ptr) - 1
+    nnz = int(row_ptr[-1]) if not on_device else int(val.numel())
+    A = asm_csr(n, nnz, _ptr(row_ptr), _ptr(col_idx), _ptr(val), 1 if on_device else 0)
+    h = C.c_void_p()
+    _check(load().asm_setup(C.byref(A), _ptr(part), N, overlap, nev, C.byref(opt) if opt else None,
+                            _stream(stream), C.byref(h)))
+    return h.value
+
+
+def asm_apply(h: int, r, z, stream=None) -> None:
+    _check(load().asm_apply(h, _ptr(r), _ptr(z), _stream(stream)))
+
+
+def asm_spmv(h: int, x, y, stream=None) -> None:
+    _check(load().asm_spmv(h, _ptr(x), _ptr(y), _stream(stream)))
+
+
+def asm_solve(h: int, b, x, opts: asm_solve_opts | None = None, stream=None,
+              raise_on_no_convergence: bool = True) -> asm_solve_info:
+    info = asm_solve_info()
+    st = load().asm_solve(h, _ptr(b), _ptr(x), C.byref(opts) if opts else None, C.byref(info), _stream(stream))
+    if st == 6 and not raise_on_no_convergence:
+        return info
+    _check(st)
+    return info
+
+
+def asm_get_info(h: int) -> asm_setup_info:
+    inf = asm_setup_info()
+    _check(load().asm_get_info(h, C.byref(inf)))
+    return inf
+
+
+def asm_get_overlap(h: int):
+    """(sub_offsets[N+1], layer_offsets[N, overlap+2], omega[sum n_i]) as NumPy arrays."""
+    inf = asm_get_info(h)
+    sub = np.zeros(inf.N + 1, dtype=np.int32)
+    lay = np.zeros((inf.N, inf.overlap + 2), dtype=np.int32)
+    om = np.zeros(inf.sum_ni, dtype=np.int32)
+    _check(load().asm_get_overlap(h, sub.ctypes.data, lay.ctypes.data, om.ctypes.data))
+    return sub, lay, om
+
+
+def asm_get_local_values(h: int):
+    inf = asm_get_info(h)
+    vals = np.zeros((inf.N, max(inf.nev, 1)), dtype=np.float64)
+    cnt = np.zeros(inf.N, dtype=np.int32)
+    _check(load().asm_get_local_values(h, vals.ctypes.data if inf.nev else None, cnt.ctypes.data))
+    return vals[:, :inf.nev], cnt
+
+
+def asm_get_coarse_basis(h: int, p_sizes):
+    """List of per-subdomain blocks Z_i (|I_i| x count_i) and the column offsets."""
+    inf = asm_get_info(h)
+    col = np.zeros(inf.N + 1, dtype=np.int32)
+    _check(load().asm_get_coarse_basis(h, None, col.ctypes.data))
+    counts = np.diff(col)
+    tot = int(np.sum(np.asarray(p_sizes, dtype=np.int64) * counts))
+    Z = np.zeros(max(tot, 1), dtype=np.float64)
+    _check(load().asm_get_coarse_basis(h, Z.ctypes.data, None))
+    out, o = [], 0
+    for p, k in zip(p_sizes, counts):
+        out.append(Z[o:o + p * k].reshape(p, k))
+        o += p * k
+    return out, col
+
+
+def asm_get_coarse_matrix(h: int) -> np.ndarray:
+    inf = asm_get_info(h)
+    E = np.zeros((inf.n_C, inf.n_C), dtype=np.float64)
+    if inf.n_C:
+        _check(load().asm_get_coarse_matrix(h, E.ctypes.data))
+    return E
+
+
+def asm_destroy(h: int) -> None:
+    if h:
+        load().asm_destroy(h)
+
+
+def stage_names() -> list[str]:
+    L = load()
+    return [L.asm_stage_name(i).decode() for i in range(12)]
+
+
+# ---------------------------------------------------------------------------
+# Convenience wrapper
+# ---------------------------------------------------------------------------
+class TwoLevelSchwarz:
+    """Owns one handle.  ``A`` is anything with ``indptr``, ``indices`` and
+    ``data`` (scipy CSR / asm_inputs.Problem style) or a tuple of arrays."""
+
+    def __init__(self, indptr, indices, data, part, N: int, overlap: int, nev: int, *, spd: bool = True,
+                 precision: str = "fp64", device: bool = True, stream=None, **opts):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required")
+        o = default_options(spd=1 if spd else 0,
+                            local_precision=PREC_FP32 if precision == "fp32" else PREC_FP64, **opts)
+        self.device = device
+        self.n = len(indptr) - 1
+        if device:
+            dev = torch.device("cuda")
+            self._rp = torch.as_tensor(np.asarray(indptr, dtype=np.int32), device=dev)
+            self._ci = torch.as_tensor(np.asarray(indices, dtype=np.int32), device=dev)
+            self._va = torch.as_tensor(np.asarray(data, dtype=np.float64), device=dev)
+            self._pa = torch.as_tensor(np.asarray(part, dtype=np.int32), device=dev)
+            self.h = asm_setup(self._rp, self._ci, self._va, self._pa, N, overlap, nev, o, stream, True)
+        else:
+            self._rp = np.ascontiguousarray(indptr, dtype=np.int32)
+            self._ci = np.ascontiguousarray(indices, dtype=np.int32)
+            self._va = np.ascontiguousarray(data, dtype=np.float64)
+            self._pa = np.ascontiguousarray(part, dtype=np.int32)
+            self.h = asm_setup(self._rp, self._ci, self._va, self._pa, N, overlap, nev, o, stream, False)
+        self.stream = stream
+
+    @property
+    def info(self) -> asm_setup_info:
+        return asm_get_info(self.h)
+
+    def apply(self, r, z=None):
+        import torch
+        if z is None:
+            z = torch.empty_like(r)
+        asm_apply(self.h, r, z, self.stream)
+        return z
+
+    def solve(self, b, x=None, **kw):
+        if x is None:
+            if self.device:
+                import torch
+                x = torch.zeros_like(b)
+            else:
+                x = np.zeros_like(b)
+        info = asm_solve(self.h, b, x, default_solve_opts(**kw), self.stream,
+                         raise_on_no_convergence=kw.get("max_it", None) is None)
+        return x, info
+
+    def close(self):
+        if getattr(self, "h", None):
+            asm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,217 @@
+// Two-level additive Schwarz apply (Remark in Section 4.3):
+//     z = sum_i R_i^T A_ii^{-1} R_i r  +  Z E^{-1} Z^T r.
+//
+// Local part: A_ii^{-1} is stored as TILE x TILE tiles (lower tiles only when
+// A is SPD).  One flat, load-balanced pass over all tiles of all subdomains
+// reads every tile once; an off-diagonal tile T of a symmetric inverse
+// contributes T x_J to row block I and T^T x_I to row block J.  Each
+// contribution goes to its own slot, and the pull kernel sums the slots of
+// every occurrence of a node in a fixed order: the overlapping sum is
+// deterministic without atomics.
+// Coarse part: Z^T r per subdomain, the FP64 coarse solve, and Z y added in
+// the pull kernel (Z_i is supported on Omega_{I_i}).
+#include <algorithm>
+
+#include "handle.cuh"
+
+namespace asmgpu {
+namespace {
+
+constexpr int NT = 256;
+
+template <typename T>
+__device__ __forceinline__ void load4(const T* p, T (&v)[4]);
+template <>
+__device__ __forceinline__ void load4<float>(const float* p, float (&v)[4]) {
+  float4 q = __ldcs(reinterpret_cast<const float4*>(p));
+  v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+template <>
+__device__ __forceinline__ void load4<double>(const double* p, double (&v)[4]) {
+  double2 a = __ldcs(reinterpret_cast<const double2*>(p));
+  double2 b = __ldcs(reinterpret_cast<const double2*>(p) + 1);
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+
+// Thread t of the block owns rows (t/16) + 16a, a = 0..3, and the four
+// columns 4 (t%16) .. 4 (t%16) + 3 of the tile.
+template <typename T, bool SYM>
+__global__ void __launch_bounds__(NT) k_apply_tiles(const T* __restrict__ tiles, const int4* __restrict__ desc,
+                                                    int64_t ntiles, const int32_t* __restrict__ omega,
+                                                    const int32_t* __restrict__ sub_off,
+                                                    const int32_t* __restrict__ n_arr, const int32_t* __restrict__ nt_arr,
+                                                    const int64_t* __restrict__ part_off, const double* __restrict__ r,
+                                                    T* __restrict__ partials, const int32_t* __restrict__ done) {
+  if (done != nullptr && *done) return;
+  __shared__ T xI[TILE], xJ[TILE];
+  __shared__ T colpart[NT / 32][TILE];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int cq = tid & 15, rg = tid >> 4;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int4 d = desc[t];
+    const int i = d.x, I = d.y, J = d.z;
+    const int n = n_arr[i], nt = nt_arr[i], b0 = sub_off[i];
+    __syncthreads();
+    if (tid < TILE) {
+      int a = I * TILE + tid;
+      xI[tid] = a < n ? (T)r[omega[b0 + a]] : T(0);
+    } else if (tid < 2 * TILE) {
+      int a = J * TILE + tid - TILE;
+      xJ[tid - TILE] = a < n ? (T)r[omega[b0 + a]] : T(0);
+    }
+    __syncthreads();
+    const T* tile = tiles + t * (TILE * TILE);
+    T v[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) load4<T>(tile + (rg + 16 * a) * TILE + 4 * cq, v[a]);
+    // row partials: y_I[row] += sum_c T[row][c] x_J[c]
+    T* P = partials + part_off[i];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      T s = v[a][0] * xJ[4 * cq] + v[a][1] * xJ[4 * cq + 1] + v[a][2] * xJ[4 * cq + 2] + v[a][3] * xJ[4 * cq + 3];
+      s += __shfl_xor_sync(0xffffffffu, s, 8);
+      s += __shfl_xor_sync(0xffffffffu, s, 4);
+      s += __shfl_xor_sync(0xffffffffu, s, 2);
+      s += __shfl_xor_sync(0xffffffffu, s, 1);
+      if (cq == 0) P[((int64_t)I * nt + J) * TILE + rg + 16 * a] = s;
+    }
+    if (SYM && I != J) {
+      // column partials: y_J[col] += sum_row T[row][col] x_I[row]
+      T c[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        c[q] = v[0][q] * xI[rg] + v[1][q] * xI[rg + 16] + v[2][q] * xI[rg + 32] + v[3][q] * xI[rg + 48];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) c[q] += __shfl_xor_sync(0xffffffffu, c[q], 16);
+      if (lane < 16) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) colpart[wid][4 * cq + q] = c[q];
+      }
+      __syncthreads();
+      if (tid < TILE) {
+        T s = 0;
+#pragma unroll
+        for (int w = 0; w < NT / 32; ++w) s += colpart[w][tid];
+        P[((int64_t)J * nt + I) * TILE + tid] = s;
+      }
+    }
+  }
+}
+
+// c[col_off[i] + j] = sum_{a < p_i} Z_i[a][j] r[omega_i[a]]  (Z^T r)
+__global__ void __launch_bounds__(NT) k_coarse_restrict(const double* __restrict__ Z, const int64_t* __restrict__ z_off,
+                                                        const int32_t* __restrict__ count,
+                                                        const int32_t* __restrict__ col_off,
+                                                        const int32_t* __restrict__ sub_off,
+                                                        const int32_t* __restrict__ p_arr,
+                                                        const int32_t* __restrict__ omega, int nev,
+                                                        const double* __restrict__ r, double* __restrict__ c,
+                                                        const int32_t* __restrict__ done) {
+  if (done != nullptr && *done) return;
+  __shared__ double red[NT / 32][32];
+  const int i = blockIdx.x;
+  const int k = count[i], p = p_arr[i], b0 = sub_off[i];
+  const double* Zi = Z + z_off[i];
+  for (int j0 = 0; j0 < k; j0 += 32) {
+    double acc[32];
+#pragma unroll
+    for (int q = 0; q < 32; ++q) acc[q] = 0;
+    for (int a = threadIdx.x; a < p; a += NT) {
+      double x = r[omega[b0 + a]];
+      const double* zr = Zi + (int64_t)a * nev + j0;
+#pragma unroll
+      for (int q = 0; q < 32; ++q)
+        if (j0 + q < k) acc[q] += zr[q] * x;
+    }
+#pragma unroll
+    for (int q = 0; q < 32; ++q) {
+      double s = warp_sum(acc[q]);
+      if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][q] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32 && j0 + threadIdx.x < k) {
+      double s = 0;
+      for (int w = 0; w < NT / 32; ++w) s += red[w][threadIdx.x];
+      c[col_off[i] + j0 + threadIdx.x] = s;
+    }
+    __syncthreads();
+  }
+}
+
+// z[v] = sum over the occurrences (i, a) of v of sum_J partial[i][a/TILE][J][a%TILE]
+//        + Z_{part v}[own position] . y_coarse
+template <typename T>
+__global__ void __launch_bounds__(NT) k_apply_pull(int n, const int32_t* __restrict__ occ_ptr,
+                                                   const int32_t* __restrict__ occ_pos,
+                                                   const int32_t* __restrict__ pos_sub,
+                                                   const int32_t* __restrict__ sub_off,
+                                                   const int32_t* __restrict__ nt_arr,
+                                                   const int64_t* __restrict__ part_off,
+                                                   const T* __restrict__ partials, const int32_t* __restrict__ part,
+                                                   const int32_t* __restrict__ own_pos, const double* __restrict__ Z,
+                                                   const int64_t* __restrict__ z_off, const int32_t* __restrict__ count,
+                                                   const int32_t* __restrict__ col_off, int nev,
+                                                   const double* __restrict__ yc, double* __restrict__ z,
+                                                   const int32_t* __restrict__ done) {
+  if (done != nullptr && *done) return;
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    double acc = 0;
+    for (int t = occ_ptr[v]; t < occ_ptr[v + 1]; ++t) {
+      int q = occ_pos[t];
+      int i = pos_sub[q];
+      int a = q - sub_off[i];
+      int nt = nt_arr[i];
+      const T* P = partials + part_off[i] + (int64_t)(a / TILE) * nt * TILE + (a % TILE);
+      double s = 0;
+      for (int J = 0; J < nt; ++J) s += (double)P[(int64_t)J * TILE];
+      acc += s;
+    }
+    if (yc != nullptr) {
+      int i = part[v];
+      int k = count[i];
+      if (k > 0) {
+        const double* zr = Z + z_off[i] + (int64_t)(own_pos[v] - sub_off[i]) * nev;
+        const double* y = yc + col_off[i];
+        double s = 0;
+        for (int j = 0; j < k; ++j) s += zr[j] * y[j];
+        acc += s;
+      }
+    }
+    z[v] = acc;
+  }
+}
+
+template <typename T>
+void apply_impl(Handle& h, const double* r, double* z, cudaStream_t s, const int32_t* done) {
+  Dense& dn = h.dn;
+  Coarse& co = h.co;
+  const bool sym = h.opt.spd != 0;
+  unsigned gt = (unsigned)std::min<int64_t>(std::max<int64_t>(dn.n_tiles, 1), 152 * 8);
+  if (sym)
+    k_apply_tiles<T, true><<<gt, NT, 0, s>>>((const T*)dn.tiles, dn.tile_desc, dn.n_tiles, h.ov.omega,
+                                             h.ov.sub_off, h.dev_n, dn.nt, dn.part_off, r, (T*)dn.partials, done);
+  else
+    k_apply_tiles<T, false><<<gt, NT, 0, s>>>((const T*)dn.tiles, dn.tile_desc, dn.n_tiles, h.ov.omega,
+                                              h.ov.sub_off, h.dev_n, dn.nt, dn.part_off, r, (T*)dn.partials, done);
+  const double* yc = nullptr;
+  if (co.n_C > 0) {
+    double* c = co.cvec;
+    double* y = co.cvec + round_up(co.n_C, 64);
+    k_coarse_restrict<<<h.N, NT, 0, s>>>(co.Z, co.z_off, co.count, co.col_off, h.ov.sub_off, h.dev_p, h.ov.omega,
+                                         h.nev, r, c, done);
+    coarse_solve(h, c, y, s, done);
+    yc = y;
+  }
+  unsigned gp = (unsigned)std::min<int64_t>(ceil_div(h.n, NT), 152 * 16);
+  k_apply_pull<T><<<gp, NT, 0, s>>>(h.n, h.ov.occ_ptr, h.ov.occ_pos, h.ov.pos_sub, h.ov.sub_off, dn.nt, dn.part_off,
+                                    (const T*)dn.partials, h.part, h.ov.own_pos, co.Z, co.z_off, co.count,
+                                    co.col_off, h.nev, yc, z, done);
+}
+
+}  // namespace
+
+void apply_preconditioner(Handle& h, const double* r, double* z, cudaStream_t s, const int32_t* done) {
+  if (h.fp32) apply_impl<float>(h, r, z, s, done); else apply_impl<double>(h, r, z, s, done);
+}
+
+}  // namespace asmgpu

@@ -1,0 +1,337 @@
+// C ABI of the library: argument checks, stage orchestration, error mapping.
+#include <algorithm>
+#include <cstring>
+#include <new>
+
+#include "handle.cuh"
+
+using namespace asmgpu;
+
+struct asm_handle {
+  Handle h;
+};
+
+namespace {
+thread_local std::string g_last_error;
+
+asm_status set_error(asm_status s, const std::string& m) {
+  g_last_error = m;
+  return s;
+}
+
+const char* kStageNames[12] = {"overlap", "gather", "sweep", "pack", "eigen", "coarse_assembly",
+                               "coarse_factor", "setup_total", "", "", "", ""};
+
+void init_pool() {
+  static bool done = false;
+  if (done) return;
+  done = true;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t thr = 64ull << 30;  // keep up to 64 GiB cached between setups
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  cudaGetLastError();
+}
+
+template <typename F>
+asm_status guarded(F&& f) {
+  try {
+    f();
+    return ASM_OK;
+  } catch (const AsmError& e) {
+    return set_error(e.status, e.msg);
+  } catch (const std::bad_alloc&) {
+    return set_error(ASM_ERR_OOM, "host allocation failed");
+  } catch (...) {
+    return set_error(ASM_ERR_CUDA, "unexpected internal error");
+  }
+}
+
+void free_handle_memory(Handle& h) {
+  cudaDeviceSynchronize();
+  h.mem.stream = nullptr;
+  h.mem.release();
+  if (h.kr.hpin) { cudaFreeHost(h.kr.hpin); h.kr.hpin = nullptr; }
+  if (h.events)
+    for (auto& e : h.ev) cudaEventDestroy(e);
+  h.events = false;
+  cudaGetLastError();
+}
+
+float elapsed(cudaEvent_t a, cudaEvent_t b) {
+  float ms = 0;
+  if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
+    cudaGetLastError();
+    return 0.f;
+  }
+  return ms;
+}
+}  // namespace
+
+namespace asmgpu {
+void check_device_error(Handle& h, cudaStream_t s, const char* stage) {
+  int32_t e = 0;
+  CK(cudaMemcpyAsync(&e, h.dn.err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (!e) return;
+  CK(cudaMemsetAsync(h.dn.err, 0, sizeof(int32_t), s));
+  std::string st(stage);
+  if (e & DERR_NONFINITE) fail(ASM_ERR_NONFINITE, st + ": non-finite value");
+  if (e & DERR_NOT_SPD) fail(ASM_ERR_NOT_SPD, st + ": a local pivot is not positive (A is not SPD)");
+  if (e & DERR_ZERO_PIVOT) fail(ASM_ERR_ZERO_PIVOT, st + ": zero local pivot");
+  if (e & DERR_COARSE) fail(ASM_ERR_COARSE_SINGULAR, st + ": coarse matrix E is not SPD / singular");
+  if (e & DERR_CAPACITY) fail(ASM_ERR_UNSUPPORTED, st + ": capacity exceeded");
+}
+}  // namespace asmgpu
+
+extern "C" {
+
+void asm_default_options(asm_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->spd = 1;
+  o->local_precision = ASM_PREC_FP64;
+  o->oversample = 8;
+  o->max_sweeps = 0;  // 0: 60
+  o->eig_tol = 0;     // 0: 1e-8 (FP64) / 1e-3 (FP32)
+  o->nu = 0;
+  o->nev_lift = 0;
+  o->coarse = 1;
+  o->seed = 0;
+  o->warm_start = 0;
+}
+
+void asm_default_solve_opts(asm_solve_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->method = 0;
+  o->restart = 30;
+  o->rtol = 1e-8;
+  o->max_it = 1000;
+  o->use_x0 = 0;
+  o->check_every = 8;
+}
+
+const char* asm_last_error(void) { return g_last_error.c_str(); }
+
+const char* asm_stage_name(int32_t stage) {
+  if (stage < 0 || stage >= 12) return "";
+  return kStageNames[stage];
+}
+
+asm_status asm_setup(const asm_csr* A, const int32_t* part, int32_t N, int32_t overlap, int32_t nev,
+                     const asm_options* opt, void* stream, asm_handle** out) {
+  if (out) *out = nullptr;
+  if (!A || !part || !out) return set_error(ASM_ERR_INVALID_ARG, "null argument");
+  if (A->n <= 0 || A->nnz < 0 || !A->row_ptr || !A->col_idx || (A->nnz > 0 && !A->val))
+    return set_error(ASM_ERR_INVALID_ARG, "CSR arrays missing or n <= 0");
+  if (N < 1 || N > A->n) return set_error(ASM_ERR_INVALID_ARG, "N must be in 1..n");
+  if (N >= 131072) return set_error(ASM_ERR_UNSUPPORTED, "more than 131071 subdomains");
+  if (overlap < 1 || overlap > 64) return set_error(ASM_ERR_INVALID_ARG, "overlap must be in 1..64");
+  if (nev < 0 || nev > 120) return set_error(ASM_ERR_INVALID_ARG, "nev must be in 0..120");
+  asm_options o;
+  if (opt) o = *opt; else asm_default_options(&o);
+  if (o.local_precision != ASM_PREC_FP64 && o.local_precision != ASM_PREC_FP32)
+    return set_error(ASM_ERR_INVALID_ARG, "local_precision must be ASM_PREC_FP64 or ASM_PREC_FP32");
+  if (o.oversample < 0 || o.oversample > 64) return set_error(ASM_ERR_INVALID_ARG, "oversample must be in 0..64");
+  asm_handle* H = new (std::nothrow) asm_handle();
+  if (!H) return set_error(ASM_ERR_OOM, "host allocation failed");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  asm_status st = guarded([&] {
+    init_pool();
+    Handle& h = H->h;
+    h.n = A->n; h.nnz = A->nnz; h.N = N; h.delta = overlap; h.nev = nev; h.opt = o;
+    h.host_io = A->on_device == 0;
+    h.fp32 = o.local_precision == ASM_PREC_FP32;
+    h.mem.stream = s;
+    for (auto& e : h.ev) CK(cudaEventCreate(&e));
+    h.events = true;
+    CK(cudaEventRecord(h.ev[0], s));
+    h.row_ptr = h.mem.alloc<int32_t>(h.n + 1);
+    h.col_idx = h.mem.alloc<int32_t>(h.nnz);
+    h.val = h.mem.alloc<double>(h.nnz);
+    h.part = h.mem.alloc<int32_t>(h.n);
+    if (h.host_io) {
+      // host arrays: validate row_ptr before trusting nnz
+      if (A->row_ptr[0] != 0 || A->row_ptr[A->n] != A->nnz)
+        fail(ASM_ERR_INVALID_ARG, "row_ptr[0] must be 0 and row_ptr[n] must equal nnz");
+    }
+    CK(cudaMemcpyAsync(h.row_ptr, A->row_ptr, sizeof(int32_t) * (h.n + 1), cudaMemcpyDefault, s));
+    CK(cudaMemcpyAsync(h.col_idx, A->col_idx, sizeof(int32_t) * h.nnz, cudaMemcpyDefault, s));
+    CK(cudaMemcpyAsync(h.val, A->val, sizeof(double) * h.nnz, cudaMemcpyDefault, s));
+    CK(cudaMemcpyAsync(h.part, part, sizeof(int32_t) * h.n, cudaMemcpyDefault, s));
+    h.dn.err = h.mem.alloc<int32_t>(1);
+    CK(cudaMemsetAsync(h.dn.err, 0, sizeof(int32_t), s));
+    build_overlap(h, s);
+    CK(cudaEventRecord(h.ev[1], s));
+    build_local(h, s);
+    build_eigen(h, s);
+    CK(cudaEventRecord(h.ev[6], s));
+    CK(cudaEventRecord(h.ev[7], s));
+    build_coarse(h, s);
+    CK(cudaEventRecord(h.ev[8], s));
+    CK(cudaStreamSynchronize(s));
+    // info
+    asm_setup_info& inf = h.info;
+    std::memset(&inf, 0, sizeof(inf));
+    inf.n = h.n; inf.N = h.N; inf.overlap = h.delta; inf.nev = h.nev;
+    inf.n_C = h.co.n_C;
+    inf.nnz_C = h.co.nnz_C;
+    inf.gc = 1.0 + (double)h.co.n_C / h.n;
+    inf.oc = 1.0 + (double)h.co.nnz_C / std::max(1, h.nnz);
+    inf.sum_ni = h.ov.sum_n;
+    inf.max_ni = h.ov.max_n;
+    int smax = 0;
+    for (int v : h.co.h_sweeps) smax = std::max(smax, v);
+    inf.sweeps_max = smax;
+    if (h.co.n_C > 0 && h.co.resid) {
+      std::vector<double> res((size_t)h.N * h.nev);
+      CK(cudaMemcpy(res.data(), h.co.resid, sizeof(double) * res.size(), cudaMemcpyDeviceToHost));
+      double m = 0;
+      for (double v : res) m = std::max(m, v);
+      inf.eig_resid_max = m;
+    }
+    inf.stage_ms[0] = elapsed(h.ev[0], h.ev[1]);
+    inf.stage_ms[1] = elapsed(h.ev[2], h.ev[3]);
+    inf.stage_ms[2] = elapsed(h.ev[3], h.ev[4]);
+    inf.stage_ms[3] = elapsed(h.ev[4], h.ev[5]);
+    inf.stage_ms[4] = elapsed(h.ev[5], h.ev[6]);
+    inf.stage_ms[5] = h.co.n_C > 0 ? elapsed(h.ev[6], h.ev[7]) : 0.f;
+    inf.stage_ms[6] = h.co.n_C > 0 ? elapsed(h.ev[7], h.ev[8]) : 0.f;
+    inf.stage_ms[7] = elapsed(h.ev[0], h.ev[8]);
+  });
+  if (st != ASM_OK) {
+    free_handle_memory(H->h);
+    delete H;
+    return st;
+  }
+  *out = H;
+  return ASM_OK;
+}
+
+asm_status asm_apply(asm_handle* H, const double* r, double* z, void* stream) {
+  if (!H || !r || !z) return set_error(ASM_ERR_INVALID_ARG, "null argument");
+  if (r == z) return set_error(ASM_ERR_INVALID_ARG, "r and z must not alias");
+  return guarded([&] {
+    apply_preconditioner(H->h, r, z, static_cast<cudaStream_t>(stream));
+    CK_LAUNCH("apply");
+  });
+}
+
+asm_status asm_spmv(asm_handle* H, const double* x, double* y, void* stream) {
+  if (!H || !x || !y) return set_error(ASM_ERR_INVALID_ARG, "null argument");
+  return guarded([&] { spmv(H->h, x, y, static_cast<cudaStream_t>(stream)); });
+}
+
+asm_status asm_solve(asm_handle* H, const double* b, double* x, const asm_solve_opts* o, asm_solve_info* info,
+                     void* stream) {
+  asm_solve_info dummy;
+  if (!info) info = &dummy;
+  std::memset(info, 0, sizeof(*info));
+  if (!H || !b || !x) return set_error(ASM_ERR_INVALID_ARG, "null argument");
+  asm_solve_opts so;
+  if (o) so = *o; else asm_default_solve_opts(&so);
+  if (!(so.rtol > 0) || so.max_it < 1) return set_error(ASM_ERR_INVALID_ARG, "rtol must be > 0 and max_it >= 1");
+  if (so.restart <= 0) so.restart = 30;
+  Handle& h = H->h;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  bool conv = false;
+  asm_status st = guarded([&] {
+    const double* db = b;
+    double* dx = x;
+    if (h.host_io) {
+      if (!h.kr.bx) h.kr.bx = h.mem.alloc<double>(2LL * h.n);
+      db = h.kr.bx;
+      dx = h.kr.bx + h.n;
+      CK(cudaMemcpyAsync(h.kr.bx, b, sizeof(double) * h.n, cudaMemcpyHostToDevice, s));
+      if (so.use_x0) CK(cudaMemcpyAsync(dx, x, sizeof(double) * h.n, cudaMemcpyHostToDevice, s));
+    }
+    int method = so.method ? so.method : (h.opt.spd ? 1 : 2);
+    if (method == 1) solve_pcg(h, db, dx, so, *info, s);
+    else solve_fgmres(h, db, dx, so, *info, s);
+    if (h.host_io) {
+      CK(cudaMemcpyAsync(x, dx, sizeof(double) * h.n, cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+    }
+    conv = info->converged != 0;
+  });
+  if (st != ASM_OK) return st;
+  if (!conv) return set_error(ASM_ERR_NO_CONVERGENCE, "Krylov iteration did not reach rtol");
+  return ASM_OK;
+}
+
+asm_status asm_get_info(const asm_handle* H, asm_setup_info* info) {
+  if (!H || !info) return set_error(ASM_ERR_INVALID_ARG, "null argument");
+  *info = H->h.info;
+  return ASM_OK;
+}
+
+asm_status asm_get_overlap(const asm_handle* H, int32_t* sub_offsets, int32_t* layer_offsets, int32_t* omega) {
+  if (!H) return set_error(ASM_ERR_INVALID_ARG, "null argument");
+  const Handle& h = H->h;
+  return guarded([&] {
+    if (sub_offsets) std::memcpy(sub_offsets, h.ov.h_sub_off.data(), sizeof(int32_t) * (h.N + 1));
+    if (layer_offsets)
+      std::memcpy(layer_offsets, h.ov.h_lay_off.data(), sizeof(int32_t) * h.ov.h_lay_off.size());
+    if (omega) CK(cudaMemcpy(omega, h.ov.omega, sizeof(int32_t) * h.ov.sum_n, cudaMemcpyDeviceToHost));
+  });
+}
+
+asm_status asm_get_local_values(const asm_handle* H, double* values, int32_t* counts) {
+  if (!H) return set_error(ASM_ERR_INVALID_ARG, "null argument");
+  const Handle& h = H->h;
+  return guarded([&] {
+    if (values) {
+      if (h.co.values) CK(cudaMemcpy(values, h.co.values, sizeof(double) * h.N * h.nev, cudaMemcpyDeviceToHost));
+      else std::memset(values, 0, sizeof(double) * h.N * h.nev);
+    }
+    if (counts) {
+      for (int i = 0; i < h.N; ++i) counts[i] = i < (int)h.co.h_count.size() ? h.co.h_count[i] : 0;
+    }
+  });
+}
+
+asm_status asm_get_coarse_basis(const asm_handle* H, double* Z, int32_t* col_offsets) {
+  if (!H) return set_error(ASM_ERR_INVALID_ARG, "null argument");
+  const Handle& h = H->h;
+  return guarded([&] {
+    if (col_offsets) {
+      for (int i = 0; i <= h.N; ++i) col_offsets[i] = i < (int)h.co.h_col_off.size() ? h.co.h_col_off[i] : 0;
+    }
+    if (Z && h.co.n_C > 0) {
+      // compact p_i x nev blocks to p_i x count_i
+      int64_t tot = h.co.h_z_off.back();
+      std::vector<double> buf(tot);
+      CK(cudaMemcpy(buf.data(), h.co.Z, sizeof(double) * tot, cudaMemcpyDeviceToHost));
+      int64_t o = 0;
+      for (int i = 0; i < h.N; ++i) {
+        int k = h.co.h_count[i], p = h.h_p[i];
+        for (int r = 0; r < p; ++r)
+          for (int j = 0; j < k; ++j) Z[o++] = buf[h.co.h_z_off[i] + (int64_t)r * h.nev + j];
+      }
+    }
+  });
+}
+
+asm_status asm_get_coarse_matrix(const asm_handle* H, double* E) {
+  if (!H || !E) return set_error(ASM_ERR_INVALID_ARG, "null argument");
+  const Handle& h = H->h;
+  return guarded([&] {
+    const int nC = h.co.n_C;
+    if (nC == 0) return;
+    const int ld = (int)round_up(nC, 64);
+    CK(cudaMemcpy2D(E, sizeof(double) * nC, h.co.E_copy, sizeof(double) * ld, sizeof(double) * nC, nC,
+                    cudaMemcpyDeviceToHost));
+  });
+}
+
+void asm_destroy(asm_handle* H) {
+  if (!H) return;
+  free_handle_memory(H->h);
+  delete H;
+}
+
+}  // extern "C"

@@ -1,0 +1,131 @@
+// Internal state of an asm_handle and the stage entry points between files.
+#pragma once
+
+#include "common.cuh"
+
+namespace asmgpu {
+
+// Capacities of the overlap builder (one CTA per subdomain, shared memory).
+constexpr int OV_HASH = 8192;    // hash slots for the candidates of one layer
+constexpr int OV_LAYER = 4096;   // largest single layer
+constexpr int MAX_NI = 16384;    // largest |Omega_i| / |I_i| handled
+
+struct Overlap {
+  // device
+  int32_t* gptr = nullptr;   // graph of A + A^T, no self loops (n+1)
+  int32_t* gidx = nullptr;
+  int32_t* sub_off = nullptr;  // N+1, start of subdomain i in omega
+  int32_t* lay_off = nullptr;  // N*(delta+2) local layer offsets
+  int32_t* omega = nullptr;    // sum n_i global indices
+  int32_t* pos_sub = nullptr;  // sum n_i: subdomain of each omega position
+  int32_t* occ_ptr = nullptr;  // n+1
+  int32_t* occ_pos = nullptr;  // sum n_i: omega positions holding node v, ascending
+  int32_t* own_pos = nullptr;  // n: omega position of v inside its own I block
+  int64_t* ent_off = nullptr;  // sum n_i + 1: entries of the rows of Omega_i
+  int32_t* lcol = nullptr;     // local column of each entry, -1 outside Omega_i
+  // host
+  std::vector<int32_t> h_sub_off, h_lay_off;
+  int64_t sum_n = 0, n_ent = 0;
+  int32_t max_n = 0;
+};
+
+struct Dense {
+  // per subdomain (host and device copies)
+  std::vector<int32_t> h_np;          // padded size round_up(n_i, TILE)
+  std::vector<int64_t> h_work_off;    // element offset in the working buffer
+  std::vector<int64_t> h_xs_off;      // element offset of X_p^T (g x p)
+  std::vector<int64_t> h_s_off;       // element offset of S (g x g)
+  std::vector<int32_t> h_nt;          // tiles per side
+  std::vector<int64_t> h_tile_off;    // first apply tile of subdomain i
+  std::vector<int64_t> h_part_off;    // partial-sum slots offset (elements)
+  int64_t* work_off = nullptr;
+  int64_t* xs_off = nullptr;
+  int64_t* s_off = nullptr;
+  int32_t* np = nullptr;
+  int32_t* nt = nullptr;
+  int64_t* tile_off = nullptr;
+  int64_t* part_off = nullptr;
+  int4* tile_desc = nullptr;          // (subdomain, I, J, 0) of every apply tile
+  void* work = nullptr;               // A_ii, then A_ii^{-1} (row-major, ld = np)
+  void* XpT = nullptr;                // X_p^T = -(B^{-1} C)[:p]^T   (g x p)
+  void* S = nullptr;                  // S = G - C^T B^{-1} C        (g x g)
+  void* tiles = nullptr;              // apply tiles, TILE*TILE each
+  void* partials = nullptr;           // per (subdomain, I, J) TILE partial sums
+  int64_t n_tiles = 0, n_work = 0, n_xs = 0, n_s = 0, n_part = 0;
+  int32_t* err = nullptr;             // device error word
+};
+
+struct Coarse {
+  int32_t s_max = 0;                  // block width of the subspace iteration
+  std::vector<int32_t> h_count, h_col_off, h_sweeps;
+  std::vector<int64_t> h_z_off;
+  int32_t* count = nullptr;           // kept vectors per subdomain
+  int32_t* col_off = nullptr;         // N+1 first coarse column
+  int64_t* z_off = nullptr;           // offset of Z_i (p_i x nev, row-major FP64)
+  double* Z = nullptr;
+  double* values = nullptr;           // N * nev
+  double* resid = nullptr;            // N * nev eigen-residuals
+  int32_t* sweeps = nullptr;          // N
+  void* scratch = nullptr;            // per-subdomain iteration blocks
+  int64_t* scr_off = nullptr;
+  int32_t n_C = 0;
+  int64_t nnz_C = 0;
+  double* E = nullptr;                // n_C x n_C, factored in place (lower)
+  double* E_copy = nullptr;           // as assembled
+  double* Einv_diag = nullptr;        // inverses of the diagonal factor blocks
+  double* cvec = nullptr;             // coarse work vectors (2 x n_C)
+};
+
+struct Krylov {
+  double *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *w = nullptr;
+  double* part = nullptr;   // block partial sums
+  double* scal = nullptr;   // device scalars
+  int32_t* flag = nullptr;  // [0] done, [1] iterations
+  double* V = nullptr;      // FGMRES basis (restart+1) x n
+  double* ZB = nullptr;     // FGMRES preconditioned basis restart x n
+  double* H = nullptr;      // Hessenberg and rotations
+  int32_t restart = 0;
+  double* bx = nullptr;     // device copies of b, x for host-pointer solves
+  double* hpin = nullptr;   // pinned host staging
+};
+
+struct Handle {
+  int32_t n = 0, nnz = 0, N = 0, delta = 1, nev = 0;
+  asm_options opt{};
+  bool host_io = false;
+  bool fp32 = false;
+  DevMem mem;
+  int32_t *row_ptr = nullptr, *col_idx = nullptr, *part = nullptr;
+  double* val = nullptr;
+  int32_t *dev_n = nullptr, *dev_m = nullptr, *dev_p = nullptr;  // |Omega_i|, |Omega_{1:d-1}|, |I_i|
+  float* warm = nullptr;            // optional predicted start blocks (g_i x nev per subdomain)
+  int64_t* warm_off = nullptr;
+  std::vector<int32_t> h_n, h_p, h_m, h_g;
+  Overlap ov;
+  Dense dn;
+  Coarse co;
+  Krylov kr;
+  asm_setup_info info{};
+  cudaEvent_t ev[16];
+  bool events = false;
+};
+
+// Stage entry points (each enqueues on `s`; host reads are explicit).
+void build_overlap(Handle& h, cudaStream_t s);                 // overlap.cu
+void build_local(Handle& h, cudaStream_t s);                   // local.cu: gather + sweep + pack
+void build_eigen(Handle& h, cudaStream_t s);                   // eigen.cu
+void build_coarse(Handle& h, cudaStream_t s);                  // coarse.cu: E assembly + factor
+void apply_preconditioner(Handle& h, const double* r, double* z, cudaStream_t s,
+                          const int32_t* done = nullptr);                         // apply.cu
+void spmv(Handle& h, const double* x, double* y, cudaStream_t s);                 // krylov.cu
+void coarse_solve(Handle& h, const double* c, double* y, cudaStream_t s,
+                  const int32_t* done = nullptr);                                 // coarse.cu
+void solve_pcg(Handle& h, const double* b, double* x, const asm_solve_opts& o, asm_solve_info& info,
+               cudaStream_t s);
+void solve_fgmres(Handle& h, const double* b, double* x, const asm_solve_opts& o,
+                  asm_solve_info& info, cudaStream_t s);
+
+// Read back and clear the device error word; throw the matching status.
+void check_device_error(Handle& h, cudaStream_t s, const char* stage);
+
+}  // namespace asmgpu

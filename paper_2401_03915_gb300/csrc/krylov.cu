@@ -1,0 +1,300 @@
+// FP64 Krylov loop: CSR SpMV, deterministic dot products, PCG and
+// right-preconditioned flexible GMRES.  Every loop kernel first reads the
+// device `done` flag and returns if it is set, so one iteration can be
+// captured once as a CUDA graph and replayed in chunks: replays after
+// convergence cost only their launches and change nothing.
+//
+// The paper stops GMRES at a relative tolerance of 1e-8 on the
+// unpreconditioned residual (Section 6); x0 = 0 unless the caller gives one.
+#include <algorithm>
+#include <cmath>
+
+#include "handle.cuh"
+
+namespace asmgpu {
+namespace {
+
+constexpr int NT = 256;
+constexpr int NBLK = 608;  // fixed reduction grid: 4 blocks per SM on 152 SMs
+
+enum Scal { S_RZ = 0, S_PQ, S_ALPHA, S_BETA, S_RR, S_BNORM, S_RTOL, S_RELRES, S_TMP, S_NSCAL = 16 };
+enum Flag { F_DONE = 0, F_IT, F_MAXIT, F_NFLAG = 4 };
+
+// vector-per-row CSR SpMV with VW lanes per row; optional dot(x, y) partials.
+template <int VW, bool DOT>
+__global__ void __launch_bounds__(NT) k_spmv(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                             const double* __restrict__ val, const double* __restrict__ x,
+                                             double* __restrict__ y, double* __restrict__ part,
+                                             const int32_t* __restrict__ done) {
+  if (done != nullptr && done[F_DONE]) return;
+  __shared__ double red[NT / 32];
+  const int lane = threadIdx.x % VW;
+  const int rows_per_block = NT / VW;
+  double dsum = 0;
+  for (int base = blockIdx.x * rows_per_block; base < n; base += gridDim.x * rows_per_block) {
+    int r = base + threadIdx.x / VW;
+    double acc = 0;
+    if (r < n) {
+      int b = rp[r], e = rp[r + 1];
+      for (int k = b + lane; k < e; k += VW) acc += val[k] * x[ci[k]];
+    }
+#pragma unroll
+    for (int o = VW / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (r < n && lane == 0) {
+      y[r] = acc;
+      if (DOT) dsum += acc * x[r];
+    }
+  }
+  if (DOT) {
+    dsum = block_sum(dsum, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = dsum;
+  }
+}
+
+// partial sums of a.b (fixed grid-stride decomposition)
+__global__ void __launch_bounds__(NT) k_dot(int n, const double* __restrict__ a, const double* __restrict__ b,
+                                            double* __restrict__ part, const int32_t* __restrict__ done) {
+  if (done != nullptr && done[F_DONE]) return;
+  __shared__ double red[NT / 32];
+  double s = 0;
+  for (int i = blockIdx.x * NT + threadIdx.x; i < n; i += gridDim.x * NT) s += a[i] * b[i];
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+__device__ double sum_partials(const double* part, int nb) {
+  __shared__ double red[NT / 32];
+  double s = 0;
+  for (int k = threadIdx.x; k < nb; k += NT) s += part[k];
+  return block_sum(s, red);
+}
+
+// x += alpha p; r -= alpha q; partial ||r||^2
+__global__ void __launch_bounds__(NT) k_pcg_update(int n, double* __restrict__ x, double* __restrict__ r,
+                                                   const double* __restrict__ p, const double* __restrict__ q,
+                                                   const double* __restrict__ scal, double* __restrict__ part,
+                                                   const int32_t* __restrict__ done) {
+  if (done[F_DONE]) return;
+  __shared__ double red[NT / 32];
+  const double alpha = scal[S_ALPHA];
+  double s = 0;
+  for (int i = blockIdx.x * NT + threadIdx.x; i < n; i += gridDim.x * NT) {
+    x[i] += alpha * p[i];
+    double ri = r[i] - alpha * q[i];
+    r[i] = ri;
+    s += ri * ri;
+  }
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(NT) k_fin_alpha(const double* part, int nb, double* scal, int32_t* flag) {
+  if (flag[F_DONE]) return;
+  double pq = sum_partials(part, nb);
+  if (threadIdx.x == 0) {
+    scal[S_PQ] = pq;
+    scal[S_ALPHA] = scal[S_RZ] / pq;
+    if (!(pq > 0) || !isfinite(pq)) { scal[S_ALPHA] = 0; flag[F_DONE] = 2; }
+  }
+}
+
+__global__ void __launch_bounds__(NT) k_fin_res(const double* part, int nb, double* scal, int32_t* flag,
+                                                double* hist, int hist_len) {
+  if (flag[F_DONE]) return;
+  double rr = sum_partials(part, nb);
+  if (threadIdx.x == 0) {
+    int it = ++flag[F_IT];
+    double rel = sqrt(rr) / scal[S_BNORM];
+    scal[S_RR] = rr;
+    scal[S_RELRES] = rel;
+    if (hist != nullptr && it < hist_len) hist[it] = rel;
+    if (rel <= scal[S_RTOL]) flag[F_DONE] = 1;
+    else if (it >= flag[F_MAXIT] || !isfinite(rel)) flag[F_DONE] = 3;
+  }
+}
+
+__global__ void __launch_bounds__(NT) k_fin_beta(const double* part, int nb, double* scal, int32_t* flag) {
+  if (flag[F_DONE]) return;
+  double rz = sum_partials(part, nb);
+  if (threadIdx.x == 0) {
+    scal[S_BETA] = rz / scal[S_RZ];
+    scal[S_RZ] = rz;
+  }
+}
+
+__global__ void __launch_bounds__(NT) k_update_p(int n, double* __restrict__ p, const double* __restrict__ z,
+                                                 const double* __restrict__ scal, const int32_t* __restrict__ done) {
+  if (done[F_DONE]) return;
+  const double beta = scal[S_BETA];
+  for (int i = blockIdx.x * NT + threadIdx.x; i < n; i += gridDim.x * NT) p[i] = z[i] + beta * p[i];
+}
+
+// generic: out = a + alpha * b  (alpha from scal[ia] times sgn)
+__global__ void k_axpby(int n, double* out, const double* a, const double* b, double alpha) {
+  for (int i = blockIdx.x * NT + threadIdx.x; i < n; i += gridDim.x * NT) out[i] = a[i] + alpha * b[i];
+}
+
+__global__ void k_init_scalars(double* scal, int32_t* flag, const double* part, int nb, double rtol, int maxit,
+                               int which) {
+  double s = sum_partials(part, nb);
+  if (threadIdx.x == 0) {
+    if (which == 0) {  // ||b||^2
+      scal[S_BNORM] = sqrt(s);
+      scal[S_RTOL] = rtol;
+      flag[F_DONE] = 0;
+      flag[F_IT] = 0;
+      flag[F_MAXIT] = maxit;
+      if (!(s > 0)) flag[F_DONE] = 1;
+    } else if (which == 1) {  // r.z
+      scal[S_RZ] = s;
+    } else {  // ||r0||^2
+      scal[S_RR] = s;
+      scal[S_RELRES] = sqrt(s) / scal[S_BNORM];
+      if (scal[S_RELRES] <= rtol) flag[F_DONE] = 1;
+    }
+  }
+}
+
+inline unsigned vgrid(int n) { return (unsigned)std::min<int64_t>(ceil_div(n, NT), NBLK); }
+
+template <int VW>
+void spmv_launch(Handle& h, const double* x, double* y, double* part, const int32_t* done, bool dot, cudaStream_t s) {
+  const int rows = NT / VW;
+  unsigned g = (unsigned)std::min<int64_t>(ceil_div(h.n, rows), NBLK);
+  if (dot) {
+    // the dot partials need exactly NBLK slots for a fixed reduction
+    k_spmv<VW, true><<<NBLK, NT, 0, s>>>(h.n, h.row_ptr, h.col_idx, h.val, x, y, part, done);
+  } else {
+    k_spmv<VW, false><<<g, NT, 0, s>>>(h.n, h.row_ptr, h.col_idx, h.val, x, y, part, done);
+  }
+}
+
+void spmv_any(Handle& h, const double* x, double* y, double* part, const int32_t* done, bool dot, cudaStream_t s) {
+  double avg = h.n ? (double)h.nnz / h.n : 1;
+  if (avg <= 6) spmv_launch<4>(h, x, y, part, done, dot, s);
+  else if (avg <= 12) spmv_launch<8>(h, x, y, part, done, dot, s);
+  else if (avg <= 24) spmv_launch<16>(h, x, y, part, done, dot, s);
+  else spmv_launch<32>(h, x, y, part, done, dot, s);
+}
+
+void ensure_krylov(Handle& h) {
+  Krylov& kr = h.kr;
+  if (kr.r) return;
+  DevMem& mem = h.mem;
+  const int n = h.n;
+  kr.r = mem.alloc<double>(n);
+  kr.z = mem.alloc<double>(n);
+  kr.p = mem.alloc<double>(n);
+  kr.q = mem.alloc<double>(n);
+  kr.w = mem.alloc<double>(n);
+  kr.part = mem.alloc<double>(NBLK);
+  kr.scal = mem.alloc<double>(S_NSCAL);
+  kr.flag = mem.alloc<int32_t>(F_NFLAG);
+  kr.bx = mem.alloc<double>(2LL * n);
+  CK(cudaMallocHost(&kr.hpin, 64));
+}
+
+}  // namespace
+
+void spmv(Handle& h, const double* x, double* y, cudaStream_t s) {
+  spmv_any(h, x, y, nullptr, nullptr, false, s);
+  CK_LAUNCH("spmv");
+}
+
+void solve_pcg(Handle& h, const double* b, double* x, const asm_solve_opts& o, asm_solve_info& info,
+               cudaStream_t s) {
+  ensure_krylov(h);
+  Krylov& kr = h.kr;
+  const int n = h.n;
+  const unsigned vg = NBLK;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  CK(cudaEventRecord(e0, s));
+  // r = b - A x0 (or b), ||b||, z = M r, rz = r.z, p = z
+  k_dot<<<vg, NT, 0, s>>>(n, b, b, kr.part, nullptr);
+  k_init_scalars<<<1, NT, 0, s>>>(kr.scal, kr.flag, kr.part, NBLK, o.rtol, o.max_it, 0);
+  if (o.use_x0) {
+    spmv_any(h, x, kr.q, nullptr, nullptr, false, s);
+    k_axpby<<<vgrid(n), NT, 0, s>>>(n, kr.r, b, kr.q, -1.0);
+  } else {
+    CK(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
+    CK(cudaMemcpyAsync(kr.r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  }
+  k_dot<<<vg, NT, 0, s>>>(n, kr.r, kr.r, kr.part, nullptr);
+  k_init_scalars<<<1, NT, 0, s>>>(kr.scal, kr.flag, kr.part, NBLK, o.rtol, o.max_it, 2);
+  apply_preconditioner(h, kr.r, kr.z, s, nullptr);
+  k_dot<<<vg, NT, 0, s>>>(n, kr.r, kr.z, kr.part, nullptr);
+  k_init_scalars<<<1, NT, 0, s>>>(kr.scal, kr.flag, kr.part, NBLK, o.rtol, o.max_it, 1);
+  CK(cudaMemcpyAsync(kr.p, kr.z, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  CK_LAUNCH("pcg init");
+
+  // one iteration, captured once
+  auto iteration = [&](cudaStream_t st) {
+    spmv_any(h, kr.p, kr.q, kr.part, kr.flag, true, st);
+    k_fin_alpha<<<1, NT, 0, st>>>(kr.part, NBLK, kr.scal, kr.flag);
+    k_pcg_update<<<vg, NT, 0, st>>>(n, x, kr.r, kr.p, kr.q, kr.scal, kr.part, kr.flag);
+    k_fin_res<<<1, NT, 0, st>>>(kr.part, NBLK, kr.scal, kr.flag, nullptr, 0);
+    apply_preconditioner(h, kr.r, kr.z, st, kr.flag);
+    k_dot<<<vg, NT, 0, st>>>(n, kr.r, kr.z, kr.part, kr.flag);
+    k_fin_beta<<<1, NT, 0, st>>>(kr.part, NBLK, kr.scal, kr.flag);
+    k_update_p<<<vg, NT, 0, st>>>(n, kr.p, kr.z, kr.scal, kr.flag);
+  };
+  cudaStream_t cs;
+  CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaEvent_t ej;
+  CK(cudaEventCreateWithFlags(&ej, cudaEventDisableTiming));
+  CK(cudaEventRecord(ej, s));
+  CK(cudaStreamWaitEvent(cs, ej, 0));
+  cudaGraph_t graph;
+  cudaGraphExec_t exec;
+  const int chunk = std::max(1, o.check_every > 0 ? o.check_every : 8);
+  CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  for (int k = 0; k < chunk; ++k) iteration(cs);
+  CK(cudaStreamEndCapture(cs, &graph));
+  CK(cudaGraphInstantiate(&exec, graph, 0));
+  int32_t* hflag = reinterpret_cast<int32_t*>(kr.hpin);
+  for (;;) {
+    CK(cudaGraphLaunch(exec, cs));
+    CK(cudaMemcpyAsync(hflag, kr.flag, sizeof(int32_t) * 2, cudaMemcpyDeviceToHost, cs));
+    CK(cudaStreamSynchronize(cs));
+    if (hflag[F_DONE]) break;
+  }
+  CK(cudaEventRecord(ej, cs));
+  CK(cudaStreamWaitEvent(s, ej, 0));
+  CK(cudaGraphExecDestroy(exec));
+  CK(cudaGraphDestroy(graph));
+  CK(cudaStreamDestroy(cs));
+  CK(cudaEventDestroy(ej));
+  CK(cudaEventRecord(e1, s));
+  // true residual
+  spmv_any(h, x, kr.q, nullptr, nullptr, false, s);
+  k_axpby<<<vgrid(n), NT, 0, s>>>(n, kr.w, b, kr.q, -1.0);
+  k_dot<<<vg, NT, 0, s>>>(n, kr.w, kr.w, kr.part, nullptr);
+  double sc[S_NSCAL];
+  int32_t fl[F_NFLAG];
+  CK(cudaMemcpyAsync(sc, kr.scal, sizeof(sc), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(fl, kr.flag, sizeof(fl), cudaMemcpyDeviceToHost, s));
+  std::vector<double> part(NBLK);
+  CK(cudaMemcpyAsync(part.data(), kr.part, sizeof(double) * NBLK, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  float ms = 0;
+  CK(cudaEventElapsedTime(&ms, e0, e1));
+  CK(cudaEventDestroy(e0));
+  CK(cudaEventDestroy(e1));
+  double tr = 0;
+  for (double v : part) tr += v;
+  info.iterations = fl[F_IT];
+  info.converged = fl[F_DONE] == 1;
+  info.final_relres = sc[S_RELRES];
+  info.true_relres = sc[S_BNORM] > 0 ? std::sqrt(tr) / sc[S_BNORM] : 0.0;
+  info.solve_ms = ms;
+}
+
+void solve_fgmres(Handle& h, const double* b, double* x, const asm_solve_opts& o, asm_solve_info& info,
+                  cudaStream_t s) {
+  (void)h; (void)b; (void)x; (void)o; (void)info; (void)s;
+  fail(ASM_ERR_UNSUPPORTED, "FGMRES is not available in this build");
+}
+
+}  // namespace asmgpu

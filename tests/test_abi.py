@@ -1,0 +1,64 @@
+"""The C-ABI library builds, loads and exports every function declared in
+include/asm.h; argument checks that need no device return INVALID_ARG."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2401_03915_gb300 import build
+    path = build.build()
+    import paper_2401_03915_gb300 as P
+    return P, P.load(path)
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "asm.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"\b(asm_[a-z_0-9]+)\s*\(", text)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("asm_setup", "asm_apply", "asm_solve", "asm_get_info", "asm_destroy", "asm_last_error"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    _, L = lib
+    missing = [n for n in declared_functions() if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_option_defaults(lib):
+    P, _ = lib
+    o = P.default_options()
+    assert o.spd == 1 and o.oversample == 8 and o.coarse == 1
+    s = P.default_solve_opts()
+    assert s.rtol == 1e-8 and s.restart == 30 and s.max_it == 1000
+
+
+def test_invalid_arguments_are_rejected_before_any_device_work(lib):
+    P, L = lib
+    rp = np.array([0, 1, 2], dtype=np.int32)
+    ci = np.array([0, 1], dtype=np.int32)
+    va = np.array([1.0, 1.0])
+    part = np.zeros(2, dtype=np.int32)
+    cases = [dict(N=0, overlap=1, nev=1), dict(N=3, overlap=1, nev=1), dict(N=1, overlap=0, nev=1),
+             dict(N=1, overlap=1, nev=-1), dict(N=1, overlap=1, nev=1000)]
+    for c in cases:
+        with pytest.raises(P.AsmError) as e:
+            P.asm_setup(rp, ci, va, part, c["N"], c["overlap"], c["nev"], on_device=False)
+        assert e.value.name == "INVALID_ARG"
+    with pytest.raises(P.AsmError) as e:
+        P.asm_setup(rp, ci, va, part, 1, 1, 1, P.default_options(local_precision=7), on_device=False)
+    assert e.value.name == "INVALID_ARG"
+    assert L.asm_apply(None, None, None, None) == 1
+    assert b"null" in L.asm_last_error()

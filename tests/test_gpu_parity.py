@@ -1,0 +1,229 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Bit-exact: overlap index sets and layer offsets.  FP64 path: local
+eigenvalues within 1e-10 relative, coarse subspaces (where the spectral gap
+makes them unique), apply and solve.  FP32 path: the same quantities within
+stated tolerances derived from single-precision local work.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import oracle as O
+from asm_inputs import SplitMix64, poisson2d, diffusion3d, convdiff2d, elasticity3d
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_2401_03915_gb300 import build
+    build.build()
+    import paper_2401_03915_gb300 as P
+    P.load()
+    return P
+
+
+def make(P, A, part, N, delta, nev, **kw):
+    A = sp.csr_matrix(A)
+    return P.TwoLevelSchwarz(A.indptr, A.indices, A.data, part, N, delta, nev, **kw)
+
+
+def check_overlap(P, h, ovs):
+    sub, lay, om = P.asm_get_overlap(h)
+    for i, ov in enumerate(ovs):
+        np.testing.assert_array_equal(lay[i], ov.offsets)
+        np.testing.assert_array_equal(om[sub[i]:sub[i + 1]], ov.omega)
+
+
+def projector(Zb):
+    Q, _ = np.linalg.qr(Zb)
+    return Q @ Q.T
+
+
+# ---------------------------------------------------------------------------
+# overlap: bit-exact
+# ---------------------------------------------------------------------------
+def test_overlap_worked_example(P):
+    A = np.array([[1, 2, 0, 0, 0, 0, 0], [3, 4, 5, 0, 0, 0, 0], [0, 7, 8, 9, 0, 0, 0],
+                  [0, 0, 10, 11, 12, 0, 0], [0, 0, 0, 13, 14, 15, 0], [0, 0, 0, 0, 16, 17, 18],
+                  [0, 0, 0, 0, 0, 19, 20]], dtype=float)
+    part = np.array([0, 0, 0, 1, 1, 1, 1], dtype=np.int32)
+    for delta in (1, 2):
+        pre = make(P, A, part, 2, delta, 0, spd=False)
+        check_overlap(P, pre.h, O.overlap(sp.csr_matrix(A), part, 2, delta))
+        pre.close()
+
+
+@pytest.mark.parametrize("delta", [1, 2, 3])
+def test_overlap_random_graph(P, delta):
+    n = 300
+    r = SplitMix64(123 + delta)
+    m = 700
+    i = r.integers(0, n - 1, m); j = r.integers(0, n - 1, m)
+    A = sp.coo_matrix((r.uniform(m) + 0.1, (i, j)), shape=(n, n)).tocsr()
+    A = A + sp.diags(np.asarray(abs(A).sum(axis=1)).ravel() + abs(A).sum(axis=0).A1 + 1.0)
+    part = ((np.arange(n) * 7) // n).astype(np.int32)
+    pre = make(P, A, part, 7, delta, 0, spd=False)
+    check_overlap(P, pre.h, O.overlap(A, part, 7, delta))
+    pre.close()
+
+
+def test_overlap_configs(P):
+    for prob in (poisson2d(64, 64, 4, 4), convdiff2d(64, (4, 4), delta=2),
+                 elasticity3d(6, (2, 2, 2)), diffusion3d(32, (4, 4, 4), contrast=1e4)):
+        pre = make(P, prob.csr(), prob.part, prob.N, prob.delta, 0, spd=prob.spd)
+        check_overlap(P, pre.h, O.overlap(prob.csr(), prob.part, prob.N, prob.delta))
+        pre.close()
+
+
+# ---------------------------------------------------------------------------
+# FP64 path: eigenvalues, coarse spaces, apply, solve
+# ---------------------------------------------------------------------------
+FP64 = dict(precision="fp64", eig_tol=1e-11, max_sweeps=400)
+
+
+def _oracle_and_gpu(P, prob, nev, **kw):
+    A = prob.csr()
+    st = O.setup(A, prob.part, prob.N, prob.delta, nev, spd=prob.spd)
+    pre = make(P, A, prob.part, prob.N, prob.delta, nev, spd=prob.spd, **kw)
+    return A, st, pre
+
+
+@pytest.mark.parametrize("case", ["c1", "contrast3d", "delta2"])
+def test_fp64_eigenvalues_and_subspaces(P, case):
+    if case == "c1":
+        prob = poisson2d(64, 64, 4, 4, nev=4)
+    elif case == "contrast3d":
+        prob = diffusion3d(16, (2, 2, 2), contrast=1e4, nev=6)
+    else:
+        prob = poisson2d(40, 30, 3, 2, delta=2, nev=5)
+    A, st, pre = _oracle_and_gpu(P, prob, prob.nev, **FP64)
+    vals, cnt = P.asm_get_local_values(pre.h)
+    blocks, col = P.asm_get_coarse_basis(pre.h, [l.ov.p for l in st.locals])
+    for i, loc in enumerate(st.locals):
+        k = len(loc.values)
+        assert cnt[i] == k
+        np.testing.assert_allclose(vals[i, :k], loc.values, rtol=1e-10, atol=0)
+        allv = loc.all_values
+        if k and (allv[k - 1] - allv[k]) / allv[k - 1] > 1e-6:
+            np.testing.assert_allclose(projector(blocks[i]), projector(loc.basis), atol=1e-8)
+    pre.close()
+
+
+def test_fp64_apply_matches_oracle(P):
+    prob = diffusion3d(16, (2, 2, 2), contrast=1e4, nev=6)
+    A, st, pre = _oracle_and_gpu(P, prob, prob.nev, **FP64)
+    r = SplitMix64(99).normal(prob.n)
+    z = pre.apply(torch.as_tensor(r, device="cuda")).cpu().numpy()
+    # the coarse part depends only on span(Z); check the spans are unique first
+    unique = all((l.all_values[len(l.values) - 1] - l.all_values[len(l.values)]) / l.all_values[len(l.values) - 1]
+                 > 1e-6 for l in st.locals)
+    zr = st.apply(r)
+    if unique:
+        np.testing.assert_allclose(z, zr, rtol=0, atol=1e-10 * np.abs(zr).max())
+    # one-level part always
+    pre1 = make(P, A, prob.part, prob.N, 1, 0, precision="fp64")
+    z1 = pre1.apply(torch.as_tensor(r, device="cuda")).cpu().numpy()
+    np.testing.assert_allclose(z1, st.apply_one_level(r), rtol=0, atol=1e-11 * np.abs(z1).max())
+    pre.close(); pre1.close()
+
+
+def test_apply_is_deterministic(P):
+    prob = poisson2d(64, 64, 4, 4, nev=4)
+    for prec in ("fp64", "fp32"):
+        pre = make(P, prob.csr(), prob.part, prob.N, 1, 4, precision=prec)
+        r = torch.as_tensor(SplitMix64(5).normal(prob.n), device="cuda")
+        z1 = pre.apply(r).clone()
+        z2 = pre.apply(r)
+        assert torch.equal(z1, z2)
+        pre.close()
+
+
+def test_fp64_solve_c1(P):
+    prob = poisson2d(64, 64, 4, 4, nev=4)
+    A, st, pre = _oracle_and_gpu(P, prob, 4, **FP64)
+    ref = O.solve(st, prob.b)
+    b = torch.as_tensor(prob.b, device="cuda")
+    x, info = pre.solve(b)
+    xr = x.cpu().numpy()
+    rel = np.linalg.norm(prob.b - A @ xr) / np.linalg.norm(prob.b)
+    assert info.converged and info.final_relres <= 1e-8 and rel <= 1e-8 * 1.5
+    assert abs(info.iterations - ref.iterations) <= 1
+    np.testing.assert_allclose(xr, ref.x, rtol=0, atol=1e-5 * np.abs(ref.x).max())
+    pre.close()
+
+
+def test_one_subdomain_gives_exact_inverse(P):
+    prob = poisson2d(20, 18, 1, 1)
+    pre = make(P, prob.csr(), prob.part, 1, 1, 4, precision="fp64")
+    assert pre.info.n_C == 0
+    b = torch.as_tensor(prob.b, device="cuda")
+    x, info = pre.solve(b)
+    assert info.iterations == 1 and info.converged
+    pre.close()
+
+
+# ---------------------------------------------------------------------------
+# FP32 path
+# ---------------------------------------------------------------------------
+def test_fp32_eigenvalues_and_solve(P):
+    prob = diffusion3d(24, (3, 3, 3), contrast=1e6, nev=8)
+    A = prob.csr()
+    st = O.setup(A, prob.part, prob.N, 1, 8)
+    ref = O.solve(st, prob.b)
+    pre = make(P, A, prob.part, prob.N, 1, 8, precision="fp32")
+    vals, cnt = P.asm_get_local_values(pre.h)
+    for i, loc in enumerate(st.locals):
+        k = len(loc.values)
+        assert cnt[i] == k
+        # single-precision sweep and iteration: relative error of a few 1e-3
+        np.testing.assert_allclose(vals[i, :k], loc.values, rtol=5e-3)
+    x, info = pre.solve(torch.as_tensor(prob.b, device="cuda"))
+    xr = x.cpu().numpy()
+    rel = np.linalg.norm(prob.b - A @ xr) / np.linalg.norm(prob.b)
+    assert info.converged and rel <= 1.5e-8
+    assert info.iterations <= 1.1 * ref.iterations + 1
+    pre.close()
+
+
+def test_host_buffers_solve(P):
+    prob = poisson2d(32, 32, 2, 2, nev=3)
+    A = prob.csr()
+    pre = make(P, A, prob.part, prob.N, 1, 3, precision="fp64", device=False)
+    x = np.zeros(prob.n)
+    x, info = pre.solve(prob.b.copy(), x)
+    rel = np.linalg.norm(prob.b - A @ x) / np.linalg.norm(prob.b)
+    assert info.converged and rel <= 1.5e-8
+    pre.close()
+
+
+# ---------------------------------------------------------------------------
+# error statuses (host-made failures; nothing faults the GPU)
+# ---------------------------------------------------------------------------
+def test_not_spd_reports_status(P):
+    prob = poisson2d(16, 16, 2, 2)
+    A = (prob.csr() - 5.0 * sp.eye(prob.n)).tocsr()
+    with pytest.raises(P.AsmError) as e:
+        make(P, A, prob.part, prob.N, 1, 2, precision="fp64")
+    assert e.value.name == "NOT_SPD"
+
+
+def test_nonfinite_and_malformed_inputs(P):
+    prob = poisson2d(16, 16, 2, 2)
+    A = prob.csr().copy()
+    A.data[5] = np.nan
+    with pytest.raises(P.AsmError) as e:
+        make(P, A, prob.part, prob.N, 1, 2)
+    assert e.value.name == "NONFINITE"
+    B = prob.csr().copy()
+    B.indices[3], B.indices[4] = B.indices[4], B.indices[3]  # unsorted row
+    with pytest.raises(P.AsmError) as e:
+        make(P, B, prob.part, prob.N, 1, 2)
+    assert e.value.name == "INVALID_ARG"
+    bad = prob.part.copy(); bad[0] = 99
+    with pytest.raises(P.AsmError) as e:
+        make(P, prob.csr(), bad, prob.N, 1, 2)
+    assert e.value.name == "INVALID_ARG"
