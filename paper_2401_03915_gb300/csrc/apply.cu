@@ -1,7 +1,7 @@
 // Two-level additive Schwarz apply (Remark in Section 4.3):
 //     z = sum_i R_i^T A_ii^{-1} R_i r  +  Z E^{-1} Z^T r.
 //
-// Local part: A_ii^{-1} is stored as TILE x TILE tiles (lower tiles only when
+// Local part: A_ii^{-1} = D^{-1/2} A^_ii^{-1} D^{-1/2} with the scaled inverse stored as TILE x TILE tiles (lower tiles only when
 // A is SPD).  One flat, load-balanced pass over all tiles of all subdomains
 // reads every tile once; an off-diagonal tile T of a symmetric inverse
 // contributes T x_J to row block I and T^T x_I to row block J.  Each
@@ -41,7 +41,8 @@ __global__ void __launch_bounds__(NT) k_apply_tiles(const T* __restrict__ tiles,
                                                     const int32_t* __restrict__ sub_off,
                                                     const int32_t* __restrict__ n_arr, const int32_t* __restrict__ nt_arr,
                                                     const int64_t* __restrict__ part_off, const double* __restrict__ r,
-                                                    T* __restrict__ partials, const int32_t* __restrict__ done) {
+                                                    const double* __restrict__ ds, T* __restrict__ partials,
+                                                    const int32_t* __restrict__ done) {
   if (done != nullptr && *done) return;
   __shared__ T xI[TILE], xJ[TILE];
   __shared__ T colpart[NT / 32][TILE];
@@ -54,10 +55,12 @@ __global__ void __launch_bounds__(NT) k_apply_tiles(const T* __restrict__ tiles,
     __syncthreads();
     if (tid < TILE) {
       int a = I * TILE + tid;
-      xI[tid] = a < n ? (T)r[omega[b0 + a]] : T(0);
+      int v = a < n ? omega[b0 + a] : 0;
+      xI[tid] = a < n ? (T)(r[v] * ds[v]) : T(0);
     } else if (tid < 2 * TILE) {
       int a = J * TILE + tid - TILE;
-      xJ[tid - TILE] = a < n ? (T)r[omega[b0 + a]] : T(0);
+      int v = a < n ? omega[b0 + a] : 0;
+      xJ[tid - TILE] = a < n ? (T)(r[v] * ds[v]) : T(0);
     }
     __syncthreads();
     const T* tile = tiles + t * (TILE * TILE);
@@ -151,8 +154,8 @@ __global__ void __launch_bounds__(NT) k_apply_pull(int n, const int32_t* __restr
                                                    const int32_t* __restrict__ own_pos, const double* __restrict__ Z,
                                                    const int64_t* __restrict__ z_off, const int32_t* __restrict__ count,
                                                    const int32_t* __restrict__ col_off, int nev,
-                                                   const double* __restrict__ yc, double* __restrict__ z,
-                                                   const int32_t* __restrict__ done) {
+                                                   const double* __restrict__ yc, const double* __restrict__ ds,
+                                                   double* __restrict__ z, const int32_t* __restrict__ done) {
   if (done != nullptr && *done) return;
   for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
     double acc = 0;
@@ -166,6 +169,7 @@ __global__ void __launch_bounds__(NT) k_apply_pull(int n, const int32_t* __restr
       for (int J = 0; J < nt; ++J) s += (double)P[(int64_t)J * TILE];
       acc += s;
     }
+    acc *= ds[v];
     if (yc != nullptr) {
       int i = part[v];
       int k = count[i];
@@ -189,10 +193,10 @@ void apply_impl(Handle& h, const double* r, double* z, cudaStream_t s, const int
   unsigned gt = (unsigned)std::min<int64_t>(std::max<int64_t>(dn.n_tiles, 1), 152 * 8);
   if (sym)
     k_apply_tiles<T, true><<<gt, NT, 0, s>>>((const T*)dn.tiles, dn.tile_desc, dn.n_tiles, h.ov.omega,
-                                             h.ov.sub_off, h.dev_n, dn.nt, dn.part_off, r, (T*)dn.partials, done);
+                                             h.ov.sub_off, h.dev_n, dn.nt, dn.part_off, r, h.dscale, (T*)dn.partials, done);
   else
     k_apply_tiles<T, false><<<gt, NT, 0, s>>>((const T*)dn.tiles, dn.tile_desc, dn.n_tiles, h.ov.omega,
-                                              h.ov.sub_off, h.dev_n, dn.nt, dn.part_off, r, (T*)dn.partials, done);
+                                              h.ov.sub_off, h.dev_n, dn.nt, dn.part_off, r, h.dscale, (T*)dn.partials, done);
   const double* yc = nullptr;
   if (co.n_C > 0) {
     double* c = co.cvec;
@@ -205,7 +209,7 @@ void apply_impl(Handle& h, const double* r, double* z, cudaStream_t s, const int
   unsigned gp = (unsigned)std::min<int64_t>(ceil_div(h.n, NT), 152 * 16);
   k_apply_pull<T><<<gp, NT, 0, s>>>(h.n, h.ov.occ_ptr, h.ov.occ_pos, h.ov.pos_sub, h.ov.sub_off, dn.nt, dn.part_off,
                                     (const T*)dn.partials, h.part, h.ov.own_pos, co.Z, co.z_off, co.count,
-                                    co.col_off, h.nev, yc, z, done);
+                                    co.col_off, h.nev, yc, h.dscale, z, done);
 }
 
 }  // namespace

@@ -1,5 +1,5 @@
-// Coarse operator E = Z^T A Z (A_00 = R_0 A R_0^T, Section 4.1) and its FP64
-// factorisation / solve.
+// Coarse operator E = Z^T A Z (A_00 = R_0 A R_0^T, Section 4.1): assembly and
+// the subdomain graph of E for the nested-dissection factorisation.
 //
 // Z is block diagonal in the nonoverlapping partition: the block of
 // subdomain j is supported on Omega_{I_j} (the D_j in eq. coarse_space_2
@@ -17,7 +17,7 @@ namespace asmgpu {
 namespace {
 
 constexpr int NT = 256;
-constexpr int EB = 64;  // block size of the dense coarse factorisation
+constexpr int EB = 64;  // padding of the dense coarse matrix
 
 __device__ void bitonic_sort_keys(int32_t* sh, int len) {
   int sz = 1;
@@ -44,8 +44,10 @@ __global__ void __launch_bounds__(NT) k_assemble_E(
     const int32_t* __restrict__ omega, const int32_t* __restrict__ part, const int32_t* __restrict__ own_pos,
     const int32_t* __restrict__ rp, const double* __restrict__ val, const int64_t* __restrict__ ent_off,
     const int32_t* __restrict__ lcol, const int32_t* __restrict__ p_arr, const int32_t* __restrict__ n_arr,
-    int nev, double* __restrict__ AZ, const int64_t* __restrict__ az_off, unsigned long long* nnz) {
+    int nev, double* __restrict__ AZ, const int64_t* __restrict__ az_off, unsigned long long* nnz,
+    int2* __restrict__ pairs, unsigned int* __restrict__ npairs) {
   extern __shared__ int32_t keys[];
+  __shared__ int any_nz;
   const int j = blockIdx.x;
   const int kj = count[j];
   if (kj == 0) return;
@@ -76,6 +78,8 @@ __global__ void __launch_bounds__(NT) k_assemble_E(
     const int ki = count[owner];
     const double* Zi = Z + z_off[owner];
     const int ib0 = sub_off[owner];
+    if (threadIdx.x == 0) any_nz = 0;
+    __syncthreads();
     for (int idx = threadIdx.x; idx < ki * kj; idx += NT) {
       int r = idx / kj, c = idx % kj;
       double acc = 0;
@@ -85,157 +89,18 @@ __global__ void __launch_bounds__(NT) k_assemble_E(
         acc += Zi[(int64_t)ipos * nev + r] * V[(int64_t)a * kj + c];
       }
       E[(int64_t)(col_off[owner] + r) * ldE + col_off[j] + c] = acc;
+      if (acc != 0.0) any_nz = 1;
     }
-    if (threadIdx.x == 0 && ki > 0) atomicAdd(nnz, (unsigned long long)ki * kj);
+    __syncthreads();
+    if (threadIdx.x == 0 && ki > 0 && any_nz) {
+      atomicAdd(nnz, (unsigned long long)ki * kj);
+      pairs[atomicAdd(npairs, 1u)] = make_int2(owner, j);
+    }
     seg_start = seg_end;
     __syncthreads();
   }
 }
 
-__global__ void k_pad_identity(double* E, int ldE, int nC) {
-  for (int r = nC + blockIdx.x * blockDim.x + threadIdx.x; r < ldE; r += gridDim.x * blockDim.x)
-    E[(int64_t)r * ldE + r] = 1.0;
-}
-
-// Factor the diagonal block kb of E (all earlier updates applied) and store
-// its inverse factor L_kk^{-1} (lower) for the panel solve and for the apply.
-__global__ void __launch_bounds__(NT) k_potrf_diag(double* E, int ldE, int kb, double* Linv, int32_t* err) {
-  __shared__ double A[EB][EB + 1];
-  __shared__ double B[EB][EB + 1];
-  __shared__ int bad;
-  const int k0 = kb * EB;
-  for (int idx = threadIdx.x; idx < EB * EB; idx += NT) {
-    int r = idx / EB, c = idx % EB;
-    A[r][c] = E[(int64_t)(k0 + r) * ldE + k0 + c];
-  }
-  if (threadIdx.x == 0) bad = 0;
-  __syncthreads();
-  for (int j = 0; j < EB; ++j) {
-    if (threadIdx.x == 0) {
-      double d = A[j][j];
-      if (!(d > 0) || !isfinite(d)) { bad = 1; d = 1.0; }
-      A[j][j] = sqrt(d);
-    }
-    __syncthreads();
-    double dj = A[j][j];
-    for (int r = j + 1 + threadIdx.x; r < EB; r += NT) A[r][j] /= dj;
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < EB * EB; idx += NT) {
-      int r = idx / EB, c = idx % EB;
-      if (c > j && r >= c) A[r][c] -= A[r][j] * A[c][j];
-    }
-    __syncthreads();
-  }
-  // inverse of the lower factor, one column per thread
-  for (int c = threadIdx.x; c < EB; c += NT) {
-    for (int r = 0; r < EB; ++r) B[r][c] = 0;
-    for (int r = c; r < EB; ++r) {
-      double v = r == c ? 1.0 : 0.0;
-      for (int t = c; t < r; ++t) v -= A[r][t] * B[t][c];
-      B[r][c] = v / A[r][r];
-    }
-  }
-  __syncthreads();
-  for (int idx = threadIdx.x; idx < EB * EB; idx += NT) {
-    int r = idx / EB, c = idx % EB;
-    E[(int64_t)(k0 + r) * ldE + k0 + c] = c <= r ? A[r][c] : 0.0;
-    Linv[(int64_t)kb * EB * EB + idx] = B[r][c];
-  }
-  if (threadIdx.x == 0 && bad) atomicOr(err, DERR_COARSE);
-}
-
-// L_ik = E_ik L_kk^{-T} for block rows i > kb.
-__global__ void __launch_bounds__(NT) k_trsm_panel(double* E, int ldE, int kb, int nb, const double* Linv) {
-  __shared__ double Li[EB][EB + 1];
-  __shared__ double X[EB][EB + 1];
-  const int i = kb + 1 + blockIdx.x;
-  if (i >= nb) return;
-  const int k0 = kb * EB, i0 = i * EB;
-  for (int idx = threadIdx.x; idx < EB * EB; idx += NT) {
-    int r = idx / EB, c = idx % EB;
-    Li[r][c] = Linv[(int64_t)kb * EB * EB + idx];
-    X[r][c] = E[(int64_t)(i0 + r) * ldE + k0 + c];
-  }
-  __syncthreads();
-  for (int idx = threadIdx.x; idx < EB * EB; idx += NT) {
-    int r = idx / EB, c = idx % EB;
-    double acc = 0;
-    for (int t = 0; t <= c; ++t) acc += X[r][t] * Li[c][t];
-    E[(int64_t)(i0 + r) * ldE + k0 + c] = acc;
-  }
-}
-
-// E_ij -= L_ik L_jk^T for kb < j <= i.
-__global__ void __launch_bounds__(NT) k_syrk_update(double* E, int ldE, int kb, int nb) {
-  __shared__ double Ai[EB][EB + 1];
-  __shared__ double Aj[EB][EB + 1];
-  const int m = nb - kb - 1;
-  int t = blockIdx.x;
-  // map t -> (ii, jj) with 0 <= jj <= ii < m
-  int ii = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
-  while ((ii + 1) * (ii + 2) / 2 <= t) ++ii;
-  while (ii * (ii + 1) / 2 > t) --ii;
-  int jj = t - ii * (ii + 1) / 2;
-  if (ii >= m) return;
-  const int i0 = (kb + 1 + ii) * EB, j0 = (kb + 1 + jj) * EB, k0 = kb * EB;
-  for (int idx = threadIdx.x; idx < EB * EB; idx += NT) {
-    int r = idx / EB, c = idx % EB;
-    Ai[r][c] = E[(int64_t)(i0 + r) * ldE + k0 + c];
-    Aj[r][c] = E[(int64_t)(j0 + r) * ldE + k0 + c];
-  }
-  __syncthreads();
-  for (int idx = threadIdx.x; idx < EB * EB; idx += NT) {
-    int r = idx / EB, c = idx % EB;
-    double acc = 0;
-    for (int q = 0; q < EB; ++q) acc += Ai[r][q] * Aj[c][q];
-    E[(int64_t)(i0 + r) * ldE + j0 + c] -= acc;
-  }
-}
-
-// y = E^{-1} c with the blocked factor (one block: forward, then backward).
-__global__ void __launch_bounds__(NT) k_dense_solve(const double* __restrict__ L, int ldE, int nb,
-                                                    const double* __restrict__ Linv, const double* __restrict__ c,
-                                                    int nC, double* __restrict__ y, double* __restrict__ tmp,
-                                                    const int32_t* __restrict__ done) {
-  if (done != nullptr && *done) return;
-  __shared__ double rhs[EB];
-  __shared__ double red[NT / 32];
-  // forward: tmp = L^{-1} c
-  for (int k = 0; k < nb; ++k) {
-    const int k0 = k * EB;
-    for (int r = 0; r < EB; ++r) {
-      double part = 0;
-      for (int q = threadIdx.x; q < k0; q += NT) part += L[(int64_t)(k0 + r) * ldE + q] * tmp[q];
-      part = block_sum(part, red);
-      if (threadIdx.x == 0) rhs[r] = (k0 + r < nC ? c[k0 + r] : 0.0) - part;
-    }
-    __syncthreads();
-    for (int r = threadIdx.x; r < EB; r += NT) {
-      double acc = 0;
-      for (int q = 0; q <= r; ++q) acc += Linv[(int64_t)k * EB * EB + r * EB + q] * rhs[q];
-      tmp[k0 + r] = acc;
-    }
-    __syncthreads();
-  }
-  // backward: y = L^{-T} tmp
-  for (int k = nb - 1; k >= 0; --k) {
-    const int k0 = k * EB;
-    const int rest = nb * EB - (k0 + EB);
-    for (int r = 0; r < EB; ++r) {
-      double part = 0;
-      for (int q = threadIdx.x; q < rest; q += NT) part += L[(int64_t)(k0 + EB + q) * ldE + k0 + r] * y[k0 + EB + q];
-      part = block_sum(part, red);
-      if (threadIdx.x == 0) rhs[r] = tmp[k0 + r] - part;
-    }
-    __syncthreads();
-    for (int r = threadIdx.x; r < EB; r += NT) {
-      double acc = 0;
-      for (int q = r; q < EB; ++q) acc += Linv[(int64_t)k * EB * EB + q * EB + r] * rhs[q];
-      y[k0 + r] = acc;
-    }
-    __syncthreads();
-  }
-}
 
 }  // namespace
 
@@ -257,10 +122,8 @@ void build_coarse(Handle& h, cudaStream_t s) {
   co.col_off = mem.alloc<int32_t>(N + 1);
   CK(cudaMemcpyAsync(co.col_off, co.h_col_off.data(), 4 * (N + 1), cudaMemcpyHostToDevice, s));
   const int ldE = (int)round_up(co.n_C, EB);
-  const int nb = ldE / EB;
   co.E = mem.alloc<double>((int64_t)ldE * ldE);
   co.E_copy = mem.alloc<double>((int64_t)ldE * ldE);
-  co.Einv_diag = mem.alloc<double>((int64_t)nb * EB * EB);
   co.cvec = mem.alloc<double>(3LL * ldE);
   CK(cudaMemsetAsync(co.E, 0, sizeof(double) * ldE * ldE, s));
   std::vector<int64_t> az(N);
@@ -271,36 +134,39 @@ void build_coarse(Handle& h, cudaStream_t s) {
   CK(cudaMemcpyAsync(az_off, az.data(), 8 * N, cudaMemcpyHostToDevice, s));
   unsigned long long* nnz = mem.alloc<unsigned long long>(1);
   CK(cudaMemsetAsync(nnz, 0, 8, s));
+  // nonzero blocks (owner, j): at most one per (j, owner of a node of Omega_j)
+  int2* pairs = mem.alloc<int2>(h.ov.sum_n);
+  unsigned int* npairs = mem.alloc<unsigned int>(1);
+  CK(cudaMemsetAsync(npairs, 0, sizeof(unsigned int), s));
   const size_t ksm = sizeof(int32_t) * MAX_NI;
   CK(cudaFuncSetAttribute(k_assemble_E, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ksm));
   k_assemble_E<<<N, NT, ksm, s>>>(ldE, co.E, co.Z, co.z_off, co.count, co.col_off, h.ov.sub_off, h.ov.omega,
                                   h.part, h.ov.own_pos, h.row_ptr, h.val, h.ov.ent_off, h.ov.lcol, h.dev_p,
-                                  h.dev_n, nev, AZ, az_off, nnz);
-  k_pad_identity<<<4, NT, 0, s>>>(co.E, ldE, co.n_C);
+                                  h.dev_n, nev, AZ, az_off, nnz, pairs, npairs);
   CK_LAUNCH("assemble E");
   CK(cudaMemcpyAsync(co.E_copy, co.E, sizeof(double) * ldE * ldE, cudaMemcpyDeviceToDevice, s));
   unsigned long long hn = 0;
+  unsigned int hp = 0;
   CK(cudaMemcpyAsync(&hn, nnz, 8, cudaMemcpyDeviceToHost, s));
-  if (h.events) CK(cudaEventRecord(h.ev[7], s));
-  // dense right-looking blocked Cholesky
-  for (int kb = 0; kb < nb; ++kb) {
-    k_potrf_diag<<<1, NT, 0, s>>>(co.E, ldE, kb, co.Einv_diag, h.dn.err);
-    if (kb + 1 < nb) {
-      k_trsm_panel<<<nb - kb - 1, NT, 0, s>>>(co.E, ldE, kb, nb, co.Einv_diag);
-      int m = nb - kb - 1;
-      k_syrk_update<<<m * (m + 1) / 2, NT, 0, s>>>(co.E, ldE, kb, nb);
-    }
-  }
-  CK_LAUNCH("factor E");
+  CK(cudaMemcpyAsync(&hp, npairs, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
+  std::vector<int2> hpairs(hp);
+  if (hp) CK(cudaMemcpy(hpairs.data(), pairs, sizeof(int2) * hp, cudaMemcpyDeviceToHost));
   co.nnz_C = (int64_t)hn;
+  if (h.events) CK(cudaEventRecord(h.ev[7], s));
+  // subdomain graph of E (symmetrised, subdomains without coarse vectors kept)
+  std::vector<std::vector<int>> adj(N);
+  for (const int2& pr : hpairs)
+    if (pr.x != pr.y) { adj[pr.x].push_back(pr.y); adj[pr.y].push_back(pr.x); }
+  for (auto& a : adj) { std::sort(a.begin(), a.end()); a.erase(std::unique(a.begin(), a.end()), a.end()); }
+  nd_setup(h, adj, s);
+  nd_prepare_smem(h);
+  nd_factor(h, s);
   check_device_error(h, s, "coarse factorisation");
 }
 
 void coarse_solve(Handle& h, const double* c, double* y, cudaStream_t s, const int32_t* done) {
-  Coarse& co = h.co;
-  const int ldE = (int)round_up(co.n_C, EB);
-  k_dense_solve<<<1, NT, 0, s>>>(co.E, ldE, ldE / EB, co.Einv_diag, c, co.n_C, y, co.cvec + 2 * ldE, done);
+  nd_solve(h, c, y, s, done);
 }
 
 }  // namespace asmgpu

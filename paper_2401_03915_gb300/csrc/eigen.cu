@@ -13,7 +13,9 @@
 // nonzero only in rows I_i and columns Gamma_delta, where it equals X_p, so
 // its left singular vectors are those of X_p: the iteration runs on
 // X_p X_p^T with Euclidean orthonormal blocks, and the kept vectors are the
-// coarse vectors themselves.
+// coarse vectors themselves.  The Euclidean SVD is not invariant under the
+// diagonal scaling of the local sweep, so here the scaling is undone inside
+// the products with X_p.
 //
 // Each sweep: power step, CholQR2 re-orthonormalisation (Gram in FP64),
 // Rayleigh-Ritz with a cyclic Jacobi eigensolver (Golub & Van Loan, Alg.
@@ -38,10 +40,20 @@ struct SubdomainView {
   int pos0;       // omega position of row 0
 };
 
+// Diagonal scalings of the general path: X_p = S_I X^_p S_G^{-1}, where X^_p
+// comes from the scaled sweep and S = D^{-1/2}.  Null pointers: no scaling.
+struct XScale {
+  const double* ds = nullptr;
+  const int32_t* omI = nullptr;   // omega of I_i
+  const int32_t* omG = nullptr;   // omega of Gamma_delta
+  __device__ double sI(int r) const { return ds ? ds[omI[r]] : 1.0; }
+  __device__ double sG(int k) const { return ds ? ds[omG[k]] : 1.0; }
+};
+
 // V (p x s) = X_p Y (Y: g x s); XpT is g x p row-major.
 template <typename T>
 __device__ void mul_Xp(const T* __restrict__ XpT, int p, int g, const T* __restrict__ Y, T* __restrict__ V, int s,
-                       int ncols) {
+                       int ncols, XScale sc = XScale()) {
   for (int r = threadIdx.x; r < p; r += NT) {
     for (int j0 = 0; j0 < ncols; j0 += JC) {
       T acc[JC];
@@ -49,21 +61,24 @@ __device__ void mul_Xp(const T* __restrict__ XpT, int p, int g, const T* __restr
       for (int q = 0; q < JC; ++q) acc[q] = 0;
       for (int k = 0; k < g; ++k) {
         T x = XpT[(int64_t)k * p + r];
+        if (sc.ds) x = (T)((double)x / sc.sG(k));
         const T* y = Y + (int64_t)k * s + j0;
 #pragma unroll
         for (int q = 0; q < JC; ++q)
           if (j0 + q < ncols) acc[q] += x * y[q];
       }
+      const T f = (T)sc.sI(r);
 #pragma unroll
       for (int q = 0; q < JC; ++q)
-        if (j0 + q < ncols) V[(int64_t)r * s + j0 + q] = acc[q];
+        if (j0 + q < ncols) V[(int64_t)r * s + j0 + q] = acc[q] * f;
     }
   }
 }
 
 // W (g x s) = X_p^T V (V: p x s): one warp per output row.
 template <typename T>
-__device__ void mul_XpT(const T* __restrict__ XpT, int p, int g, const T* __restrict__ V, T* __restrict__ W, int s) {
+__device__ void mul_XpT(const T* __restrict__ XpT, int p, int g, const T* __restrict__ V, T* __restrict__ W, int s,
+                        XScale sc = XScale()) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int k = wid; k < g; k += NW) {
     const T* xr = XpT + (int64_t)k * p;
@@ -73,15 +88,17 @@ __device__ void mul_XpT(const T* __restrict__ XpT, int p, int g, const T* __rest
       for (int q = 0; q < JC; ++q) acc[q] = 0;
       for (int r = lane; r < p; r += 32) {
         T x = xr[r];
+        if (sc.ds) x = (T)((double)x * sc.sI(r));
         const T* v = V + (int64_t)r * s + j0;
 #pragma unroll
         for (int q = 0; q < JC; ++q)
           if (j0 + q < s) acc[q] += x * v[q];
       }
+      const T f = (T)(1.0 / sc.sG(k));
 #pragma unroll
       for (int q = 0; q < JC; ++q) {
         T t = warp_sum(acc[q]);
-        if (lane == 0 && j0 + q < s) W[(int64_t)k * s + j0 + q] = t;
+        if (lane == 0 && j0 + q < s) W[(int64_t)k * s + j0 + q] = t * f;
       }
     }
   }
@@ -90,11 +107,13 @@ __device__ void mul_XpT(const T* __restrict__ XpT, int p, int g, const T* __rest
 // AV (p x s) = A_{I,I} V, from the local CSR (columns < p).
 template <typename T>
 __device__ void mul_AII(const SubdomainView& sv, const int32_t* __restrict__ omega, const int32_t* __restrict__ rp,
-                        const double* __restrict__ val, const int64_t* __restrict__ ent_off,
+                        const int32_t* __restrict__ ci, const double* __restrict__ val,
+                        const double* __restrict__ ds, const int64_t* __restrict__ ent_off,
                         const int32_t* __restrict__ lcol, const T* __restrict__ V, T* __restrict__ AV, int s) {
   for (int a = threadIdx.x; a < sv.p; a += NT) {
     int v = omega[sv.pos0 + a];
     int b = rp[v], e = rp[v + 1];
+    const double sv_ = ds[v];
     int64_t e0 = ent_off[sv.pos0 + a];
     for (int j0 = 0; j0 < s; j0 += JC) {
       T acc[JC];
@@ -103,7 +122,7 @@ __device__ void mul_AII(const SubdomainView& sv, const int32_t* __restrict__ ome
       for (int t = 0; t < e - b; ++t) {
         int lc = lcol[e0 + t];
         if (lc < 0 || lc >= sv.p) continue;
-        T w = (T)val[b + t];
+        T w = (T)(val[b + t] * sv_ * ds[ci[b + t]]);
         const T* vr = V + (int64_t)lc * s + j0;
 #pragma unroll
         for (int q = 0; q < JC; ++q)
@@ -307,7 +326,7 @@ __global__ void __launch_bounds__(NT) k_subspace(
     const int32_t* __restrict__ np_arr, const int32_t* __restrict__ n_arr, const int32_t* __restrict__ m_arr,
     const int32_t* __restrict__ p_arr, const int32_t* __restrict__ sub_off, const int64_t* __restrict__ ent_off,
     const int32_t* __restrict__ lcol, const int32_t* __restrict__ omega, const int32_t* __restrict__ rp,
-    const double* __restrict__ val, T* scratch, const int64_t* __restrict__ scr_off, int nev, int over,
+    const int32_t* __restrict__ ci, const double* __restrict__ val, const double* __restrict__ ds, T* scratch, const int64_t* __restrict__ scr_off, int nev, int over,
     int max_sweeps, double tol, uint64_t seed, const float* __restrict__ warm, const int64_t* __restrict__ warm_off,
     double* __restrict__ values, double* __restrict__ resid, int32_t* __restrict__ count,
     int32_t* __restrict__ sweeps_out, double* __restrict__ Z, const int64_t* __restrict__ z_off) {
@@ -332,6 +351,8 @@ __global__ void __launch_bounds__(NT) k_subspace(
   const T* XpT = XpT_all + xs_off[i];
   const T* Smat = S_all + s_off[i];
   const T* R = work + work_off[i] + (int64_t)sv.m * sv.ld + sv.m;
+  XScale xs;
+  if (!SPD) { xs.ds = ds; xs.omI = omega + sv.pos0; xs.omG = omega + sv.pos0 + sv.m; }
   const int L = max(p, g);
   T* base = scratch + scr_off[i];
   T* Y = base;                       // dim x s
@@ -379,7 +400,7 @@ __global__ void __launch_bounds__(NT) k_subspace(
     // ---- K Y (SPD) or X_p^T Y (general)
     if (SPD) {
       mul_Xp(XpT, p, g, Y, V, s, s); __syncthreads();
-      mul_AII(sv, omega, rp, val, ent_off, lcol, V, AV, s); __syncthreads();
+      mul_AII(sv, omega, rp, ci, val, ds, ent_off, lcol, V, AV, s); __syncthreads();
       mul_XpT(XpT, p, g, AV, KY, s); __syncthreads();
       // H = Y^T K Y
       for (int idx = threadIdx.x; idx < s * s; idx += NT) {
@@ -389,7 +410,7 @@ __global__ void __launch_bounds__(NT) k_subspace(
         H[idx] = acc;
       }
     } else {
-      mul_XpT(XpT, p, g, Y, KY, s); __syncthreads();
+      mul_XpT(XpT, p, g, Y, KY, s, xs); __syncthreads();
       for (int idx = threadIdx.x; idx < s * s; idx += NT) {
         int t = idx / s, u = idx % s;
         T acc = 0;
@@ -413,7 +434,7 @@ __global__ void __launch_bounds__(NT) k_subspace(
     if (SPD) { right_mul(MY, TMP, dim, s, QS); T* t = MY; MY = TMP; TMP = t; }
     // ---- residuals of the first k Ritz pairs
     T mu0 = mu[0] > T(0) ? mu[0] : T(1);
-    if (!SPD) { mul_Xp(XpT, p, g, KY, V, s, s); __syncthreads(); }   // X_p X_p^T y
+    if (!SPD) { mul_Xp(XpT, p, g, KY, V, s, s, xs); __syncthreads(); }   // X_p X_p^T y
     for (int j = 0; j < k; ++j) {
       T part = 0, nrm = 0;
       for (int r = threadIdx.x; r < dim; r += NT) {
@@ -472,7 +493,7 @@ __global__ void __launch_bounds__(NT) k_subspace(
     __syncthreads();
     for (int64_t idx = threadIdx.x; idx < (int64_t)p * nev; idx += NT) {
       int r = (int)(idx / nev), j = (int)(idx % nev);
-      Zi[idx] = j < kept ? (double)V[(int64_t)r * s + j] : 0.0;
+      Zi[idx] = j < kept ? (double)V[(int64_t)r * s + j] * ds[omega[sv.pos0 + r]] : 0.0;
     }
   } else {
     for (int64_t idx = threadIdx.x; idx < (int64_t)p * nev; idx += NT) {
@@ -524,14 +545,14 @@ void run_eigen(Handle& h, cudaStream_t s) {
     CK(cudaFuncSetAttribute(k_subspace<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_subspace<T, true><<<N, NT, smem, s>>>(
         (const T*)dn.XpT, dn.xs_off, (const T*)dn.S, dn.s_off, (const T*)dn.work, dn.work_off, dn.np, h.dev_n,
-        h.dev_m, h.dev_p, h.ov.sub_off, h.ov.ent_off, h.ov.lcol, h.ov.omega, h.row_ptr, h.val, (T*)co.scratch,
+        h.dev_m, h.dev_p, h.ov.sub_off, h.ov.ent_off, h.ov.lcol, h.ov.omega, h.row_ptr, h.col_idx, h.val, h.dscale, (T*)co.scratch,
         co.scr_off, nev, over, maxsw, tol, h.opt.seed, h.warm, h.warm_off, co.values, co.resid, co.count,
         co.sweeps, co.Z, co.z_off);
   } else {
     CK(cudaFuncSetAttribute(k_subspace<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_subspace<T, false><<<N, NT, smem, s>>>(
         (const T*)dn.XpT, dn.xs_off, (const T*)dn.S, dn.s_off, (const T*)dn.work, dn.work_off, dn.np, h.dev_n,
-        h.dev_m, h.dev_p, h.ov.sub_off, h.ov.ent_off, h.ov.lcol, h.ov.omega, h.row_ptr, h.val, (T*)co.scratch,
+        h.dev_m, h.dev_p, h.ov.sub_off, h.ov.ent_off, h.ov.lcol, h.ov.omega, h.row_ptr, h.col_idx, h.val, h.dscale, (T*)co.scratch,
         co.scr_off, nev, over, maxsw, tol, h.opt.seed, nullptr, nullptr, co.values, co.resid, co.count,
         co.sweeps, co.Z, co.z_off);
   }

@@ -2,6 +2,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "coarse_nd.cuh"
 
 namespace asmgpu {
 
@@ -98,12 +99,14 @@ struct Handle {
   int32_t *row_ptr = nullptr, *col_idx = nullptr, *part = nullptr;
   double* val = nullptr;
   int32_t *dev_n = nullptr, *dev_m = nullptr, *dev_p = nullptr;  // |Omega_i|, |Omega_{1:d-1}|, |I_i|
+  double* dscale = nullptr;         // 1/sqrt(|A_vv|): symmetric diagonal scaling of every A_ii
   float* warm = nullptr;            // optional predicted start blocks (g_i x nev per subdomain)
   int64_t* warm_off = nullptr;
   std::vector<int32_t> h_n, h_p, h_m, h_g;
   Overlap ov;
   Dense dn;
   Coarse co;
+  ND nd;
   Krylov kr;
   asm_setup_info info{};
   cudaEvent_t ev[16];
@@ -124,6 +127,12 @@ void solve_pcg(Handle& h, const double* b, double* x, const asm_solve_opts& o, a
                cudaStream_t s);
 void solve_fgmres(Handle& h, const double* b, double* x, const asm_solve_opts& o,
                   asm_solve_info& info, cudaStream_t s);
+
+// coarse_nd.cu: nested-dissection multifrontal factorisation of E
+void nd_setup(Handle& h, const std::vector<std::vector<int>>& adj, cudaStream_t s);
+void nd_factor(Handle& h, cudaStream_t s);
+void nd_solve(Handle& h, const double* c, double* y, cudaStream_t s, const int32_t* done);
+void nd_prepare_smem(Handle& h);
 
 // Read back and clear the device error word; throw the matching status.
 void check_device_error(Handle& h, cudaStream_t s, const char* stage);

@@ -2,6 +2,13 @@
 // place by a blocked Gauss-Jordan sweep, and pack the inverse into the tiles
 // the apply streams.
 //
+// What is gathered is the symmetrically scaled A^_ii = D^{-1/2} A_ii D^{-1/2},
+// D = diag(A): A_ii^{-1} = D^{-1/2} A^_ii^{-1} D^{-1/2}, and the scaling maps
+// the local eigenproblem onto itself (same eigenvalues, vectors scaled by
+// D^{1/2} on Gamma and the coarse vectors by D^{-1/2} on I_i).  It removes
+// the coefficient contrast from the conditioning of the single-precision
+// sweep; the apply and the eigen stage undo it.
+//
 // The sweep eliminates the unknowns of Omega_{i,1:delta-1} first.  At that
 // midpoint the working matrix holds
 //     [ B^{-1}         B^{-1} C          ]
@@ -25,7 +32,8 @@ constexpr int KB = 32;  // pivot block of the sweep
 template <typename T>
 __global__ void k_gather(const int32_t* __restrict__ omega, int64_t m, const int32_t* __restrict__ pos_sub,
                          const int32_t* __restrict__ sub_off, const int32_t* __restrict__ rp,
-                         const double* __restrict__ val, const int64_t* __restrict__ ent_off,
+                         const int32_t* __restrict__ ci, const double* __restrict__ val,
+                         const double* __restrict__ ds, const int64_t* __restrict__ ent_off,
                          const int32_t* __restrict__ lcol, const int64_t* __restrict__ work_off,
                          const int32_t* __restrict__ np, T* work) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < m; k += (int64_t)gridDim.x * blockDim.x) {
@@ -34,9 +42,10 @@ __global__ void k_gather(const int32_t* __restrict__ omega, int64_t m, const int
     T* row = work + work_off[i] + (int64_t)a * np[i];
     int64_t e0 = ent_off[k];
     int b = rp[v], e = rp[v + 1];
+    const double sv = ds[v];
     for (int t = 0; t < e - b; ++t) {
       int lc = lcol[e0 + t];
-      if (lc >= 0) row[lc] = (T)val[b + t];
+      if (lc >= 0) row[lc] = (T)(val[b + t] * sv * ds[ci[b + t]]);
     }
   }
 }
@@ -305,7 +314,8 @@ void run_local(Handle& h, cudaStream_t s) {
   CK(cudaMemsetAsync(work, 0, sizeof(T) * w, s));
   if (h.events) CK(cudaEventRecord(h.ev[2], s));
   unsigned gg = (unsigned)std::min<int64_t>(ceil_div(ov.sum_n, NT), 152 * 16);
-  k_gather<T><<<gg, NT, 0, s>>>(ov.omega, ov.sum_n, ov.pos_sub, ov.sub_off, h.row_ptr, h.val, ov.ent_off,
+  k_gather<T><<<gg, NT, 0, s>>>(ov.omega, ov.sum_n, ov.pos_sub, ov.sub_off, h.row_ptr, h.col_idx, h.val,
+                                h.dscale, ov.ent_off,
                                 ov.lcol, dn.work_off, dn.np, work);
   CK_LAUNCH("gather A_ii");
   if (h.events) CK(cudaEventRecord(h.ev[3], s));

@@ -209,6 +209,16 @@ __global__ void __launch_bounds__(NT) k_bfs(const int32_t* __restrict__ gptr, co
   }
 }
 
+// s_v = 1 / sqrt(|A_vv|) (1 if the diagonal is absent or zero).
+__global__ void k_diag_scale(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                             const double* __restrict__ val, int n, double* __restrict__ ds) {
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+    int k = bsearch_i32(ci, rp[r], rp[r + 1], r);
+    double d = k >= 0 ? fabs(val[k]) : 0.0;
+    ds[r] = d > 0 ? 1.0 / sqrt(d) : 1.0;
+  }
+}
+
 __global__ void k_pos_sub(const int32_t* __restrict__ sub_off, int32_t* pos_sub) {
   int i = blockIdx.x;
   for (int k = sub_off[i] + threadIdx.x; k < sub_off[i + 1]; k += blockDim.x) pos_sub[k] = i;
@@ -288,6 +298,10 @@ void build_overlap(Handle& h, cudaStream_t s) {
                                     " (row_ptr, column range/order, or part outside 0..N-1)");
     if (e & DERR_NONFINITE) fail(ASM_ERR_NONFINITE, "A has a NaN or Inf value");
   }
+
+  // -- diagonal scaling used by every local matrix
+  h.dscale = mem.alloc<double>(n);
+  k_diag_scale<<<grid_for(n), NT, 0, s>>>(h.row_ptr, h.col_idx, h.val, n, h.dscale);
 
   // -- graph of A + A^T without self loops
   int32_t* tcnt = mem.alloc<int32_t>(n + 1);

@@ -227,3 +227,27 @@ def test_nonfinite_and_malformed_inputs(P):
     with pytest.raises(P.AsmError) as e:
         make(P, prob.csr(), bad, prob.N, 1, 2)
     assert e.value.name == "INVALID_ARG"
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_coarse_correction_matches_its_definition(P, prec):
+    """Two-level minus one-level apply equals Z E^{-1} Z^T r for the GPU's own
+    Z and E, solved densely on the CPU: checks the nested-dissection coarse
+    factorisation and solve on a tree with several levels."""
+    prob = diffusion3d(24, (4, 4, 4), contrast=1e3, nev=8)
+    A = prob.csr()
+    pre2 = make(P, A, prob.part, prob.N, 1, 8, precision=prec)
+    pre1 = make(P, A, prob.part, prob.N, 1, 0, precision=prec)
+    r = SplitMix64(7).normal(prob.n)
+    rt = torch.as_tensor(r, device="cuda")
+    zc = (pre2.apply(rt) - pre1.apply(rt)).cpu().numpy()
+    ovs = O.overlap(A, prob.part, prob.N, 1)
+    blocks, col = P.asm_get_coarse_basis(pre2.h, [ov.p for ov in ovs])
+    E = P.asm_get_coarse_matrix(pre2.h)
+    Z = np.zeros((prob.n, col[-1]))
+    for i, ov in enumerate(ovs):
+        Z[ov.omega[:ov.p], col[i]:col[i + 1]] = blocks[i]
+    np.testing.assert_allclose(E, Z.T @ (A @ Z), rtol=0, atol=1e-10 * np.abs(E).max())
+    ref = Z @ np.linalg.solve(0.5 * (E + E.T), Z.T @ r)
+    np.testing.assert_allclose(zc, ref, rtol=0, atol=1e-9 * np.abs(ref).max())
+    pre1.close(); pre2.close()
