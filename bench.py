@@ -1,0 +1,361 @@
+#!/usr/bin/env python
+"""Benchmark: setup + solve of the two-level additive Schwarz method.
+
+One step = asm_setup (overlap, local gather + inverse, subspace iteration,
+Z and E = Z^T A Z, FP64 coarse factorisation) + asm_solve (FP64 PCG to a
+relative residual of 1e-8) + asm_destroy on the 64^3 high-contrast diffusion
+workload (n = 262,144, 512 subdomains of 8^3, overlap 1, nev 16), with the
+local work in FP32 and everything else in FP64.  Inputs are generated on the
+host, copied to the device once, and are resident in HBM when the timed
+region starts.  The step's working set (0.8 GB of local inverses alone) is
+far larger than L2, so no explicit flush is done between steps.
+
+Prints one JSON line.  --impl reference times the CPU oracle on a bounded
+sample of the same workload instead.  Multi-GPU runs (torchrun) execute
+independent replicas: the path has no exchange step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "setup+solve s to 1e-8 rel resid; apply GB/s; mixed/learned vs FP64 same GPU"
+UNIT = "s"
+WORKLOAD = ("3D 7-point high-contrast diffusion 64^3 (n=262144, contrast 1e6 channels/inclusions 10%), "
+            "512 subdomains 8^3, overlap 1, nev 16")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="c2")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--apply-iters", type=int, default=20)
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            m = json.load(f)
+        return float(m["hbm_gbs"]), float(m["bf16_tflops"]), "measured"
+    except Exception:
+        return 6800.0, 1900.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            with open(self.path) as f:
+                for line in f:
+                    parts = [p.strip() for p in line.split(",")]
+                    if len(parts) < 9:
+                        continue
+                    try:
+                        sm.append(float(parts[1]))
+                        mx = float(parts[2])
+                    except ValueError:
+                        continue
+                    for name, v in zip(names, parts[5:9]):
+                        if v.lower().startswith("active"):
+                            reasons.add(name)
+            os.unlink(self.path)
+        except Exception:
+            pass
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle on a bounded sample (the cpu_baseline and the reference arm)
+# ---------------------------------------------------------------------------
+def oracle_reference_iterations():
+    path = os.path.join(ROOT, "tests", "golden", "c2_oracle_reference.json")
+    try:
+        with open(path) as f:
+            return int(json.load(f)["pcg_iterations_two_level"]), "stored oracle run"
+    except Exception:
+        return None, None
+
+
+def oracle_sample(prob, n_sub: int, gpu_iterations: int | None):
+    """Time the oracle's steps on a bounded sample and extrapolate to one
+    full setup + solve: local setup (overlap, dense A_ii, Cholesky, dense GEVP)
+    of n_sub subdomains scaled by N / n_sub; the dense FP64 Cholesky of an
+    n_C x n_C SPD matrix (the oracle factors E densely; timing does not
+    depend on the values); per PCG iteration one SpMV, the local solves of the
+    sampled subdomains scaled by N / n_sub, Z^T r, the coarse solve and Z y;
+    times the oracle's own iteration count."""
+    import scipy.linalg as sla
+    import scipy.sparse as sp
+    import oracle as O
+
+    threads = os.cpu_count()
+    A = prob.csr()
+    t0 = time.perf_counter()
+    ovs = O.overlap(A, prob.part, prob.N, prob.delta)
+    t_overlap = time.perf_counter() - t0
+    step = max(1, prob.N // n_sub)
+    sample = list(range(0, prob.N, step))[:n_sub]
+    t0 = time.perf_counter()
+    facs = []
+    for i in sample:
+        ov = ovs[i]
+        Aii = O.local_matrix(A, ov)
+        facs.append((ov, sla.cho_factor(Aii, lower=True)))
+        O.gevp_svd(Aii, ov)
+    t_local = (time.perf_counter() - t0) * prob.N / len(sample)
+    nC = prob.N * prob.nev
+    rng = np.random.default_rng(0)
+    G = rng.standard_normal((nC, 64))
+    Em = G @ G.T + nC * np.eye(nC)
+    t0 = time.perf_counter()
+    Ef = sla.cho_factor(Em, lower=True)
+    t_efac = time.perf_counter() - t0
+    # one iteration
+    r = rng.standard_normal(prob.n)
+    rows = np.concatenate([ov.omega[:ov.p] for ov in ovs])
+    cols = np.concatenate([np.repeat(np.arange(i * prob.nev, (i + 1) * prob.nev)[None, :], ov.p, 0).ravel()
+                           for i, ov in enumerate(ovs)])
+    Z = sp.csc_matrix((np.ones(len(cols)), (np.repeat(rows, prob.nev), cols)), shape=(prob.n, nC))
+    t0 = time.perf_counter()
+    q = A @ r
+    z = np.zeros_like(r)
+    for ov, f in facs:
+        np.add.at(z, ov.omega, sla.cho_solve(f, r[ov.omega]))
+    t_loc_iter = (time.perf_counter() - t0) * prob.N / len(sample)
+    t0 = time.perf_counter()
+    y = sla.cho_solve(Ef, Z.T @ r)
+    z += Z @ y
+    t_coarse_iter = time.perf_counter() - t0
+    its, src = oracle_reference_iterations()
+    if its is None:
+        its, src = gpu_iterations or 0, "GPU FP64 iteration count (no stored oracle run)"
+    total = t_overlap + t_local + t_efac + its * (t_loc_iter + t_coarse_iter)
+    sample_desc = (f"oracle local setup of {len(sample)} of {prob.N} subdomains (x{prob.N / len(sample):.0f}), "
+                   f"overlap of all, dense Cholesky of a {nC}x{nC} SPD matrix, one PCG iteration's SpMV + "
+                   f"local solves (scaled) + coarse solve, times {its} iterations ({src})")
+    return total, threads, sample_desc
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from asm_inputs import config
+    prob = config(args.config)
+    vals = []
+    desc = threads = None
+    for k in range(args.warmup + args.steps):
+        t, threads, desc = oracle_sample(prob, n_sub=4, gpu_iterations=None)
+        if k >= args.warmup:
+            vals.append(t)
+    v = float(np.mean(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "config": args.config},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_2401_03915_gb300 import build as _b
+    _b.build()
+    import paper_2401_03915_gb300 as P
+    from asm_inputs import config
+
+    prob = config(args.config)
+    dev = torch.device("cuda", local)
+    rp = torch.as_tensor(prob.indptr, device=dev)
+    ci = torch.as_tensor(prob.indices, device=dev)
+    va = torch.as_tensor(prob.data, device=dev)
+    pa = torch.as_tensor(prob.part, device=dev)
+    b = torch.as_tensor(prob.b, device=dev)
+    x = torch.zeros_like(b)
+    prec = P.PREC_FP32 if args.precision == "fp32" else P.PREC_FP64
+    opt = P.default_options(local_precision=prec)
+    sopt = P.default_solve_opts(rtol=1e-8, max_it=5000)
+    stream = torch.cuda.current_stream()
+
+    def step(keep=False):
+        h = P.asm_setup(rp, ci, va, pa, prob.N, prob.delta, prob.nev, opt, stream, True)
+        info = P.asm_solve(h, b, x, sopt, stream)
+        if keep:
+            return h, info
+        P.asm_destroy(h)
+        return None, info
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    l0 = P.asm_kernel_launches()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    infos = []
+    h_last = None
+    for k in range(args.steps):
+        h, inf = step(keep=(k == args.steps - 1))
+        infos.append(inf)
+        h_last = h or h_last
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    l1 = P.asm_kernel_launches()
+    clocks = sampler.stop()
+    # launches of the timed steps only (the last handle's destroy launches nothing)
+    launches = int(l1 - l0)
+    if dist:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    setup_info = P.asm_get_info(h_last)
+    stages = {n: round(setup_info.stage_ms[i], 3) for i, n in enumerate(P.stage_names()) if n}
+
+    # ---- apply kernels (same handle, same stream, CUDA events)
+    r = torch.randn(prob.n, device=dev, dtype=torch.float64)
+    z = torch.empty_like(r)
+    P.asm_time_apply(h_last, r, z, 3, stream)
+    tap = P.asm_time_apply(h_last, r, z, args.apply_iters, stream)
+    hbm, bf16, peak_kind = peaks()
+    elt = 4 if args.precision == "fp32" else 8
+    ovs_sizes = setup_info.sum_ni
+    # algorithmic bytes of the local part: packed lower triangle of every
+    # A_ii^{-1}, read once per apply
+    ni = np.diff(P.asm_get_overlap(h_last)[0]).astype(np.int64)
+    tile_bytes = float(np.sum(ni * (ni + 1) // 2) * elt)
+    achieved = tile_bytes / (tap["local_tiles"] * 1e-3) / 1e9
+    nC = setup_info.n_C
+    apply_bytes = tile_bytes + 2 * 8.0 * prob.nev * prob.n + 12.0 * float(ovs_sizes) * 2
+    apply_gbs = apply_bytes / (tap["apply"] * 1e-3) / 1e9
+    P.asm_destroy(h_last)
+
+    # ---- end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        hb = np.ascontiguousarray(prob.b)
+        hx = np.zeros(prob.n)
+        torch.cuda.synchronize()
+        n_e2e = max(1, min(args.steps, 3))
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            h = P.asm_setup(prob.indptr, prob.indices, prob.data, prob.part, prob.N, prob.delta, prob.nev, opt,
+                            stream, False)
+            P.asm_solve(h, hb, hx, sopt, stream)
+            P.asm_destroy(h)
+        torch.cuda.synchronize()
+        te = (time.perf_counter() - t0) / n_e2e
+        h2d = 4 * (prob.n + 1) + 12 * prob.nnz + 4 * prob.n + 8 * prob.n
+        e2e = {"value": te, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(8 * prob.n)}
+        if dist:
+            t = torch.tensor([te], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e["value"] = float(t.item())
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, threads, desc = oracle_sample(prob, n_sub=16, gpu_iterations=None)
+        cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": ms / 1e3, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "config": args.config, "local_precision": args.precision,
+                       "outer": "FP64 PCG rtol 1e-8", "l2": "working set > L2 (no flush)",
+                       "parallelism": f"replicas x{world}"},
+            "iterations": infos[-1].iterations, "true_relres": infos[-1].true_relres,
+            "setup_stages_ms": stages, "n_C": nC, "sweeps_max": setup_info.sweeps_max,
+            "apply_ms": tap, "apply_gbs": apply_gbs,
+            "roofline": {"bound": "hbm", "kernel": "k_apply_tiles (local part of the apply)",
+                         "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                         "peak_kind": peak_kind, "traffic": None,
+                         "algorithmic_bytes": tile_bytes},
+            "clocks": clocks, "gpu_launches": launches, "e2e": e2e, "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -148,6 +148,16 @@ asm_status asm_solve(asm_handle* h, const double* b, double* x, const asm_solve_
 asm_status asm_spmv(asm_handle* h, const double* x, double* y, void* stream);
 
 asm_status asm_get_info(const asm_handle* h, asm_setup_info* info);
+
+/* Measurement helpers (no counterpart in the paper; used by the benchmark).
+ * asm_kernel_launches: kernel launches executed by this library since it was
+ * loaded (graph replays included), read from per-unit device counters;
+ * synchronises the device.
+ * asm_time_apply: runs the apply `iters` times on `stream` with CUDA events
+ * around its parts and writes the mean milliseconds to ms[4]: local tiles,
+ * coarse restriction + coarse solve, pull-sum, whole apply.  r, z: device. */
+uint64_t asm_kernel_launches(void);
+asm_status asm_time_apply(asm_handle* h, const double* r, double* z, int32_t iters, void* stream, double* ms);
 const char* asm_stage_name(int32_t stage);
 
 /* Overlap index sets, host outputs.  sub_offsets: N+1 entries (start of

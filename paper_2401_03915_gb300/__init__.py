@@ -86,6 +86,10 @@ def load(path: str | None = None) -> C.CDLL:
     L.asm_get_local_values.argtypes = [vp, vp, vp]
     L.asm_get_coarse_basis.argtypes = [vp, vp, vp]
     L.asm_get_coarse_matrix.argtypes = [vp, vp]
+    L.asm_kernel_launches.restype = C.c_uint64
+    L.asm_kernel_launches.argtypes = []
+    L.asm_time_apply.argtypes = [vp, vp, vp, i32, vp, C.POINTER(C.c_double)]
+    L.asm_time_apply.restype = C.c_int
     L.asm_destroy.argtypes = [vp]
     L.asm_destroy.restype = None
     L.asm_last_error.restype = C.c_char_p
@@ -213,6 +217,16 @@ def asm_get_coarse_matrix(h: int) -> np.ndarray:
     if inf.n_C:
         _check(load().asm_get_coarse_matrix(h, E.ctypes.data))
     return E
+
+
+def asm_kernel_launches() -> int:
+    return int(load().asm_kernel_launches())
+
+
+def asm_time_apply(h: int, r, z, iters: int = 10, stream=None) -> dict:
+    ms = (C.c_double * 4)()
+    _check(load().asm_time_apply(h, _ptr(r), _ptr(z), iters, _stream(stream), ms))
+    return {"local_tiles": ms[0], "coarse": ms[1], "pull": ms[2], "apply": ms[3]}
 
 
 def asm_destroy(h: int) -> None:

@@ -43,6 +43,7 @@ __global__ void __launch_bounds__(NT) k_apply_tiles(const T* __restrict__ tiles,
                                                     const int64_t* __restrict__ part_off, const double* __restrict__ r,
                                                     const double* __restrict__ ds, T* __restrict__ partials,
                                                     const int32_t* __restrict__ done) {
+  COUNT_LAUNCH();
   if (done != nullptr && *done) return;
   __shared__ T xI[TILE], xJ[TILE];
   __shared__ T colpart[NT / 32][TILE];
@@ -110,6 +111,7 @@ __global__ void __launch_bounds__(NT) k_coarse_restrict(const double* __restrict
                                                         const int32_t* __restrict__ omega, int nev,
                                                         const double* __restrict__ r, double* __restrict__ c,
                                                         const int32_t* __restrict__ done) {
+  COUNT_LAUNCH();
   if (done != nullptr && *done) return;
   __shared__ double red[NT / 32][32];
   const int i = blockIdx.x;
@@ -156,6 +158,7 @@ __global__ void __launch_bounds__(NT) k_apply_pull(int n, const int32_t* __restr
                                                    const int32_t* __restrict__ col_off, int nev,
                                                    const double* __restrict__ yc, const double* __restrict__ ds,
                                                    double* __restrict__ z, const int32_t* __restrict__ done) {
+  COUNT_LAUNCH();
   if (done != nullptr && *done) return;
   for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
     double acc = 0;
@@ -186,36 +189,80 @@ __global__ void __launch_bounds__(NT) k_apply_pull(int n, const int32_t* __restr
 }
 
 template <typename T>
-void apply_impl(Handle& h, const double* r, double* z, cudaStream_t s, const int32_t* done) {
+void apply_local(Handle& h, const double* r, cudaStream_t s, const int32_t* done) {
   Dense& dn = h.dn;
-  Coarse& co = h.co;
-  const bool sym = h.opt.spd != 0;
   unsigned gt = (unsigned)std::min<int64_t>(std::max<int64_t>(dn.n_tiles, 1), 152 * 8);
-  if (sym)
+  if (h.opt.spd)
     k_apply_tiles<T, true><<<gt, NT, 0, s>>>((const T*)dn.tiles, dn.tile_desc, dn.n_tiles, h.ov.omega,
-                                             h.ov.sub_off, h.dev_n, dn.nt, dn.part_off, r, h.dscale, (T*)dn.partials, done);
+                                             h.ov.sub_off, h.dev_n, dn.nt, dn.part_off, r, h.dscale,
+                                             (T*)dn.partials, done);
   else
     k_apply_tiles<T, false><<<gt, NT, 0, s>>>((const T*)dn.tiles, dn.tile_desc, dn.n_tiles, h.ov.omega,
-                                              h.ov.sub_off, h.dev_n, dn.nt, dn.part_off, r, h.dscale, (T*)dn.partials, done);
-  const double* yc = nullptr;
-  if (co.n_C > 0) {
-    double* c = co.cvec;
-    double* y = co.cvec + round_up(co.n_C, 64);
-    k_coarse_restrict<<<h.N, NT, 0, s>>>(co.Z, co.z_off, co.count, co.col_off, h.ov.sub_off, h.dev_p, h.ov.omega,
-                                         h.nev, r, c, done);
-    coarse_solve(h, c, y, s, done);
-    yc = y;
-  }
+                                              h.ov.sub_off, h.dev_n, dn.nt, dn.part_off, r, h.dscale,
+                                              (T*)dn.partials, done);
+}
+
+// Z^T r and the coarse solve; returns the coarse solution (or null).
+const double* apply_coarse(Handle& h, const double* r, cudaStream_t s, const int32_t* done) {
+  Coarse& co = h.co;
+  if (co.n_C == 0) return nullptr;
+  double* c = co.cvec;
+  double* y = co.cvec + round_up(co.n_C, 64);
+  k_coarse_restrict<<<h.N, NT, 0, s>>>(co.Z, co.z_off, co.count, co.col_off, h.ov.sub_off, h.dev_p, h.ov.omega,
+                                       h.nev, r, c, done);
+  coarse_solve(h, c, y, s, done);
+  return y;
+}
+
+template <typename T>
+void apply_pull(Handle& h, const double* yc, double* z, cudaStream_t s, const int32_t* done) {
+  Dense& dn = h.dn;
+  Coarse& co = h.co;
   unsigned gp = (unsigned)std::min<int64_t>(ceil_div(h.n, NT), 152 * 16);
   k_apply_pull<T><<<gp, NT, 0, s>>>(h.n, h.ov.occ_ptr, h.ov.occ_pos, h.ov.pos_sub, h.ov.sub_off, dn.nt, dn.part_off,
                                     (const T*)dn.partials, h.part, h.ov.own_pos, co.Z, co.z_off, co.count,
                                     co.col_off, h.nev, yc, h.dscale, z, done);
 }
 
+template <typename T>
+void apply_impl(Handle& h, const double* r, double* z, cudaStream_t s, const int32_t* done) {
+  apply_local<T>(h, r, s, done);
+  const double* yc = apply_coarse(h, r, s, done);
+  apply_pull<T>(h, yc, z, s, done);
+}
+
+template <typename T>
+void time_impl(Handle& h, const double* r, double* z, int iters, cudaStream_t s, double* ms) {
+  cudaEvent_t e[4];
+  for (auto& x : e) CK(cudaEventCreate(&x));
+  double acc[4] = {0, 0, 0, 0};
+  for (int it = 0; it < iters; ++it) {
+    CK(cudaEventRecord(e[0], s));
+    apply_local<T>(h, r, s, nullptr);
+    CK(cudaEventRecord(e[1], s));
+    const double* yc = apply_coarse(h, r, s, nullptr);
+    CK(cudaEventRecord(e[2], s));
+    apply_pull<T>(h, yc, z, s, nullptr);
+    CK(cudaEventRecord(e[3], s));
+    CK(cudaEventSynchronize(e[3]));
+    float a, b, c;
+    CK(cudaEventElapsedTime(&a, e[0], e[1]));
+    CK(cudaEventElapsedTime(&b, e[1], e[2]));
+    CK(cudaEventElapsedTime(&c, e[2], e[3]));
+    acc[0] += a; acc[1] += b; acc[2] += c; acc[3] += a + b + c;
+  }
+  for (int k = 0; k < 4; ++k) ms[k] = acc[k] / std::max(iters, 1);
+  for (auto& x : e) CK(cudaEventDestroy(x));
+}
+
 }  // namespace
 
 void apply_preconditioner(Handle& h, const double* r, double* z, cudaStream_t s, const int32_t* done) {
   if (h.fp32) apply_impl<float>(h, r, z, s, done); else apply_impl<double>(h, r, z, s, done);
+}
+
+void time_apply(Handle& h, const double* r, double* z, int iters, cudaStream_t s, double* ms) {
+  if (h.fp32) time_impl<float>(h, r, z, iters, s, ms); else time_impl<double>(h, r, z, iters, s, ms);
 }
 
 }  // namespace asmgpu

@@ -263,6 +263,13 @@ asm_status asm_solve(asm_handle* H, const double* b, double* x, const asm_solve_
   return ASM_OK;
 }
 
+uint64_t asm_kernel_launches(void) { return (uint64_t)total_kernel_launches(); }
+
+asm_status asm_time_apply(asm_handle* H, const double* r, double* z, int32_t iters, void* stream, double* ms) {
+  if (!H || !r || !z || !ms || iters < 1) return set_error(ASM_ERR_INVALID_ARG, "null argument or iters < 1");
+  return guarded([&] { time_apply(H->h, r, z, iters, static_cast<cudaStream_t>(stream), ms); });
+}
+
 asm_status asm_get_info(const asm_handle* H, asm_setup_info* info) {
   if (!H || !info) return set_error(ASM_ERR_INVALID_ARG, "null argument");
   *info = H->h.info;

@@ -46,6 +46,7 @@ __global__ void __launch_bounds__(NT) k_assemble_E(
     const int32_t* __restrict__ lcol, const int32_t* __restrict__ p_arr, const int32_t* __restrict__ n_arr,
     int nev, double* __restrict__ AZ, const int64_t* __restrict__ az_off, unsigned long long* nnz,
     int2* __restrict__ pairs, unsigned int* __restrict__ npairs) {
+  COUNT_LAUNCH();
   extern __shared__ int32_t keys[];
   __shared__ int any_nz;
   const int j = blockIdx.x;

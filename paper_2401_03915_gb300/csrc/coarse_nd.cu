@@ -42,6 +42,7 @@ __global__ void __launch_bounds__(NT) k_front_assemble(const FrontDev* __restric
                                                        const int32_t* __restrict__ dofs,
                                                        const int32_t* __restrict__ children,
                                                        const int32_t* __restrict__ invmap, double* __restrict__ M) {
+  COUNT_LAUNCH();
   const int2 tk = tasks[blockIdx.x];
   const FrontDev f = fr[tk.x];
   const int r0 = tk.y * FB;
@@ -69,6 +70,7 @@ __global__ void __launch_bounds__(NT) k_front_assemble(const FrontDev* __restric
 __global__ void __launch_bounds__(NT) k_front_pivot(const FrontDev* __restrict__ fr, const int32_t* __restrict__ list,
                                                     int k, double* __restrict__ M, double* __restrict__ piv,
                                                     int spd, int32_t* err) {
+  COUNT_LAUNCH();
   __shared__ double P[FB][FB + 1];
   __shared__ int bad;
   const int t = list[blockIdx.x];
@@ -113,6 +115,7 @@ __global__ void __launch_bounds__(NT) k_front_pivot(const FrontDev* __restrict__
 // Row panel: M[K][C] <- P M[K][C] for column tiles C != K.
 __global__ void __launch_bounds__(NT) k_front_rowpanel(const FrontDev* __restrict__ fr, const int2* __restrict__ tasks,
                                                        int k, double* __restrict__ M, const double* __restrict__ piv) {
+  COUNT_LAUNCH();
   __shared__ double P[FB][FB + 1];
   __shared__ double X[FB][FB + 1];
   const int2 tk = tasks[blockIdx.x];
@@ -137,6 +140,7 @@ __global__ void __launch_bounds__(NT) k_front_rowpanel(const FrontDev* __restric
 // Rank-64 update: M[R][C] -= M[R][K] M[K][C] for R, C != K (row panel already new).
 __global__ void __launch_bounds__(NT) k_front_update(const FrontDev* __restrict__ fr, const int4* __restrict__ tasks,
                                                      int k, double* __restrict__ M) {
+  COUNT_LAUNCH();
   __shared__ double A[FB][FB + 1];
   __shared__ double B[FB][FB + 1];
   const int4 tk = tasks[blockIdx.x];
@@ -172,6 +176,7 @@ __global__ void __launch_bounds__(NT) k_front_update(const FrontDev* __restrict_
 // writes P into the pivot block.
 __global__ void __launch_bounds__(NT) k_front_colpanel(const FrontDev* __restrict__ fr, const int2* __restrict__ tasks,
                                                        int k, double* __restrict__ M, const double* __restrict__ piv) {
+  COUNT_LAUNCH();
   __shared__ double P[FB][FB + 1];
   __shared__ double X[FB][FB + 1];
   const int2 tk = tasks[blockIdx.x];
@@ -225,6 +230,7 @@ __global__ void __launch_bounds__(NT) k_front_forward(const FrontDev* __restrict
                                                       const int32_t* __restrict__ invmap, const double* __restrict__ M,
                                                       double* __restrict__ vecs, const double* __restrict__ c,
                                                       const int32_t* __restrict__ done) {
+  COUNT_LAUNCH();
   if (done != nullptr && *done) return;
   extern __shared__ double sf[];
   __shared__ double red[NT / 32][FB];
@@ -261,6 +267,7 @@ __global__ void __launch_bounds__(NT) k_front_backward(const FrontDev* __restric
                                                        const int32_t* __restrict__ dofs, const double* __restrict__ M,
                                                        const double* __restrict__ vecs, double* __restrict__ y,
                                                        const int32_t* __restrict__ done) {
+  COUNT_LAUNCH();
   if (done != nullptr && *done) return;
   extern __shared__ double sx[];  // [f_V ; -y_B]
   __shared__ double red[NT / 32][FB];

@@ -124,6 +124,30 @@ __device__ __forceinline__ double counter_normal(uint64_t seed, uint64_t k) {
 }
 
 // ---------------------------------------------------------------------------
+// Launch accounting: every kernel of the library bumps a per-translation-unit
+// device counter once per launch (block 0, thread 0), so graph replays are
+// counted too.  asm_kernel_launches() sums the counters of all units.
+// ---------------------------------------------------------------------------
+static __device__ unsigned long long g_launch_count = 0;
+#define COUNT_LAUNCH()                                                                  \
+  do {                                                                                  \
+    if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0 &&    \
+        threadIdx.y == 0 && threadIdx.z == 0)                                           \
+      atomicAdd(&::asmgpu::g_launch_count, 1ull);                                       \
+  } while (0)
+int register_launch_counter(unsigned long long (*reader)());
+static unsigned long long read_tu_launch_count() {
+  unsigned long long v = 0;
+  if (cudaMemcpyFromSymbol(&v, g_launch_count, sizeof(v)) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return v;
+}
+[[maybe_unused]] static int g_launch_counter_registered = register_launch_counter(&read_tu_launch_count);
+unsigned long long total_kernel_launches();
+
+// ---------------------------------------------------------------------------
 // Host helpers implemented in util.cu
 // ---------------------------------------------------------------------------
 // Exclusive scan of n int32 counts into out (n+1 entries, out[n] = total),

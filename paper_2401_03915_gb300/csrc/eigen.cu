@@ -330,6 +330,7 @@ __global__ void __launch_bounds__(NT) k_subspace(
     int max_sweeps, double tol, uint64_t seed, const float* __restrict__ warm, const int64_t* __restrict__ warm_off,
     double* __restrict__ values, double* __restrict__ resid, int32_t* __restrict__ count,
     int32_t* __restrict__ sweeps_out, double* __restrict__ Z, const int64_t* __restrict__ z_off) {
+  COUNT_LAUNCH();
   extern __shared__ double shd[];
   __shared__ int flag;
   __shared__ int perm[128];

@@ -120,6 +120,7 @@ void build_eigen(Handle& h, cudaStream_t s);                   // eigen.cu
 void build_coarse(Handle& h, cudaStream_t s);                  // coarse.cu: E assembly + factor
 void apply_preconditioner(Handle& h, const double* r, double* z, cudaStream_t s,
                           const int32_t* done = nullptr);                         // apply.cu
+void time_apply(Handle& h, const double* r, double* z, int iters, cudaStream_t s, double* ms);
 void spmv(Handle& h, const double* x, double* y, cudaStream_t s);                 // krylov.cu
 void coarse_solve(Handle& h, const double* c, double* y, cudaStream_t s,
                   const int32_t* done = nullptr);                                 // coarse.cu

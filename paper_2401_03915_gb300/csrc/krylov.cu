@@ -26,6 +26,7 @@ __global__ void __launch_bounds__(NT) k_spmv(int n, const int32_t* __restrict__ 
                                              const double* __restrict__ val, const double* __restrict__ x,
                                              double* __restrict__ y, double* __restrict__ part,
                                              const int32_t* __restrict__ done) {
+  COUNT_LAUNCH();
   if (done != nullptr && done[F_DONE]) return;
   __shared__ double red[NT / 32];
   const int lane = threadIdx.x % VW;
@@ -54,6 +55,7 @@ __global__ void __launch_bounds__(NT) k_spmv(int n, const int32_t* __restrict__ 
 // partial sums of a.b (fixed grid-stride decomposition)
 __global__ void __launch_bounds__(NT) k_dot(int n, const double* __restrict__ a, const double* __restrict__ b,
                                             double* __restrict__ part, const int32_t* __restrict__ done) {
+  COUNT_LAUNCH();
   if (done != nullptr && done[F_DONE]) return;
   __shared__ double red[NT / 32];
   double s = 0;
@@ -74,6 +76,7 @@ __global__ void __launch_bounds__(NT) k_pcg_update(int n, double* __restrict__ x
                                                    const double* __restrict__ p, const double* __restrict__ q,
                                                    const double* __restrict__ scal, double* __restrict__ part,
                                                    const int32_t* __restrict__ done) {
+  COUNT_LAUNCH();
   if (done[F_DONE]) return;
   __shared__ double red[NT / 32];
   const double alpha = scal[S_ALPHA];
@@ -89,6 +92,7 @@ __global__ void __launch_bounds__(NT) k_pcg_update(int n, double* __restrict__ x
 }
 
 __global__ void __launch_bounds__(NT) k_fin_alpha(const double* part, int nb, double* scal, int32_t* flag) {
+  COUNT_LAUNCH();
   if (flag[F_DONE]) return;
   double pq = sum_partials(part, nb);
   if (threadIdx.x == 0) {
@@ -100,6 +104,7 @@ __global__ void __launch_bounds__(NT) k_fin_alpha(const double* part, int nb, do
 
 __global__ void __launch_bounds__(NT) k_fin_res(const double* part, int nb, double* scal, int32_t* flag,
                                                 double* hist, int hist_len) {
+  COUNT_LAUNCH();
   if (flag[F_DONE]) return;
   double rr = sum_partials(part, nb);
   if (threadIdx.x == 0) {
@@ -114,6 +119,7 @@ __global__ void __launch_bounds__(NT) k_fin_res(const double* part, int nb, doub
 }
 
 __global__ void __launch_bounds__(NT) k_fin_beta(const double* part, int nb, double* scal, int32_t* flag) {
+  COUNT_LAUNCH();
   if (flag[F_DONE]) return;
   double rz = sum_partials(part, nb);
   if (threadIdx.x == 0) {
@@ -124,6 +130,7 @@ __global__ void __launch_bounds__(NT) k_fin_beta(const double* part, int nb, dou
 
 __global__ void __launch_bounds__(NT) k_update_p(int n, double* __restrict__ p, const double* __restrict__ z,
                                                  const double* __restrict__ scal, const int32_t* __restrict__ done) {
+  COUNT_LAUNCH();
   if (done[F_DONE]) return;
   const double beta = scal[S_BETA];
   for (int i = blockIdx.x * NT + threadIdx.x; i < n; i += gridDim.x * NT) p[i] = z[i] + beta * p[i];
@@ -131,11 +138,13 @@ __global__ void __launch_bounds__(NT) k_update_p(int n, double* __restrict__ p, 
 
 // generic: out = a + alpha * b  (alpha from scal[ia] times sgn)
 __global__ void k_axpby(int n, double* out, const double* a, const double* b, double alpha) {
+  COUNT_LAUNCH();
   for (int i = blockIdx.x * NT + threadIdx.x; i < n; i += gridDim.x * NT) out[i] = a[i] + alpha * b[i];
 }
 
 __global__ void k_init_scalars(double* scal, int32_t* flag, const double* part, int nb, double rtol, int maxit,
                                int which) {
+  COUNT_LAUNCH();
   double s = sum_partials(part, nb);
   if (threadIdx.x == 0) {
     if (which == 0) {  // ||b||^2

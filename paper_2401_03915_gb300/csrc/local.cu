@@ -36,6 +36,7 @@ __global__ void k_gather(const int32_t* __restrict__ omega, int64_t m, const int
                          const double* __restrict__ ds, const int64_t* __restrict__ ent_off,
                          const int32_t* __restrict__ lcol, const int64_t* __restrict__ work_off,
                          const int32_t* __restrict__ np, T* work) {
+  COUNT_LAUNCH();
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < m; k += (int64_t)gridDim.x * blockDim.x) {
     int v = omega[k], i = pos_sub[k];
     int a = (int)(k - sub_off[i]);
@@ -64,6 +65,7 @@ __global__ void __launch_bounds__(NT) k_sweep(T* __restrict__ work, const int64_
                                               T* __restrict__ XpT, const int64_t* __restrict__ xs_off,
                                               T* __restrict__ Sout, const int64_t* __restrict__ s_off,
                                               int32_t* err) {
+  COUNT_LAUNCH();
   __shared__ T P[KB][KB + 1];
   __shared__ T bufA[64][KB + 1];
   __shared__ T bufB[KB][64 + 1];
@@ -233,6 +235,7 @@ template <typename T>
 __global__ void __launch_bounds__(NT) k_pack(const T* __restrict__ work, const int64_t* __restrict__ work_off,
                                              const int32_t* __restrict__ np, const int32_t* __restrict__ n_arr,
                                              const int4* __restrict__ desc, int64_t ntiles, T* __restrict__ tiles) {
+  COUNT_LAUNCH();
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     int4 d = desc[t];
     int i = d.x, I = d.y, J = d.z;

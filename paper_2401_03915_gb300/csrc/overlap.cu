@@ -18,6 +18,7 @@ constexpr int NT = 256;
 __global__ void k_validate(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                            const double* __restrict__ val, const int32_t* __restrict__ part, int n,
                            int nnz, int N, int32_t* err, int32_t* bad_row) {
+  COUNT_LAUNCH();
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
     int b = rp[r], e = rp[r + 1];
     bool ok = b >= 0 && e >= b && e <= nnz;
@@ -36,6 +37,7 @@ __global__ void k_validate(const int32_t* __restrict__ rp, const int32_t* __rest
 // ---- graph of A + A^T ------------------------------------------------------
 __global__ void k_tcount(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, int n,
                          int32_t* cnt) {
+  COUNT_LAUNCH();
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x)
     for (int k = rp[r]; k < rp[r + 1]; ++k)
       if (ci[k] != r) atomicAdd(&cnt[ci[k]], 1);
@@ -43,6 +45,7 @@ __global__ void k_tcount(const int32_t* __restrict__ rp, const int32_t* __restri
 
 __global__ void k_tfill(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, int n,
                         const int32_t* __restrict__ tptr, int32_t* cur, int32_t* tidx) {
+  COUNT_LAUNCH();
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x)
     for (int k = rp[r]; k < rp[r + 1]; ++k) {
       int c = ci[k];
@@ -54,6 +57,7 @@ __global__ void k_tfill(const int32_t* __restrict__ rp, const int32_t* __restric
 
 // insertion sort of each segment ptr[i]..ptr[i+1] (segments are short)
 __global__ void k_sort_rows(const int32_t* __restrict__ ptr, int32_t* idx, int n) {
+  COUNT_LAUNCH();
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
     int b = ptr[r], e = ptr[r + 1];
     for (int k = b + 1; k < e; ++k) {
@@ -71,6 +75,7 @@ template <bool FILL>
 __global__ void k_merge(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                         const int32_t* __restrict__ tptr, const int32_t* __restrict__ tidx, int n,
                         const int32_t* __restrict__ gptr, int32_t* out) {
+  COUNT_LAUNCH();
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
     int a = rp[r], ae = rp[r + 1], b = tptr[r], be = tptr[r + 1];
     int cnt = 0, last = -1;
@@ -90,11 +95,13 @@ __global__ void k_merge(const int32_t* __restrict__ rp, const int32_t* __restric
 
 // ---- I_i lists -----------------------------------------------------------------
 __global__ void k_part_count(const int32_t* __restrict__ part, int n, int32_t* cnt) {
+  COUNT_LAUNCH();
   for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
     atomicAdd(&cnt[part[v]], 1);
 }
 __global__ void k_part_fill(const int32_t* __restrict__ part, int n, const int32_t* __restrict__ off,
                             int32_t* cur, int32_t* list) {
+  COUNT_LAUNCH();
   for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
     int i = part[v];
     list[off[i] + atomicAdd(&cur[i], 1)] = v;
@@ -124,6 +131,7 @@ __device__ void bitonic_sort(int32_t* sh, int len) {
 
 // sort each I_i (one block per subdomain, <= MAX_NI entries)
 __global__ void k_sort_segments(const int32_t* __restrict__ off, int32_t* list) {
+  COUNT_LAUNCH();
   extern __shared__ int32_t sh[];
   int b = off[blockIdx.x], len = off[blockIdx.x + 1] - b;
   for (int k = threadIdx.x; k < len; k += blockDim.x) sh[k] = list[b + k];
@@ -143,6 +151,7 @@ __global__ void __launch_bounds__(NT) k_bfs(const int32_t* __restrict__ gptr, co
                       const int32_t* __restrict__ ilist, int delta, int32_t* lay_size,
                       const int32_t* __restrict__ sub_off, const int32_t* __restrict__ lay_off,
                       int32_t* omega, int32_t* err) {
+  COUNT_LAUNCH();
   extern __shared__ int32_t sm[];
   int32_t* tab = sm;
   int32_t* buf[3] = {sm + OV_HASH, sm + OV_HASH + OV_LAYER, sm + OV_HASH + 2 * OV_LAYER};
@@ -212,6 +221,7 @@ __global__ void __launch_bounds__(NT) k_bfs(const int32_t* __restrict__ gptr, co
 // s_v = 1 / sqrt(|A_vv|) (1 if the diagonal is absent or zero).
 __global__ void k_diag_scale(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                              const double* __restrict__ val, int n, double* __restrict__ ds) {
+  COUNT_LAUNCH();
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
     int k = bsearch_i32(ci, rp[r], rp[r + 1], r);
     double d = k >= 0 ? fabs(val[k]) : 0.0;
@@ -220,16 +230,19 @@ __global__ void k_diag_scale(const int32_t* __restrict__ rp, const int32_t* __re
 }
 
 __global__ void k_pos_sub(const int32_t* __restrict__ sub_off, int32_t* pos_sub) {
+  COUNT_LAUNCH();
   int i = blockIdx.x;
   for (int k = sub_off[i] + threadIdx.x; k < sub_off[i + 1]; k += blockDim.x) pos_sub[k] = i;
 }
 
 __global__ void k_occ_count(const int32_t* __restrict__ omega, int64_t m, int32_t* cnt) {
+  COUNT_LAUNCH();
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < m; k += (int64_t)gridDim.x * blockDim.x)
     atomicAdd(&cnt[omega[k]], 1);
 }
 __global__ void k_occ_fill(const int32_t* __restrict__ omega, int64_t m, const int32_t* __restrict__ ptr,
                            int32_t* cur, int32_t* pos) {
+  COUNT_LAUNCH();
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < m; k += (int64_t)gridDim.x * blockDim.x) {
     int v = omega[k];
     pos[ptr[v] + atomicAdd(&cur[v], 1)] = (int32_t)k;
@@ -238,6 +251,7 @@ __global__ void k_occ_fill(const int32_t* __restrict__ omega, int64_t m, const i
 
 __global__ void k_own_pos(const int32_t* __restrict__ sub_off, const int32_t* __restrict__ lay_off,
                           int delta, const int32_t* __restrict__ omega, int32_t* own) {
+  COUNT_LAUNCH();
   int i = blockIdx.x;
   int b = sub_off[i], p = lay_off[i * (delta + 2) + 1];
   for (int a = threadIdx.x; a < p; a += blockDim.x) own[omega[b + a]] = b + a;
@@ -245,6 +259,7 @@ __global__ void k_own_pos(const int32_t* __restrict__ sub_off, const int32_t* __
 
 __global__ void k_rowlen(const int32_t* __restrict__ omega, int64_t m, const int32_t* __restrict__ rp,
                          int64_t* len) {
+  COUNT_LAUNCH();
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < m; k += (int64_t)gridDim.x * blockDim.x) {
     int v = omega[k];
     len[k] = rp[v + 1] - rp[v];
@@ -257,6 +272,7 @@ __global__ void k_lcol(const int32_t* __restrict__ omega, int64_t m, const int32
                        const int32_t* __restrict__ ci, const int32_t* __restrict__ occ_ptr,
                        const int32_t* __restrict__ occ_pos, const int64_t* __restrict__ ent_off,
                        int32_t* lcol) {
+  COUNT_LAUNCH();
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < m; k += (int64_t)gridDim.x * blockDim.x) {
     int v = omega[k], i = pos_sub[k];
     int lo = sub_off[i], hi = sub_off[i + 1];

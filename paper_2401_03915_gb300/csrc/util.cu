@@ -5,6 +5,24 @@ namespace asmgpu {
 
 [[noreturn]] void fail(asm_status s, const std::string& msg) { throw AsmError{s, msg}; }
 
+namespace {
+std::vector<unsigned long long (*)()>& counters() {
+  static std::vector<unsigned long long (*)()> v;
+  return v;
+}
+}  // namespace
+
+int register_launch_counter(unsigned long long (*reader)()) {
+  counters().push_back(reader);
+  return (int)counters().size();
+}
+
+unsigned long long total_kernel_launches() {
+  unsigned long long t = 0;
+  for (auto f : counters()) t += f();
+  return t;
+}
+
 void cuda_check(cudaError_t e, const char* what, const char* file, int line) {
   if (e == cudaSuccess) return;
   cudaGetLastError();
@@ -20,6 +38,7 @@ constexpr int SCAN_CHUNK = SCAN_THREADS * SCAN_PER_THREAD;  // elements per bloc
 
 template <typename In>
 __global__ void k_chunk_sums(const In* __restrict__ in, int64_t n, int64_t* __restrict__ sums) {
+  COUNT_LAUNCH();
   __shared__ int64_t sh[SCAN_THREADS / 32];
   int64_t base = (int64_t)blockIdx.x * SCAN_CHUNK;
   int64_t acc = 0;
@@ -33,6 +52,7 @@ __global__ void k_chunk_sums(const In* __restrict__ in, int64_t n, int64_t* __re
 
 // Exclusive scan of up to SCAN_THREADS * 32 block sums in one block.
 __global__ void k_scan_sums(int64_t* sums, int64_t nb) {
+  COUNT_LAUNCH();
   __shared__ int64_t sh[SCAN_THREADS];
   const int per = (int)ceil_div(nb, SCAN_THREADS);
   int64_t local = 0;
@@ -62,6 +82,7 @@ __global__ void k_scan_sums(int64_t* sums, int64_t nb) {
 template <typename In, typename Out>
 __global__ void k_chunk_scan(const In* __restrict__ in, int64_t n, const int64_t* __restrict__ sums,
                              Out* __restrict__ out) {
+  COUNT_LAUNCH();
   __shared__ int64_t sh[SCAN_THREADS];
   int64_t base = (int64_t)blockIdx.x * SCAN_CHUNK + (int64_t)threadIdx.x * SCAN_PER_THREAD;
   int64_t v[SCAN_PER_THREAD];
