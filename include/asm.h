@@ -80,7 +80,9 @@ typedef struct {
   uint64_t seed;            /* counter-based random start of the iteration     */
   int32_t warm_start;       /* 1: predict the start block with the network set
                                by asm_set_warm_start                           */
-  int32_t reserved[7];
+  int32_t filter_degree;    /* Chebyshev filter degree between Rayleigh-Ritz
+                               steps of the subspace iteration (0: 4)          */
+  int32_t reserved[6];
 } asm_options;
 
 typedef struct {

@@ -38,7 +38,7 @@ class asm_options(C.Structure):
     _fields_ = [("spd", C.c_int32), ("local_precision", C.c_int32), ("oversample", C.c_int32),
                 ("max_sweeps", C.c_int32), ("eig_tol", C.c_double), ("nu", C.c_double),
                 ("nev_lift", C.c_int32), ("coarse", C.c_int32), ("seed", C.c_uint64),
-                ("warm_start", C.c_int32), ("reserved", C.c_int32 * 7)]
+                ("warm_start", C.c_int32), ("filter_degree", C.c_int32), ("reserved", C.c_int32 * 6)]
 
 
 class asm_solve_opts(C.Structure):

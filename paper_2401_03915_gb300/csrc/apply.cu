@@ -102,7 +102,9 @@ __global__ void __launch_bounds__(NT) k_apply_tiles(const T* __restrict__ tiles,
   }
 }
 
-// c[col_off[i] + j] = sum_{a < p_i} Z_i[a][j] r[omega_i[a]]  (Z^T r)
+// c[col_off[i] + j] = sum_{a < p_i} Z_i[a][j] r[omega_i[a]]  (Z^T r).
+// Thread (g, c) of the block sums rows a = g, g + 16, ... of column j0 + c;
+// the 16 row groups are added in a fixed order.
 __global__ void __launch_bounds__(NT) k_coarse_restrict(const double* __restrict__ Z, const int64_t* __restrict__ z_off,
                                                         const int32_t* __restrict__ count,
                                                         const int32_t* __restrict__ col_off,
@@ -113,47 +115,54 @@ __global__ void __launch_bounds__(NT) k_coarse_restrict(const double* __restrict
                                                         const int32_t* __restrict__ done) {
   COUNT_LAUNCH();
   if (done != nullptr && *done) return;
-  __shared__ double red[NT / 32][32];
+  __shared__ double red[16][17];
   const int i = blockIdx.x;
   const int k = count[i], p = p_arr[i], b0 = sub_off[i];
   const double* Zi = Z + z_off[i];
-  for (int j0 = 0; j0 < k; j0 += 32) {
-    double acc[32];
-#pragma unroll
-    for (int q = 0; q < 32; ++q) acc[q] = 0;
-    for (int a = threadIdx.x; a < p; a += NT) {
-      double x = r[omega[b0 + a]];
-      const double* zr = Zi + (int64_t)a * nev + j0;
-#pragma unroll
-      for (int q = 0; q < 32; ++q)
-        if (j0 + q < k) acc[q] += zr[q] * x;
-    }
-#pragma unroll
-    for (int q = 0; q < 32; ++q) {
-      double s = warp_sum(acc[q]);
-      if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][q] = s;
-    }
+  const int g = threadIdx.x >> 4, cc = threadIdx.x & 15;
+  for (int j0 = 0; j0 < k; j0 += 16) {
+    double acc = 0;
+    if (j0 + cc < k)
+      for (int a = g; a < p; a += 16) acc += Zi[(int64_t)a * nev + j0 + cc] * r[omega[b0 + a]];
+    red[g][cc] = acc;
     __syncthreads();
-    if (threadIdx.x < 32 && j0 + threadIdx.x < k) {
+    if (threadIdx.x < 16 && j0 + threadIdx.x < k) {
       double s = 0;
-      for (int w = 0; w < NT / 32; ++w) s += red[w][threadIdx.x];
+      for (int q = 0; q < 16; ++q) s += red[q][threadIdx.x];
       c[col_off[i] + j0 + threadIdx.x] = s;
     }
     __syncthreads();
   }
 }
 
-// z[v] = sum over the occurrences (i, a) of v of sum_J partial[i][a/TILE][J][a%TILE]
-//        + Z_{part v}[own position] . y_coarse
+// y_pos[k] = sum_J partial[i][a/TILE][J][a%TILE] for every omega position k = (i, a)
 template <typename T>
+__global__ void __launch_bounds__(NT) k_reduce_partials(int64_t m, const int32_t* __restrict__ pos_sub,
+                                                        const int32_t* __restrict__ sub_off,
+                                                        const int32_t* __restrict__ nt_arr,
+                                                        const int64_t* __restrict__ part_off,
+                                                        const T* __restrict__ partials, double* __restrict__ ypos,
+                                                        const int32_t* __restrict__ done) {
+  COUNT_LAUNCH();
+  if (done != nullptr && *done) return;
+  for (int64_t k = blockIdx.x * (int64_t)NT + threadIdx.x; k < m; k += (int64_t)gridDim.x * NT) {
+    const int i = pos_sub[k];
+    const int a = (int)(k - sub_off[i]);
+    const int nt = nt_arr[i];
+    const T* P = partials + part_off[i] + (int64_t)(a / TILE) * nt * TILE + (a % TILE);
+    double s = 0;
+    for (int J = 0; J < nt; ++J) s += (double)P[(int64_t)J * TILE];
+    ypos[k] = s;
+  }
+}
+
+// z[v] = s_v * sum over the occurrences (i, a) of v of y_pos[(i, a)]
+//        + Z_{part v}[own position] . y_coarse   (fixed order, no atomics)
 __global__ void __launch_bounds__(NT) k_apply_pull(int n, const int32_t* __restrict__ occ_ptr,
                                                    const int32_t* __restrict__ occ_pos,
-                                                   const int32_t* __restrict__ pos_sub,
-                                                   const int32_t* __restrict__ sub_off,
-                                                   const int32_t* __restrict__ nt_arr,
-                                                   const int64_t* __restrict__ part_off,
-                                                   const T* __restrict__ partials, const int32_t* __restrict__ part,
-                                                   const int32_t* __restrict__ own_pos, const double* __restrict__ Z,
+                                                   const double* __restrict__ ypos, const int32_t* __restrict__ part,
+                                                   const int32_t* __restrict__ own_pos,
+                                                   const int32_t* __restrict__ sub_off, const double* __restrict__ Z,
                                                    const int64_t* __restrict__ z_off, const int32_t* __restrict__ count,
                                                    const int32_t* __restrict__ col_off, int nev,
                                                    const double* __restrict__ yc, const double* __restrict__ ds,
@@ -162,16 +171,7 @@ __global__ void __launch_bounds__(NT) k_apply_pull(int n, const int32_t* __restr
   if (done != nullptr && *done) return;
   for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
     double acc = 0;
-    for (int t = occ_ptr[v]; t < occ_ptr[v + 1]; ++t) {
-      int q = occ_pos[t];
-      int i = pos_sub[q];
-      int a = q - sub_off[i];
-      int nt = nt_arr[i];
-      const T* P = partials + part_off[i] + (int64_t)(a / TILE) * nt * TILE + (a % TILE);
-      double s = 0;
-      for (int J = 0; J < nt; ++J) s += (double)P[(int64_t)J * TILE];
-      acc += s;
-    }
+    for (int t = occ_ptr[v]; t < occ_ptr[v + 1]; ++t) acc += ypos[occ_pos[t]];
     acc *= ds[v];
     if (yc != nullptr) {
       int i = part[v];
@@ -180,7 +180,14 @@ __global__ void __launch_bounds__(NT) k_apply_pull(int n, const int32_t* __restr
         const double* zr = Z + z_off[i] + (int64_t)(own_pos[v] - sub_off[i]) * nev;
         const double* y = yc + col_off[i];
         double s = 0;
-        for (int j = 0; j < k; ++j) s += zr[j] * y[j];
+        int j = 0;
+        if ((nev & 1) == 0) {
+          for (; j + 1 < k; j += 2) {
+            double2 zz = *reinterpret_cast<const double2*>(zr + j);
+            s += zz.x * y[j] + zz.y * y[j + 1];
+          }
+        }
+        for (; j < k; ++j) s += zr[j] * y[j];
         acc += s;
       }
     }
@@ -218,10 +225,12 @@ template <typename T>
 void apply_pull(Handle& h, const double* yc, double* z, cudaStream_t s, const int32_t* done) {
   Dense& dn = h.dn;
   Coarse& co = h.co;
+  unsigned gr = (unsigned)std::min<int64_t>(ceil_div(h.ov.sum_n, NT), 152 * 16);
+  k_reduce_partials<T><<<gr, NT, 0, s>>>(h.ov.sum_n, h.ov.pos_sub, h.ov.sub_off, dn.nt, dn.part_off,
+                                         (const T*)dn.partials, dn.ypos, done);
   unsigned gp = (unsigned)std::min<int64_t>(ceil_div(h.n, NT), 152 * 16);
-  k_apply_pull<T><<<gp, NT, 0, s>>>(h.n, h.ov.occ_ptr, h.ov.occ_pos, h.ov.pos_sub, h.ov.sub_off, dn.nt, dn.part_off,
-                                    (const T*)dn.partials, h.part, h.ov.own_pos, co.Z, co.z_off, co.count,
-                                    co.col_off, h.nev, yc, h.dscale, z, done);
+  k_apply_pull<<<gp, NT, 0, s>>>(h.n, h.ov.occ_ptr, h.ov.occ_pos, dn.ypos, h.part, h.ov.own_pos, h.ov.sub_off,
+                                 co.Z, co.z_off, co.count, co.col_off, h.nev, yc, h.dscale, z, done);
 }
 
 template <typename T>

@@ -95,13 +95,14 @@ void asm_default_options(asm_options* o) {
   o->spd = 1;
   o->local_precision = ASM_PREC_FP64;
   o->oversample = 8;
-  o->max_sweeps = 0;  // 0: 60
+  o->max_sweeps = 0;  // 0: 40
   o->eig_tol = 0;     // 0: 1e-8 (FP64) / 1e-3 (FP32)
   o->nu = 0;
   o->nev_lift = 0;
   o->coarse = 1;
   o->seed = 0;
   o->warm_start = 0;
+  o->filter_degree = 0;  // 0: 4
 }
 
 void asm_default_solve_opts(asm_solve_opts* o) {

@@ -224,6 +224,7 @@ __device__ void assemble_rhs(const FrontDev& f, const FrontDev* __restrict__ fr,
 }
 
 // Forward: task (front, B row tile) computes u rows; tile -1 stores f_V.
+// Four blocks per task, 16 rows each; a warp reads a row contiguously.
 __global__ void __launch_bounds__(NT) k_front_forward(const FrontDev* __restrict__ fr, const int2* __restrict__ tasks,
                                                       const int32_t* __restrict__ dofs,
                                                       const int32_t* __restrict__ children,
@@ -233,36 +234,29 @@ __global__ void __launch_bounds__(NT) k_front_forward(const FrontDev* __restrict
   COUNT_LAUNCH();
   if (done != nullptr && *done) return;
   extern __shared__ double sf[];
-  __shared__ double red[NT / 32][FB];
-  const int2 tk = tasks[blockIdx.x];
+  const int2 tk = tasks[blockIdx.x >> 2];
+  const int quarter = blockIdx.x & 3;
   const FrontDev f = fr[tk.x];
+  if (tk.y < 0 && quarter != 0) return;
   assemble_rhs(f, fr, dofs + f.dof_off, children, invmap, vecs, c, sf);
   double* vec = vecs + f.vec_off;
   if (tk.y < 0) {
     for (int a = threadIdx.x; a < f.nvp; a += NT) vec[a] = sf[a];
     return;
   }
-  // u[r] = f_B[r] + sum_q M[nvp + r][q] f_V[q]; warp w takes q = w, w + 8, ... ; lane = row pair
   const double* F = M + f.mat_off;
-  const int r0 = tk.y * FB;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  double a0 = 0, a1 = 0;
-  for (int q = wid; q < f.nvp; q += NT / 32) {
-    double x = sf[q];
-    a0 += F[(int64_t)(f.nvp + r0 + lane) * f.m + q] * x;
-    a1 += F[(int64_t)(f.nvp + r0 + lane + 32) * f.m + q] * x;
-  }
-  red[wid][lane] = a0;
-  red[wid][lane + 32] = a1;
-  __syncthreads();
-  if (threadIdx.x < FB) {
-    double s = sf[f.nvp + r0 + threadIdx.x];
-    for (int w = 0; w < NT / 32; ++w) s += red[w][threadIdx.x];
-    vec[f.nvp + r0 + threadIdx.x] = s;
+  for (int rr = wid; rr < FB / 4; rr += NT / 32) {
+    const int r = tk.y * FB + quarter * (FB / 4) + rr;
+    const double* row = F + (int64_t)(f.nvp + r) * f.m;
+    double acc = 0;
+    for (int q = lane; q < f.nvp; q += 32) acc += row[q] * sf[q];
+    acc = warp_sum(acc);
+    if (lane == 0) vec[f.nvp + r] = sf[f.nvp + r] + acc;
   }
 }
 
-// Backward: task (front, V row tile): y_V = M_VV f_V - M_VB y_B.
+// Backward: task (front, V row tile): y_V = M_VV f_V - M_VB y_B; four blocks per task.
 __global__ void __launch_bounds__(NT) k_front_backward(const FrontDev* __restrict__ fr, const int2* __restrict__ tasks,
                                                        const int32_t* __restrict__ dofs, const double* __restrict__ M,
                                                        const double* __restrict__ vecs, double* __restrict__ y,
@@ -270,8 +264,8 @@ __global__ void __launch_bounds__(NT) k_front_backward(const FrontDev* __restric
   COUNT_LAUNCH();
   if (done != nullptr && *done) return;
   extern __shared__ double sx[];  // [f_V ; -y_B]
-  __shared__ double red[NT / 32][FB];
-  const int2 tk = tasks[blockIdx.x];
+  const int2 tk = tasks[blockIdx.x >> 2];
+  const int quarter = blockIdx.x & 3;
   const FrontDev f = fr[tk.x];
   const int32_t* dof = dofs + f.dof_off;
   const double* vec = vecs + f.vec_off;
@@ -281,22 +275,15 @@ __global__ void __launch_bounds__(NT) k_front_backward(const FrontDev* __restric
   }
   __syncthreads();
   const double* F = M + f.mat_off;
-  const int r0 = tk.y * FB;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  double a0 = 0, a1 = 0;
-  for (int q = wid; q < f.m; q += NT / 32) {
-    double x = sx[q];
-    a0 += F[(int64_t)(r0 + lane) * f.m + q] * x;
-    a1 += F[(int64_t)(r0 + lane + 32) * f.m + q] * x;
-  }
-  red[wid][lane] = a0;
-  red[wid][lane + 32] = a1;
-  __syncthreads();
-  if (threadIdx.x < FB) {
-    double s = 0;
-    for (int w = 0; w < NT / 32; ++w) s += red[w][threadIdx.x];
-    int d = dof[r0 + threadIdx.x];
-    if (d >= 0) y[d] = s;
+  for (int rr = wid; rr < FB / 4; rr += NT / 32) {
+    const int r = tk.y * FB + quarter * (FB / 4) + rr;
+    const double* row = F + (int64_t)r * f.m;
+    double acc = 0;
+    for (int q = lane; q < f.m; q += 32) acc += row[q] * sx[q];
+    acc = warp_sum(acc);
+    const int d = dof[r];
+    if (lane == 0 && d >= 0) y[d] = acc;
   }
 }
 
@@ -605,12 +592,12 @@ void nd_solve(Handle& h, const double* c, double* y, cudaStream_t s, const int32
   const size_t smem = sizeof(double) * std::max(nd.max_m, 1);
   for (int L = 0; L < nd.nlevels; ++L) {
     int nf = nd.lv_fwd[L + 1] - nd.lv_fwd[L];
-    if (nf) k_front_forward<<<nf, NT, smem, s>>>(nd.fr, nd.t_fwd + nd.lv_fwd[L], nd.dofs, nd.children, nd.invmap,
+    if (nf) k_front_forward<<<4 * nf, NT, smem, s>>>(nd.fr, nd.t_fwd + nd.lv_fwd[L], nd.dofs, nd.children, nd.invmap,
                                                  nd.M, nd.vecs, c, done);
   }
   for (int L = nd.nlevels - 1; L >= 0; --L) {
     int nb = nd.lv_bwd[L + 1] - nd.lv_bwd[L];
-    if (nb) k_front_backward<<<nb, NT, smem, s>>>(nd.fr, nd.t_bwd + nd.lv_bwd[L], nd.dofs, nd.M, nd.vecs, y, done);
+    if (nb) k_front_backward<<<4 * nb, NT, smem, s>>>(nd.fr, nd.t_bwd + nd.lv_bwd[L], nd.dofs, nd.M, nd.vecs, y, done);
   }
 }
 

@@ -1,25 +1,28 @@
-// Local coarse vectors by randomized block subspace iteration, one block per
-// subdomain, all subdomains in one launch.
+// Local coarse vectors by randomized block subspace iteration with Chebyshev
+// acceleration, one block per subdomain, all subdomains in one launch.
 //
 // SPD (eq. gevpsvd, Section 5.1).  With X = -B^{-1}C, X_p its first |I_i| rows,
 // S = G - C^T B^{-1} C and K = X_p^T A_{I_i,I_i} X_p, every eigenpair of
 // eq. gevpsvd with lambda^2 > 0 satisfies K y = lambda^2 S y with y = w_Gamma,
 // the A_ii-normalisation of w is the S-normalisation of y, and the coarse
 // vector R_i^T D_i Pi_i w is [X_p y; 0] on Omega_{I_i}.  The iteration runs on
-// S^{-1} K (S^{-1} is the trailing block of A_ii^{-1} left by the sweep) with
-// S-orthonormal blocks and Rayleigh-Ritz on Y^T K Y.
+// OP = S^{-1} K (S^{-1} is the trailing block of A_ii^{-1} left by the sweep)
+// with S-orthonormal blocks and Rayleigh-Ritz on Y^T K Y.
 //
-// General A (Section 5 of the paper's nonsymmetric extension).  D_i Pi_i is
-// nonzero only in rows I_i and columns Gamma_delta, where it equals X_p, so
-// its left singular vectors are those of X_p: the iteration runs on
-// X_p X_p^T with Euclidean orthonormal blocks, and the kept vectors are the
-// coarse vectors themselves.  The Euclidean SVD is not invariant under the
-// diagonal scaling of the local sweep, so here the scaling is undone inside
-// the products with X_p.
+// General A (the paper's nonsymmetric extension).  D_i Pi_i is nonzero only
+// in rows I_i and columns Gamma_delta, where it equals X_p, so its left
+// singular vectors are those of X_p: the iteration runs on OP = X_p X_p^T
+// with Euclidean orthonormal blocks, and the kept vectors are the coarse
+// vectors themselves.  The Euclidean SVD is not invariant under the diagonal
+// scaling of the local sweep, so the scaling is undone inside the products
+// with X_p.
 //
-// Each sweep: power step, CholQR2 re-orthonormalisation (Gram in FP64),
-// Rayleigh-Ritz with a cyclic Jacobi eigensolver (Golub & Van Loan, Alg.
-// 8.5.3) of the small projected matrix, and a relative eigen-residual test.
+// One sweep: Rayleigh-Ritz (cyclic Jacobi on the projected s x s matrix,
+// Golub & Van Loan Alg. 8.5.3), relative eigen-residual test, then a
+// degree-d Chebyshev polynomial in OP that damps the part of the spectrum
+// below the smallest Ritz value of the block (scaled three-term recurrence of
+// Zhou & Saad, 2007), and CholQR2 re-orthonormalisation.  Dense block
+// products go through a shared-memory tiled CTA GEMM.
 #include <algorithm>
 
 #include "handle.cuh"
@@ -28,183 +31,108 @@ namespace asmgpu {
 namespace {
 
 constexpr int NT = 256;
-constexpr int NW = NT / 32;
-constexpr int JC = 16;  // column chunk held in registers
+constexpr int GM = 128;  // rows per CTA-GEMM tile
+constexpr int GK = 32;   // K chunk
+constexpr int GN = 32;   // columns per pass
 
-struct SubdomainView {
-  int n, m, p, g, ld;
-  const void* XpT;
-  const void* S;
-  const void* R;  // S^{-1}: trailing block of A_ii^{-1} (ld = padded size)
-  int64_t ent0;   // first entry of row 0 of Omega_i in the local CSR
-  int pos0;       // omega position of row 0
-};
-
-// Diagonal scalings of the general path: X_p = S_I X^_p S_G^{-1}, where X^_p
-// comes from the scaled sweep and S = D^{-1/2}.  Null pointers: no scaling.
-struct XScale {
+// Optional diagonal scalings (general path): factor for index q.
+struct Scale {
   const double* ds = nullptr;
-  const int32_t* omI = nullptr;   // omega of I_i
-  const int32_t* omG = nullptr;   // omega of Gamma_delta
-  __device__ double sI(int r) const { return ds ? ds[omI[r]] : 1.0; }
-  __device__ double sG(int k) const { return ds ? ds[omG[k]] : 1.0; }
+  const int32_t* om = nullptr;
+  __device__ double operator()(int q) const { return ds ? ds[om[q]] : 1.0; }
+  __device__ bool on() const { return ds != nullptr; }
 };
 
-// V (p x s) = X_p Y (Y: g x s); XpT is g x p row-major.
-template <typename T>
-__device__ void mul_Xp(const T* __restrict__ XpT, int p, int g, const T* __restrict__ Y, T* __restrict__ V, int s,
-                       int ncols, XScale sc = XScale()) {
-  for (int r = threadIdx.x; r < p; r += NT) {
-    for (int j0 = 0; j0 < ncols; j0 += JC) {
-      T acc[JC];
+// C (M x N, ldc) = A (M x K) B (K x N, ldb); A row-major (A[m*lda + k]) or,
+// with ACOL, column-major (A[k*lda + m]).  C row m is multiplied by rs(m);
+// A's column k by ks(k) (or divided, with kinv).
+template <typename T, bool ACOL>
+__device__ void cta_gemm(int M, int N, int K, const T* __restrict__ A, int lda, const T* __restrict__ B, int ldb,
+                         T* __restrict__ C, int ldc, T* sm, Scale rs = Scale(), Scale ks = Scale(), bool kinv = false) {
+  T* As = sm;                  // GM x (GK + 1)
+  T* Bs = sm + GM * (GK + 1);  // GK x GN
+  const int t = threadIdx.x, row = t % GM, cg = t / GM;  // 2 column groups of 16
+  for (int n0 = 0; n0 < N; n0 += GN) {
+    const int nw = min(GN, N - n0);
+    for (int m0 = 0; m0 < M; m0 += GM) {
+      T acc[16];
 #pragma unroll
-      for (int q = 0; q < JC; ++q) acc[q] = 0;
-      for (int k = 0; k < g; ++k) {
-        T x = XpT[(int64_t)k * p + r];
-        if (sc.ds) x = (T)((double)x / sc.sG(k));
-        const T* y = Y + (int64_t)k * s + j0;
+      for (int q = 0; q < 16; ++q) acc[q] = 0;
+      for (int k0 = 0; k0 < K; k0 += GK) {
+        __syncthreads();
+        if (!ACOL) {
+          for (int idx = t; idx < GM * GK; idx += NT) {
+            int r = idx / GK, kk = idx % GK;
+            T v = (m0 + r < M && k0 + kk < K) ? A[(int64_t)(m0 + r) * lda + k0 + kk] : T(0);
+            if (ks.on() && k0 + kk < K) v = (T)(kinv ? (double)v / ks(k0 + kk) : (double)v * ks(k0 + kk));
+            As[r * (GK + 1) + kk] = v;
+          }
+        } else {
+          for (int idx = t; idx < GM * GK; idx += NT) {
+            int kk = idx / GM, r = idx % GM;
+            T v = (m0 + r < M && k0 + kk < K) ? A[(int64_t)(k0 + kk) * lda + m0 + r] : T(0);
+            if (ks.on() && k0 + kk < K) v = (T)(kinv ? (double)v / ks(k0 + kk) : (double)v * ks(k0 + kk));
+            As[r * (GK + 1) + kk] = v;
+          }
+        }
+        for (int idx = t; idx < GK * GN; idx += NT) {
+          int kk = idx / GN, c = idx % GN;
+          Bs[idx] = (k0 + kk < K && c < nw) ? B[(int64_t)(k0 + kk) * ldb + n0 + c] : T(0);
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int kk = 0; kk < GK; ++kk) {
+          const T a = As[row * (GK + 1) + kk];
+          const T* b = Bs + kk * GN + cg * 16;
 #pragma unroll
-        for (int q = 0; q < JC; ++q)
-          if (j0 + q < ncols) acc[q] += x * y[q];
+          for (int q = 0; q < 16; ++q) acc[q] += a * b[q];
+        }
       }
-      const T f = (T)sc.sI(r);
+      if (m0 + row < M) {
+        const T f = rs.on() ? (T)rs(m0 + row) : T(1);
 #pragma unroll
-      for (int q = 0; q < JC; ++q)
-        if (j0 + q < ncols) V[(int64_t)r * s + j0 + q] = acc[q] * f;
+        for (int q = 0; q < 16; ++q) {
+          int c = cg * 16 + q;
+          if (c < nw) C[(int64_t)(m0 + row) * ldc + n0 + c] = acc[q] * f;
+        }
+      }
     }
-  }
-}
-
-// W (g x s) = X_p^T V (V: p x s): one warp per output row.
-template <typename T>
-__device__ void mul_XpT(const T* __restrict__ XpT, int p, int g, const T* __restrict__ V, T* __restrict__ W, int s,
-                        XScale sc = XScale()) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int k = wid; k < g; k += NW) {
-    const T* xr = XpT + (int64_t)k * p;
-    for (int j0 = 0; j0 < s; j0 += JC) {
-      T acc[JC];
-#pragma unroll
-      for (int q = 0; q < JC; ++q) acc[q] = 0;
-      for (int r = lane; r < p; r += 32) {
-        T x = xr[r];
-        if (sc.ds) x = (T)((double)x * sc.sI(r));
-        const T* v = V + (int64_t)r * s + j0;
-#pragma unroll
-        for (int q = 0; q < JC; ++q)
-          if (j0 + q < s) acc[q] += x * v[q];
-      }
-      const T f = (T)(1.0 / sc.sG(k));
-#pragma unroll
-      for (int q = 0; q < JC; ++q) {
-        T t = warp_sum(acc[q]);
-        if (lane == 0 && j0 + q < s) W[(int64_t)k * s + j0 + q] = t * f;
-      }
-    }
-  }
-}
-
-// AV (p x s) = A_{I,I} V, from the local CSR (columns < p).
-template <typename T>
-__device__ void mul_AII(const SubdomainView& sv, const int32_t* __restrict__ omega, const int32_t* __restrict__ rp,
-                        const int32_t* __restrict__ ci, const double* __restrict__ val,
-                        const double* __restrict__ ds, const int64_t* __restrict__ ent_off,
-                        const int32_t* __restrict__ lcol, const T* __restrict__ V, T* __restrict__ AV, int s) {
-  for (int a = threadIdx.x; a < sv.p; a += NT) {
-    int v = omega[sv.pos0 + a];
-    int b = rp[v], e = rp[v + 1];
-    const double sv_ = ds[v];
-    int64_t e0 = ent_off[sv.pos0 + a];
-    for (int j0 = 0; j0 < s; j0 += JC) {
-      T acc[JC];
-#pragma unroll
-      for (int q = 0; q < JC; ++q) acc[q] = 0;
-      for (int t = 0; t < e - b; ++t) {
-        int lc = lcol[e0 + t];
-        if (lc < 0 || lc >= sv.p) continue;
-        T w = (T)(val[b + t] * sv_ * ds[ci[b + t]]);
-        const T* vr = V + (int64_t)lc * s + j0;
-#pragma unroll
-        for (int q = 0; q < JC; ++q)
-          if (j0 + q < s) acc[q] += w * vr[q];
-      }
-#pragma unroll
-      for (int q = 0; q < JC; ++q)
-        if (j0 + q < s) AV[(int64_t)a * s + j0 + q] = acc[q];
-    }
-  }
-}
-
-// W (g x s) = Mat Y for a symmetric g x g Mat with leading dimension ld
-// (read by columns so that consecutive threads read consecutive addresses).
-template <typename T>
-__device__ void mul_sym(const T* __restrict__ Mat, int ld, int g, const T* __restrict__ Y, T* __restrict__ W, int s) {
-  for (int k = threadIdx.x; k < g; k += NT) {
-    for (int j0 = 0; j0 < s; j0 += JC) {
-      T acc[JC];
-#pragma unroll
-      for (int q = 0; q < JC; ++q) acc[q] = 0;
-      for (int t = 0; t < g; ++t) {
-        T mv = Mat[(int64_t)t * ld + k];
-        const T* y = Y + (int64_t)t * s + j0;
-#pragma unroll
-        for (int q = 0; q < JC; ++q)
-          if (j0 + q < s) acc[q] += mv * y[q];
-      }
-#pragma unroll
-      for (int q = 0; q < JC; ++q)
-        if (j0 + q < s) W[(int64_t)k * s + j0 + q] = acc[q];
-    }
-  }
-}
-
-// G (s x s, FP64, shared) = A^T B over L rows.
-template <typename T>
-__device__ void gram(const T* __restrict__ A, const T* __restrict__ B, int L, int s, double* G) {
-  const int npair = s * s;
-  for (int idx = threadIdx.x; idx < npair; idx += NT) {
-    int t = idx / s, u = idx % s;
-    double acc = 0;
-    for (int r = 0; r < L; ++r) acc += (double)A[(int64_t)r * s + t] * (double)B[(int64_t)r * s + u];
-    G[idx] = acc;
   }
   __syncthreads();
 }
 
-// OUT (L x s) = IN (L x s) * Mat (s x s, shared, FP64 or T), rows in parallel.
-template <typename T, typename MT>
-__device__ void right_mul(const T* __restrict__ IN, T* __restrict__ OUT, int L, int s, const MT* Mat) {
-  for (int r = threadIdx.x; r < L; r += NT) {
-    const T* in = IN + (int64_t)r * s;
-    for (int j0 = 0; j0 < s; j0 += JC) {
-      MT acc[JC];
-#pragma unroll
-      for (int q = 0; q < JC; ++q) acc[q] = 0;
-      for (int l = 0; l < s; ++l) {
-        MT x = (MT)in[l];
-#pragma unroll
-        for (int q = 0; q < JC; ++q)
-          if (j0 + q < s) acc[q] += x * Mat[l * s + j0 + q];
-      }
-#pragma unroll
-      for (int q = 0; q < JC; ++q)
-        if (j0 + q < s) OUT[(int64_t)r * s + j0 + q] = (T)acc[q];
+// AV (p x s) = A^_{I,I} V from the local CSR (columns < p), scaled values.
+template <typename T>
+__device__ void mul_AII(int p, int pos0, const int32_t* __restrict__ omega, const int32_t* __restrict__ rp,
+                        const int32_t* __restrict__ ci, const double* __restrict__ val, const double* __restrict__ ds,
+                        const int64_t* __restrict__ ent_off, const int32_t* __restrict__ lcol, const T* __restrict__ V,
+                        T* __restrict__ AV, int s, int sp) {
+  for (int idx = threadIdx.x; idx < p * s; idx += NT) {
+    const int a = idx / s, j = idx % s;
+    const int v = omega[pos0 + a];
+    const int b = rp[v], e = rp[v + 1];
+    const double sv = ds[v];
+    const int64_t e0 = ent_off[pos0 + a];
+    T acc = 0;
+    for (int q = 0; q < e - b; ++q) {
+      const int lc = lcol[e0 + q];
+      if (lc < 0 || lc >= p) continue;
+      acc += (T)(val[b + q] * sv * ds[ci[b + q]]) * V[(int64_t)lc * sp + j];
     }
+    AV[(int64_t)a * sp + j] = acc;
   }
   __syncthreads();
 }
 
 // Cholesky of the s x s Gram matrix G (warp 0), then Minv = L^{-T} so that
-// Y <- Y Minv is orthonormal in the metric of G.  Returns false if a pivot
-// is not positive (dependent block).
-__device__ bool chol_inv_t(double* G, double* Minv, int s, int* flag) {
+// Y <- Y Minv is orthonormal in the metric of G.
+__device__ void chol_inv_t(double* G, double* Minv, int s) {
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x;
-    int ok = 1;
     for (int j = 0; j < s; ++j) {
       double d = G[j * s + j];
       for (int k = 0; k < j; ++k) d -= G[j * s + k] * G[j * s + k];
-      if (!(d > 0)) { ok = 0; d = 1e-300; }
+      if (!(d > 0)) d = 1e-300;
       d = sqrt(d);
       __syncwarp();
       for (int r = j + 1 + lane; r < s; r += 32) {
@@ -216,17 +144,15 @@ __device__ bool chol_inv_t(double* G, double* Minv, int s, int* flag) {
       if (lane == 0) G[j * s + j] = d;
       __syncwarp();
     }
-    // lower-triangular inverse, column by column (lane = column)
     for (int c = lane; c < s; c += 32) {
       for (int r = 0; r < s; ++r) Minv[r * s + c] = 0;
       for (int r = c; r < s; ++r) {
         double v = (r == c) ? 1.0 : 0.0;
-        for (int k = c; k < r; ++k) v -= G[r * s + k] * Minv[k * s + c];  // Minv holds L^{-1} temporarily as [r][c]
+        for (int k = c; k < r; ++k) v -= G[r * s + k] * Minv[k * s + c];
         Minv[r * s + c] = v / G[r * s + r];
       }
     }
     __syncwarp();
-    // transpose in place: Minv[l][j] = Linv[j][l]
     for (int idx = lane; idx < s * s; idx += 32) {
       int r = idx / s, c = idx % s;
       if (r < c) {
@@ -235,61 +161,60 @@ __device__ bool chol_inv_t(double* G, double* Minv, int s, int* flag) {
         Minv[c * s + r] = a;
       }
     }
-    if (lane == 0) *flag = ok;
   }
   __syncthreads();
-  return *flag != 0;
 }
 
 // Cyclic Jacobi on the symmetric s x s matrix H (shared); Q accumulates the
 // rotations; on exit diag(H) holds the eigenvalues.  One warp.
 template <typename T>
 __device__ void jacobi(T* H, T* Q, int s) {
-  if (threadIdx.x >= 32) return;
-  const int lane = threadIdx.x;
-  for (int idx = lane; idx < s * s; idx += 32) Q[idx] = (idx / s == idx % s) ? T(1) : T(0);
-  __syncwarp();
-  const T eps = sizeof(T) == 8 ? T(1e-15) : T(1e-7);
-  for (int sweep = 0; sweep < 40; ++sweep) {
-    T off = 0, dg = 0;
-    for (int idx = lane; idx < s * s; idx += 32) {
-      int r = idx / s, c = idx % s;
-      T v = H[idx];
-      if (r != c) off += v * v; else dg += v * v;
-    }
-    off = warp_sum(off);
-    dg = warp_sum(dg);
-    if (off <= eps * eps * dg || dg == T(0)) break;
-    for (int pp = 0; pp < s - 1; ++pp) {
-      for (int qq = pp + 1; qq < s; ++qq) {
-        T apq = H[pp * s + qq];
-        T app = H[pp * s + pp], aqq = H[qq * s + qq];
-        if (fabs((double)apq) <= (double)eps * 1e-3 * sqrt(fabs((double)app * (double)aqq))) continue;
-        T tau = (aqq - app) / (T(2) * apq);
-        T t = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + sqrt(T(1) + tau * tau));
-        T c = T(1) / sqrt(T(1) + t * t), sn = t * c;
-        __syncwarp();
-        for (int k = lane; k < s; k += 32) {
-          T hp = H[k * s + pp], hq = H[k * s + qq];
-          H[k * s + pp] = c * hp - sn * hq;
-          H[k * s + qq] = sn * hp + c * hq;
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    for (int idx = lane; idx < s * s; idx += 32) Q[idx] = (idx / s == idx % s) ? T(1) : T(0);
+    __syncwarp();
+    const T eps = sizeof(T) == 8 ? T(1e-15) : T(1e-7);
+    for (int sweep = 0; sweep < 40; ++sweep) {
+      T off = 0, dg = 0;
+      for (int idx = lane; idx < s * s; idx += 32) {
+        T v = H[idx];
+        if (idx / s != idx % s) off += v * v; else dg += v * v;
+      }
+      off = warp_sum(off);
+      dg = warp_sum(dg);
+      if (off <= eps * eps * dg || dg == T(0)) break;
+      for (int pp = 0; pp < s - 1; ++pp) {
+        for (int qq = pp + 1; qq < s; ++qq) {
+          T apq = H[pp * s + qq];
+          T app = H[pp * s + pp], aqq = H[qq * s + qq];
+          if (fabs((double)apq) <= (double)eps * 1e-3 * sqrt(fabs((double)app * (double)aqq))) continue;
+          T tau = (aqq - app) / (T(2) * apq);
+          T tt = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + sqrt(T(1) + tau * tau));
+          T c = T(1) / sqrt(T(1) + tt * tt), sn = tt * c;
+          __syncwarp();
+          for (int k = lane; k < s; k += 32) {
+            T hp = H[k * s + pp], hq = H[k * s + qq];
+            H[k * s + pp] = c * hp - sn * hq;
+            H[k * s + qq] = sn * hp + c * hq;
+          }
+          __syncwarp();
+          for (int k = lane; k < s; k += 32) {
+            T hp = H[pp * s + k], hq = H[qq * s + k];
+            H[pp * s + k] = c * hp - sn * hq;
+            H[qq * s + k] = sn * hp + c * hq;
+            T qp = Q[k * s + pp], qv = Q[k * s + qq];
+            Q[k * s + pp] = c * qp - sn * qv;
+            Q[k * s + qq] = sn * qp + c * qv;
+          }
+          __syncwarp();
         }
-        __syncwarp();
-        for (int k = lane; k < s; k += 32) {
-          T hp = H[pp * s + k], hq = H[qq * s + k];
-          H[pp * s + k] = c * hp - sn * hq;
-          H[qq * s + k] = sn * hp + c * hq;
-          T qp = Q[k * s + pp], qv = Q[k * s + qq];
-          Q[k * s + pp] = c * qp - sn * qv;
-          Q[k * s + qq] = sn * qp + c * qv;
-        }
-        __syncwarp();
       }
     }
   }
+  __syncthreads();
 }
 
-// Sort eigenvalues (diag H) descending and permute Q's columns into QS (T).
+// Sort eigenvalues (diag H) descending and permute Q's columns into QS.
 template <typename T>
 __device__ void sort_desc(const T* H, const T* Q, T* QS, T* mu, int* perm, int s) {
   if (threadIdx.x == 0) {
@@ -311,10 +236,10 @@ __device__ void sort_desc(const T* H, const T* Q, T* QS, T* mu, int* perm, int s
 }
 
 template <typename T>
-__device__ void fill_random(T* Y, int L, int s, int j0, uint64_t seed, uint64_t salt) {
+__device__ void fill_random(T* Y, int L, int s, int sp, int j0, uint64_t seed, uint64_t salt) {
   for (int64_t idx = threadIdx.x; idx < (int64_t)L * (s - j0); idx += NT) {
     int r = (int)(idx / (s - j0)), j = j0 + (int)(idx % (s - j0));
-    Y[(int64_t)r * s + j] = (T)counter_normal(seed, salt + (uint64_t)r * 131071u + (uint64_t)j * 2654435761u);
+    Y[(int64_t)r * sp + j] = (T)counter_normal(seed, salt + (uint64_t)r * 131071u + (uint64_t)j * 2654435761u);
   }
   __syncthreads();
 }
@@ -326,127 +251,144 @@ __global__ void __launch_bounds__(NT) k_subspace(
     const int32_t* __restrict__ np_arr, const int32_t* __restrict__ n_arr, const int32_t* __restrict__ m_arr,
     const int32_t* __restrict__ p_arr, const int32_t* __restrict__ sub_off, const int64_t* __restrict__ ent_off,
     const int32_t* __restrict__ lcol, const int32_t* __restrict__ omega, const int32_t* __restrict__ rp,
-    const int32_t* __restrict__ ci, const double* __restrict__ val, const double* __restrict__ ds, T* scratch, const int64_t* __restrict__ scr_off, int nev, int over,
-    int max_sweeps, double tol, uint64_t seed, const float* __restrict__ warm, const int64_t* __restrict__ warm_off,
-    double* __restrict__ values, double* __restrict__ resid, int32_t* __restrict__ count,
-    int32_t* __restrict__ sweeps_out, double* __restrict__ Z, const int64_t* __restrict__ z_off) {
+    const int32_t* __restrict__ ci, const double* __restrict__ val, const double* __restrict__ ds, T* scratch,
+    const int64_t* __restrict__ scr_off, int nev, int over, int max_sweeps, int degree, double tol, uint64_t seed,
+    const float* __restrict__ warm, const int64_t* __restrict__ warm_off, double* __restrict__ values,
+    double* __restrict__ resid, int32_t* __restrict__ count, int32_t* __restrict__ sweeps_out,
+    double* __restrict__ Z, const int64_t* __restrict__ z_off) {
   COUNT_LAUNCH();
   extern __shared__ double shd[];
-  __shared__ int flag;
   __shared__ int perm[128];
+  __shared__ T red[NT / 32];
   const int i = blockIdx.x;
-  SubdomainView sv;
-  sv.n = n_arr[i]; sv.m = m_arr[i]; sv.p = p_arr[i]; sv.g = sv.n - sv.m; sv.ld = np_arr[i];
-  sv.pos0 = sub_off[i];
-  const int p = sv.p, g = sv.g;
-  // dimension of the operator's space and usable block width
+  const int n = n_arr[i], m = m_arr[i], p = p_arr[i], ld = np_arr[i];
+  const int g = n - m, pos0 = sub_off[i];
   const int dim = SPD ? g : p;
-  const int rank_cap = min(p, g);
   const int s = min(nev + over, dim);
-  const int k = min(nev, min(s, rank_cap));
+  const int k = min(nev, min(s, min(p, g)));
   if (k <= 0 || s <= 0) {
     if (threadIdx.x == 0) { count[i] = 0; sweeps_out[i] = 0; }
     for (int j = threadIdx.x; j < nev; j += NT) { values[(int64_t)i * nev + j] = 0; resid[(int64_t)i * nev + j] = 0; }
+    for (int64_t idx = threadIdx.x; idx < (int64_t)p * nev; idx += NT) Z[z_off[i] + idx] = 0;
     return;
   }
+  const int sp = (s + 3) & ~3;
   const T* XpT = XpT_all + xs_off[i];
   const T* Smat = S_all + s_off[i];
-  const T* R = work + work_off[i] + (int64_t)sv.m * sv.ld + sv.m;
-  XScale xs;
-  if (!SPD) { xs.ds = ds; xs.omI = omega + sv.pos0; xs.omG = omega + sv.pos0 + sv.m; }
+  const T* R = work + work_off[i] + (int64_t)m * ld + m;
   const int L = max(p, g);
+  const int64_t blk = (int64_t)L * sp;
   T* base = scratch + scr_off[i];
-  T* Y = base;                       // dim x s
-  T* MY = base + (int64_t)L * s;     // S Y (SPD) / unused
-  T* KY = base + 2 * (int64_t)L * s; // K Y (SPD) / X_p^T Y (general, g x s)
-  T* V = base + 3 * (int64_t)L * s;  // p x s
-  T* AV = base + 4 * (int64_t)L * s; // p x s
-  T* TMP = base + 5 * (int64_t)L * s;
-  double* G = shd;                   // s*s
-  double* Minv = G + s * s;          // s*s
-  T* H = (T*)(Minv + s * s);         // s*s
-  T* Q = H + s * s;                  // s*s
-  T* QS = Q + s * s;                 // s*s
-  T* mu = QS + s * s;                // s
-  T* rn = mu + s;                    // s: residual norms
+  T* Y = base;            // current block (dim x s)
+  T* Yb = base + blk;     // Chebyshev / rotation buffers
+  T* Yc = base + 2 * blk;
+  T* T1 = base + 3 * blk;
+  T* KY = base + 4 * blk; // K Y (dim x s)
+  T* MY = base + 5 * blk; // S Y (SPD)
+  T* V = base + 6 * blk;  // p x s
+  T* AV = base + 7 * blk; // p x s  (general: g x s)
+  // shared memory: GEMM tiles, then the small dense matrices
+  T* gsm = reinterpret_cast<T*>(shd);
+  double* G = shd + (sizeof(T) * (GM * (GK + 1) + GK * GN) + 7) / 8;
+  double* Minv = G + s * s;
+  T* H = reinterpret_cast<T*>(Minv + s * s);
+  T* Q = H + s * s;
+  T* QS = Q + s * s;
+  T* mu = QS + s * s;
+  T* rn = mu + s;
+  Scale sI, sG;
+  if (!SPD) { sI.ds = ds; sI.om = omega + pos0; sG.ds = ds; sG.om = omega + pos0 + m; }
+
+  // K-apply: SPD: K y = X_p^T A^_II X_p y (g-space); general: X_p X_p^T y (p-space)
+  auto applyK = [&](const T* Yin, T* out) {
+    if (SPD) {
+      cta_gemm<T, true>(p, s, g, XpT, p, Yin, sp, V, sp, gsm);          // V = X_p Y
+      mul_AII(p, pos0, omega, rp, ci, val, ds, ent_off, lcol, V, AV, s, sp);
+      cta_gemm<T, false>(g, s, p, XpT, p, AV, sp, out, sp, gsm);        // X_p^T (A V)
+    } else {
+      // W = X_p^T Y = S_G^{-1} X^_p^T S_I Y ; out = X_p W = S_I X^_p S_G^{-1} W
+      cta_gemm<T, false>(g, s, p, XpT, p, Yin, sp, AV, sp, gsm, Scale(), sI, false);
+      for (int idx = threadIdx.x; idx < g * s; idx += NT) {
+        int r = idx / s, j = idx % s;
+        AV[(int64_t)r * sp + j] = (T)((double)AV[(int64_t)r * sp + j] / sG(r));
+      }
+      __syncthreads();
+      cta_gemm<T, true>(p, s, g, XpT, p, AV, sp, out, sp, gsm, sI, sG, true);
+    }
+  };
+  // OP given K y: SPD: S^{-1} (K y); general: K y itself
+  auto applyR = [&](const T* KYin, T* out) {
+    if (SPD) {
+      cta_gemm<T, false>(g, s, g, R, ld, KYin, sp, out, sp, gsm);
+    } else {
+      for (int64_t idx = threadIdx.x; idx < blk; idx += NT) out[idx] = KYin[idx];
+      __syncthreads();
+    }
+  };
+  auto applyM = [&](const T* Yin, T* out) {
+    if (SPD) cta_gemm<T, false>(g, s, g, Smat, g, Yin, sp, out, sp, gsm);
+  };
+  auto swap = [](T*& a, T*& b) { T* t = a; a = b; b = t; };
+  auto orthonormalize = [&]() {
+    for (int pass = 0; pass < 2; ++pass) {
+      T* Gt = QS;  // s*s scratch in T
+      cta_gemm<T, true>(s, s, dim, Y, sp, SPD ? MY : Y, sp, Gt, s, gsm);
+      for (int idx = threadIdx.x; idx < s * s; idx += NT) {
+        int a = idx / s, b = idx % s;
+        G[idx] = 0.5 * ((double)Gt[a * s + b] + (double)Gt[b * s + a]);
+      }
+      __syncthreads();
+      chol_inv_t(G, Minv, s);
+      for (int idx = threadIdx.x; idx < s * s; idx += NT) QS[idx] = (T)Minv[idx];
+      __syncthreads();
+      cta_gemm<T, false>(dim, s, s, Y, sp, QS, s, Yb, sp, gsm);
+      swap(Y, Yb);
+      if (SPD) {
+        cta_gemm<T, false>(dim, s, s, MY, sp, QS, s, Yb, sp, gsm);
+        swap(MY, Yb);
+      }
+    }
+  };
 
   // ---- start block
-  fill_random(Y, dim, s, 0, seed, (uint64_t)i * 0x100000001ull);
+  fill_random(Y, dim, s, sp, 0, seed, (uint64_t)i * 0x100000001ull);
   if (warm != nullptr && SPD) {
     const float* wb = warm + warm_off[i];
     for (int64_t idx = threadIdx.x; idx < (int64_t)dim * k; idx += NT) {
       int r = (int)(idx / k), j = (int)(idx % k);
-      Y[(int64_t)r * s + j] = (T)wb[idx];
+      Y[(int64_t)r * sp + j] = (T)wb[idx];
     }
     __syncthreads();
   }
-  auto orthonormalize = [&](T*& Yb, T*& MYb) {
-    for (int pass = 0; pass < 2; ++pass) {
-      if (SPD) gram(Yb, MYb, dim, s, G); else gram(Yb, Yb, dim, s, G);
-      chol_inv_t(G, Minv, s, &flag);
-      right_mul(Yb, TMP, dim, s, Minv);
-      { T* t = Yb; Yb = TMP; TMP = t; }
-      if (SPD) {
-        right_mul(MYb, TMP, dim, s, Minv);
-        T* t = MYb; MYb = TMP; TMP = t;
-      }
-    }
-  };
-  if (SPD) { mul_sym(Smat, g, g, Y, MY, s); __syncthreads(); }
-  orthonormalize(Y, MY);
+  applyM(Y, MY);
+  orthonormalize();
 
   int sweep = 0;
-  T res_max = 0;
   for (;;) {
-    // ---- K Y (SPD) or X_p^T Y (general)
-    if (SPD) {
-      mul_Xp(XpT, p, g, Y, V, s, s); __syncthreads();
-      mul_AII(sv, omega, rp, ci, val, ds, ent_off, lcol, V, AV, s); __syncthreads();
-      mul_XpT(XpT, p, g, AV, KY, s); __syncthreads();
-      // H = Y^T K Y
-      for (int idx = threadIdx.x; idx < s * s; idx += NT) {
-        int t = idx / s, u = idx % s;
-        T acc = 0;
-        for (int r = 0; r < g; ++r) acc += Y[(int64_t)r * s + t] * KY[(int64_t)r * s + u];
-        H[idx] = acc;
-      }
-    } else {
-      mul_XpT(XpT, p, g, Y, KY, s, xs); __syncthreads();
-      for (int idx = threadIdx.x; idx < s * s; idx += NT) {
-        int t = idx / s, u = idx % s;
-        T acc = 0;
-        for (int r = 0; r < g; ++r) acc += KY[(int64_t)r * s + t] * KY[(int64_t)r * s + u];
-        H[idx] = acc;
-      }
-    }
-    __syncthreads();
-    // symmetrise
+    // ---- Rayleigh-Ritz
+    applyK(Y, KY);
+    cta_gemm<T, true>(s, s, dim, Y, sp, KY, sp, H, s, gsm);
     for (int idx = threadIdx.x; idx < s * s; idx += NT) {
-      int t = idx / s, u = idx % s;
-      if (t < u) { T a = T(0.5) * (H[t * s + u] + H[u * s + t]); H[t * s + u] = a; H[u * s + t] = a; }
+      int a = idx / s, b = idx % s;
+      if (a < b) { T v = T(0.5) * (H[a * s + b] + H[b * s + a]); H[a * s + b] = v; H[b * s + a] = v; }
     }
     __syncthreads();
     jacobi(H, Q, s);
-    __syncthreads();
     sort_desc(H, Q, QS, mu, perm, s);
-    // ---- rotate to Ritz vectors
-    right_mul(Y, TMP, dim, s, QS); { T* t = Y; Y = TMP; TMP = t; }
-    right_mul(KY, TMP, g, s, QS); { T* t = KY; KY = TMP; TMP = t; }
-    if (SPD) { right_mul(MY, TMP, dim, s, QS); T* t = MY; MY = TMP; TMP = t; }
+    cta_gemm<T, false>(dim, s, s, Y, sp, QS, s, Yb, sp, gsm); swap(Y, Yb);
+    cta_gemm<T, false>(dim, s, s, KY, sp, QS, s, Yb, sp, gsm); swap(KY, Yb);
+    if (SPD) { cta_gemm<T, false>(dim, s, s, MY, sp, QS, s, Yb, sp, gsm); swap(MY, Yb); }
     // ---- residuals of the first k Ritz pairs
-    T mu0 = mu[0] > T(0) ? mu[0] : T(1);
-    if (!SPD) { mul_Xp(XpT, p, g, KY, V, s, s, xs); __syncthreads(); }   // X_p X_p^T y
+    const T mu0 = mu[0] > T(0) ? mu[0] : T(1);
     for (int j = 0; j < k; ++j) {
       T part = 0, nrm = 0;
       for (int r = threadIdx.x; r < dim; r += NT) {
-        T a, b;
-        if (SPD) { a = KY[(int64_t)r * s + j]; b = MY[(int64_t)r * s + j]; }
-        else { a = V[(int64_t)r * s + j]; b = Y[(int64_t)r * s + j]; }
+        T a = KY[(int64_t)r * sp + j];
+        T b = SPD ? MY[(int64_t)r * sp + j] : Y[(int64_t)r * sp + j];
         T d = a - mu[j] * b;
         part += d * d;
         nrm += b * b;
       }
-      __shared__ T red[NW];
       part = block_sum(part, red);
       nrm = block_sum(nrm, red);
       if (threadIdx.x == 0) {
@@ -455,32 +397,49 @@ __global__ void __launch_bounds__(NT) k_subspace(
       }
     }
     __syncthreads();
-    res_max = 0;
+    T res_max = 0;
     for (int j = 0; j < k; ++j) res_max = max(res_max, rn[j]);
     ++sweep;
     if ((double)res_max <= tol || sweep >= max_sweeps) break;
-    // ---- power step, columns scaled by the Ritz values; near-null columns restart randomly
-    if (SPD) { mul_sym(R, sv.ld, g, KY, Y, s); }
-    else { for (int64_t idx = threadIdx.x; idx < (int64_t)p * s; idx += NT) Y[idx] = V[idx]; }
+    // ---- Chebyshev filter of degree d on OP, damping [0, b], b = smallest Ritz value
+    T bnd = mu[s - 1];
+    const T floor_b = T(1e-3) * mu0;
+    if (!(bnd > floor_b)) bnd = floor_b;
+    const int d = (bnd < T(0.98) * mu0) ? max(degree, 1) : 1;
+    const T e = bnd / 2, c = bnd / 2;
+    const T sig1 = e / (mu0 - c);
+    T sig = sig1;
+    applyR(KY, Yc);  // OP Y from the K Y at hand
+    for (int64_t idx = threadIdx.x; idx < (int64_t)dim * sp; idx += NT) Yc[idx] = (sig1 / e) * (Yc[idx] - c * Y[idx]);
     __syncthreads();
-    for (int64_t idx = threadIdx.x; idx < (int64_t)dim * s; idx += NT) {
-      int j = (int)(idx % s);
-      T sc = mu[j] > T(1e-10) * mu0 ? T(1) / mu[j] : T(0);
-      Y[idx] *= sc;
+    // Y: previous iterate, Yc: current iterate
+    for (int step = 2; step <= d; ++step) {
+      const T sig_new = T(1) / (T(2) / sig1 - sig);
+      applyK(Yc, T1);
+      applyR(T1, Yb);
+      for (int64_t idx = threadIdx.x; idx < (int64_t)dim * sp; idx += NT)
+        Yb[idx] = T(2) * (sig_new / e) * (Yb[idx] - c * Yc[idx]) - (sig * sig_new) * Y[idx];
+      __syncthreads();
+      swap(Y, Yc);   // previous <- current
+      swap(Yc, Yb);  // current  <- new
+      sig = sig_new;
     }
-    __syncthreads();
+    swap(Y, Yc);
+    // near-null directions restart from fresh random vectors
     int first_null = s;
     for (int j = 0; j < s; ++j)
       if (!(mu[j] > T(1e-10) * mu0)) { first_null = j; break; }
-    if (first_null < s) fill_random(Y, dim, s, first_null, seed ^ 0xA5A5A5A5ull, (uint64_t)i * 7919u + sweep * 104729u);
-    if (SPD) { mul_sym(Smat, g, g, Y, MY, s); __syncthreads(); }
-    orthonormalize(Y, MY);
+    if (first_null < s) fill_random(Y, dim, s, sp, first_null, seed ^ 0xA5A5A5A5ull, (uint64_t)i * 7919u + sweep * 104729u);
+    applyM(Y, MY);
+    orthonormalize();
   }
   // ---- outputs
   int kept = 0;
-  T mu0 = mu[0] > T(0) ? mu[0] : T(0);
-  for (int j = 0; j < k; ++j)
-    if (mu[j] > T(sizeof(T) == 8 ? 1e-12 : 1e-6) * mu0) kept = j + 1;
+  {
+    const T mu0 = mu[0] > T(0) ? mu[0] : T(0);
+    for (int j = 0; j < k; ++j)
+      if (mu[j] > T(sizeof(T) == 8 ? 1e-12 : 1e-6) * mu0) kept = j + 1;
+  }
   if (threadIdx.x == 0) { count[i] = kept; sweeps_out[i] = sweep; }
   for (int j = threadIdx.x; j < nev; j += NT) {
     double v = j < kept ? (SPD ? (double)mu[j] : sqrt(fmax((double)mu[j], 0.0))) : 0.0;
@@ -489,17 +448,16 @@ __global__ void __launch_bounds__(NT) k_subspace(
   }
   double* Zi = Z + z_off[i];
   if (SPD) {
-    // Z_i = X_p y, FP64 output (p x nev, columns >= kept zero)
-    mul_Xp(XpT, p, g, Y, V, s, kept);
-    __syncthreads();
+    // Z_i = S_I X^_p y (undo the diagonal scaling), FP64 output p x nev
+    cta_gemm<T, true>(p, s, g, XpT, p, Y, sp, V, sp, gsm);
     for (int64_t idx = threadIdx.x; idx < (int64_t)p * nev; idx += NT) {
       int r = (int)(idx / nev), j = (int)(idx % nev);
-      Zi[idx] = j < kept ? (double)V[(int64_t)r * s + j] * ds[omega[sv.pos0 + r]] : 0.0;
+      Zi[idx] = j < kept ? (double)V[(int64_t)r * sp + j] * ds[omega[pos0 + r]] : 0.0;
     }
   } else {
     for (int64_t idx = threadIdx.x; idx < (int64_t)p * nev; idx += NT) {
       int r = (int)(idx / nev), j = (int)(idx % nev);
-      Zi[idx] = j < kept ? (double)Y[(int64_t)r * s + j] : 0.0;
+      Zi[idx] = j < kept ? (double)Y[(int64_t)r * sp + j] : 0.0;
     }
   }
 }
@@ -518,15 +476,16 @@ void run_eigen(Handle& h, cudaStream_t s) {
   for (int i = 0; i < N; ++i) {
     int p = h.h_p[i], g = h.h_g[i];
     int dim = spd ? g : p;
-    int sb = std::min(nev + over, dim);
+    int sb = std::max(1, std::min(nev + over, dim));
+    int sp = (sb + 3) & ~3;
     smax = std::max(smax, sb);
     scr[i] = tot;
-    tot += 6LL * std::max(p, g) * std::max(sb, 1);
+    tot += 8LL * std::max(p, g) * sp;
     zo[i] = zt;
     zt += (int64_t)p * nev;
   }
   zo[N] = zt;
-  if (smax > 128) fail(ASM_ERR_UNSUPPORTED, "nev + oversample exceeds 128");
+  if (smax > 96) fail(ASM_ERR_UNSUPPORTED, "nev + oversample exceeds 96");
   co.s_max = smax;
   co.h_z_off = zo;
   co.scratch = mem.alloc<T>(tot);
@@ -539,24 +498,22 @@ void run_eigen(Handle& h, cudaStream_t s) {
   co.sweeps = mem.alloc<int32_t>(N);
   CK(cudaMemcpyAsync(co.scr_off, scr.data(), 8 * N, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(co.z_off, zo.data(), 8 * (N + 1), cudaMemcpyHostToDevice, s));
-  size_t smem = (size_t)2 * smax * smax * sizeof(double) + (size_t)(3 * smax * smax + 2 * smax) * sizeof(T) + 64;
+  size_t gemm_bytes = ((sizeof(T) * (GM * (GK + 1) + GK * GN) + 7) / 8) * 8;
+  size_t smem = gemm_bytes + (size_t)2 * smax * smax * sizeof(double) +
+                (size_t)(3 * smax * smax + 2 * smax) * sizeof(T) + 64;
   const double tol = h.opt.eig_tol > 0 ? h.opt.eig_tol : (h.fp32 ? 1e-3 : 1e-8);
-  const int maxsw = h.opt.max_sweeps > 0 ? h.opt.max_sweeps : 60;
-  if (spd) {
-    CK(cudaFuncSetAttribute(k_subspace<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_subspace<T, true><<<N, NT, smem, s>>>(
-        (const T*)dn.XpT, dn.xs_off, (const T*)dn.S, dn.s_off, (const T*)dn.work, dn.work_off, dn.np, h.dev_n,
-        h.dev_m, h.dev_p, h.ov.sub_off, h.ov.ent_off, h.ov.lcol, h.ov.omega, h.row_ptr, h.col_idx, h.val, h.dscale, (T*)co.scratch,
-        co.scr_off, nev, over, maxsw, tol, h.opt.seed, h.warm, h.warm_off, co.values, co.resid, co.count,
-        co.sweeps, co.Z, co.z_off);
-  } else {
-    CK(cudaFuncSetAttribute(k_subspace<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_subspace<T, false><<<N, NT, smem, s>>>(
-        (const T*)dn.XpT, dn.xs_off, (const T*)dn.S, dn.s_off, (const T*)dn.work, dn.work_off, dn.np, h.dev_n,
-        h.dev_m, h.dev_p, h.ov.sub_off, h.ov.ent_off, h.ov.lcol, h.ov.omega, h.row_ptr, h.col_idx, h.val, h.dscale, (T*)co.scratch,
-        co.scr_off, nev, over, maxsw, tol, h.opt.seed, nullptr, nullptr, co.values, co.resid, co.count,
-        co.sweeps, co.Z, co.z_off);
-  }
+  const int maxsw = h.opt.max_sweeps > 0 ? h.opt.max_sweeps : 40;
+  const int degree = h.opt.filter_degree > 0 ? h.opt.filter_degree : 4;
+  auto launch = [&](auto kern, const float* warm, const int64_t* woff) {
+    CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<N, NT, smem, s>>>((const T*)dn.XpT, dn.xs_off, (const T*)dn.S, dn.s_off, (const T*)dn.work, dn.work_off,
+                             dn.np, h.dev_n, h.dev_m, h.dev_p, h.ov.sub_off, h.ov.ent_off, h.ov.lcol, h.ov.omega,
+                             h.row_ptr, h.col_idx, h.val, h.dscale, (T*)co.scratch, co.scr_off, nev, over, maxsw,
+                             degree, tol, h.opt.seed, warm, woff, co.values, co.resid, co.count, co.sweeps, co.Z,
+                             co.z_off);
+  };
+  if (spd) launch(k_subspace<T, true>, h.warm, h.warm_off);
+  else launch(k_subspace<T, false>, nullptr, nullptr);
   CK_LAUNCH("subspace iteration");
 }
 

@@ -52,6 +52,7 @@ struct Dense {
   void* S = nullptr;                  // S = G - C^T B^{-1} C        (g x g)
   void* tiles = nullptr;              // apply tiles, TILE*TILE each
   void* partials = nullptr;           // per (subdomain, I, J) TILE partial sums
+  double* ypos = nullptr;             // per omega position: local solution before the pull
   int64_t n_tiles = 0, n_work = 0, n_xs = 0, n_s = 0, n_part = 0;
   int32_t* err = nullptr;             // device error word
 };

@@ -312,6 +312,7 @@ void run_local(Handle& h, cudaStream_t s) {
   dn.S = mem.alloc<T>(ss);
   dn.tiles = mem.alloc<T>(tl * TILE * TILE);
   dn.partials = mem.alloc<T>(pt);
+  dn.ypos = mem.alloc<double>(ov.sum_n);
   h.dev_n = d_n; h.dev_m = d_m; h.dev_p = d_p;
   // -- gather A_ii
   CK(cudaMemsetAsync(work, 0, sizeof(T) * w, s));
