@@ -18,11 +18,15 @@
 // with X_p.
 //
 // One sweep: Rayleigh-Ritz (cyclic Jacobi on the projected s x s matrix,
-// Golub & Van Loan Alg. 8.5.3), relative eigen-residual test, then a
-// degree-d Chebyshev polynomial in OP that damps the part of the spectrum
-// below the smallest Ritz value of the block (scaled three-term recurrence of
-// Zhou & Saad, 2007), and CholQR2 re-orthonormalisation.  Dense block
-// products go through a shared-memory tiled CTA GEMM.
+// Golub & Van Loan Alg. 8.5.3), relative eigen-residual test, locking of the
+// converged leading Ritz pairs, then a degree-d Chebyshev polynomial in OP
+// applied to the remaining columns (scaled three-term recurrence of Zhou &
+// Saad, 2007) that damps the spectrum below the smallest Ritz value, with the
+// locked vectors projected out after every application of OP and the degree
+// capped by the filter's growth over the active Ritz values (subdomains with
+// a floating high-contrast inclusion have one eigenvalue 10^6 times the
+// rest), and CholQR2 re-orthonormalisation of column-normalised blocks.
+// Dense block products go through a shared-memory tiled CTA GEMM.
 #include <algorithm>
 
 #include "handle.cuh"
@@ -43,10 +47,10 @@ struct Scale {
   __device__ bool on() const { return ds != nullptr; }
 };
 
-// C (M x N, ldc) = A (M x K) B (K x N, ldb); A row-major (A[m*lda + k]) or,
-// with ACOL, column-major (A[k*lda + m]).  C row m is multiplied by rs(m);
-// A's column k by ks(k) (or divided, with kinv).
-template <typename T, bool ACOL>
+// C (M x N, ldc) = A (M x K) B (K x N, ldb) (with SUB: C -= A B); A row-major
+// (A[m*lda + k]) or, with ACOL, column-major (A[k*lda + m]).  The product's
+// row m is multiplied by rs(m); A's column k by ks(k) (or divided, with kinv).
+template <typename T, bool ACOL, bool SUB = false>
 __device__ void cta_gemm(int M, int N, int K, const T* __restrict__ A, int lda, const T* __restrict__ B, int ldb,
                          T* __restrict__ C, int ldc, T* sm, Scale rs = Scale(), Scale ks = Scale(), bool kinv = false) {
   T* As = sm;                  // GM x (GK + 1)
@@ -93,7 +97,10 @@ __device__ void cta_gemm(int M, int N, int K, const T* __restrict__ A, int lda, 
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
           int c = cg * 16 + q;
-          if (c < nw) C[(int64_t)(m0 + row) * ldc + n0 + c] = acc[q] * f;
+          if (c < nw) {
+            T* cp = C + (int64_t)(m0 + row) * ldc + n0 + c;
+            if (SUB) *cp -= acc[q] * f; else *cp = acc[q] * f;
+          }
         }
       }
     }
@@ -296,40 +303,71 @@ __global__ void __launch_bounds__(NT) k_subspace(
   T* QS = Q + s * s;
   T* mu = QS + s * s;
   T* rn = mu + s;
+  T* Pbuf = rn + s;   // s x s
   Scale sI, sG;
   if (!SPD) { sI.ds = ds; sI.om = omega + pos0; sG.ds = ds; sG.om = omega + pos0 + m; }
 
   // K-apply: SPD: K y = X_p^T A^_II X_p y (g-space); general: X_p X_p^T y (p-space)
-  auto applyK = [&](const T* Yin, T* out) {
+  // Column c0.. c0+nc-1 of the blocks (stride sp).
+  auto applyK = [&](const T* Yin, T* out, int c0, int nc) {
     if (SPD) {
-      cta_gemm<T, true>(p, s, g, XpT, p, Yin, sp, V, sp, gsm);          // V = X_p Y
-      mul_AII(p, pos0, omega, rp, ci, val, ds, ent_off, lcol, V, AV, s, sp);
-      cta_gemm<T, false>(g, s, p, XpT, p, AV, sp, out, sp, gsm);        // X_p^T (A V)
+      cta_gemm<T, true>(p, nc, g, XpT, p, Yin + c0, sp, V + c0, sp, gsm);          // V = X_p Y
+      mul_AII(p, pos0, omega, rp, ci, val, ds, ent_off, lcol, V + c0, AV + c0, nc, sp);
+      cta_gemm<T, false>(g, nc, p, XpT, p, AV + c0, sp, out + c0, sp, gsm);        // X_p^T (A V)
     } else {
       // W = X_p^T Y = S_G^{-1} X^_p^T S_I Y ; out = X_p W = S_I X^_p S_G^{-1} W
-      cta_gemm<T, false>(g, s, p, XpT, p, Yin, sp, AV, sp, gsm, Scale(), sI, false);
-      for (int idx = threadIdx.x; idx < g * s; idx += NT) {
-        int r = idx / s, j = idx % s;
+      cta_gemm<T, false>(g, nc, p, XpT, p, Yin + c0, sp, AV + c0, sp, gsm, Scale(), sI, false);
+      for (int idx = threadIdx.x; idx < g * nc; idx += NT) {
+        int r = idx / nc, j = c0 + idx % nc;
         AV[(int64_t)r * sp + j] = (T)((double)AV[(int64_t)r * sp + j] / sG(r));
       }
       __syncthreads();
-      cta_gemm<T, true>(p, s, g, XpT, p, AV, sp, out, sp, gsm, sI, sG, true);
+      cta_gemm<T, true>(p, nc, g, XpT, p, AV + c0, sp, out + c0, sp, gsm, sI, sG, true);
     }
   };
   // OP given K y: SPD: S^{-1} (K y); general: K y itself
-  auto applyR = [&](const T* KYin, T* out) {
+  auto applyR = [&](const T* KYin, T* out, int c0, int nc) {
     if (SPD) {
-      cta_gemm<T, false>(g, s, g, R, ld, KYin, sp, out, sp, gsm);
+      cta_gemm<T, false>(g, nc, g, R, ld, KYin + c0, sp, out + c0, sp, gsm);
     } else {
-      for (int64_t idx = threadIdx.x; idx < blk; idx += NT) out[idx] = KYin[idx];
+      for (int64_t idx = threadIdx.x; idx < (int64_t)dim * nc; idx += NT) {
+        int64_t r = idx / nc, j = c0 + idx % nc;
+        out[r * sp + j] = KYin[r * sp + j];
+      }
       __syncthreads();
     }
   };
   auto applyM = [&](const T* Yin, T* out) {
     if (SPD) cta_gemm<T, false>(g, s, g, Smat, g, Yin, sp, out, sp, gsm);
   };
+  // W[:, c0:] -= Y_L (MY_L^T W[:, c0:]) with Y_L = the first c0 columns of Y
+  // (S-orthonormal, MY_L = S Y_L): keeps the active block S-orthogonal to the
+  // locked Ritz vectors.
+  T* Pt = Pbuf;
+  auto deflate = [&](T* W, int c0, int nc) {
+    if (c0 == 0) return;
+    cta_gemm<T, true>(c0, nc, dim, SPD ? MY : Y, sp, W + c0, sp, Pt, nc, gsm);
+    cta_gemm<T, false, true>(dim, nc, c0, Y, sp, Pt, nc, W + c0, sp, gsm);
+  };
   auto swap = [](T*& a, T*& b) { T* t = a; a = b; b = t; };
   auto orthonormalize = [&]() {
+    // unit M-norm columns first, so the Gram matrix carries only the angles
+    for (int j = 0; j < s; ++j) {
+      T part = 0;
+      for (int r = threadIdx.x; r < dim; r += NT)
+        part += Y[(int64_t)r * sp + j] * (SPD ? MY[(int64_t)r * sp + j] : Y[(int64_t)r * sp + j]);
+      part = block_sum(part, red);
+      if (threadIdx.x == 0) Pbuf[j] = part > T(0) ? T(1) / sqrt(part) : T(1);
+    }
+    __syncthreads();
+    for (int64_t idx = threadIdx.x; idx < (int64_t)dim * sp; idx += NT) {
+      int j = (int)(idx % sp);
+      if (j < s) {
+        Y[idx] *= Pbuf[j];
+        if (SPD) MY[idx] *= Pbuf[j];
+      }
+    }
+    __syncthreads();
     for (int pass = 0; pass < 2; ++pass) {
       T* Gt = QS;  // s*s scratch in T
       cta_gemm<T, true>(s, s, dim, Y, sp, SPD ? MY : Y, sp, Gt, s, gsm);
@@ -366,7 +404,7 @@ __global__ void __launch_bounds__(NT) k_subspace(
   int sweep = 0;
   for (;;) {
     // ---- Rayleigh-Ritz
-    applyK(Y, KY);
+    applyK(Y, KY, 0, s);
     cta_gemm<T, true>(s, s, dim, Y, sp, KY, sp, H, s, gsm);
     for (int idx = threadIdx.x; idx < s * s; idx += NT) {
       int a = idx / s, b = idx % s;
@@ -401,30 +439,57 @@ __global__ void __launch_bounds__(NT) k_subspace(
     for (int j = 0; j < k; ++j) res_max = max(res_max, rn[j]);
     ++sweep;
     if ((double)res_max <= tol || sweep >= max_sweeps) break;
-    // ---- Chebyshev filter of degree d on OP, damping [0, b], b = smallest Ritz value
+    // ---- lock the converged leading Ritz pairs; filter the rest
+    int nl = 0;
+    while (nl < k && rn[nl] <= (T)tol) ++nl;
+    const int na = s - nl;
+    // Chebyshev filter of degree d on OP, damping [0, b] (b = smallest Ritz
+    // value), normalised at the largest active Ritz value a0; the degree is
+    // capped so that the filter's growth over [b, a0] stays representable.
     T bnd = mu[s - 1];
-    const T floor_b = T(1e-3) * mu0;
+    const T a0 = mu[nl] > T(0) ? mu[nl] : mu0;
+    const T floor_b = T(1e-3) * a0;
     if (!(bnd > floor_b)) bnd = floor_b;
-    const int d = (bnd < T(0.98) * mu0) ? max(degree, 1) : 1;
     const T e = bnd / 2, c = bnd / 2;
-    const T sig1 = e / (mu0 - c);
+    const double rL = (2.0 * (double)a0 - (double)bnd) / (double)bnd;   // L(a0) >= 1
+    const double gmax = sizeof(T) == 8 ? 1e8 : 1e3;
+    int d = max(degree, 1);
+    if (rL > 1.0 + 1e-12) d = min(d, max(1, (int)floor(acosh(gmax) / acosh(rL))));
+    else d = 1;
+    const T sig1 = (rL > 1.0 + 1e-12) ? e / (a0 - c) : T(1);
     T sig = sig1;
-    applyR(KY, Yc);  // OP Y from the K Y at hand
-    for (int64_t idx = threadIdx.x; idx < (int64_t)dim * sp; idx += NT) Yc[idx] = (sig1 / e) * (Yc[idx] - c * Y[idx]);
+    applyR(KY, Yc, nl, na);  // OP Y from the K Y at hand
+    deflate(Yc, nl, na);
+    for (int64_t idx = threadIdx.x; idx < (int64_t)dim * na; idx += NT) {
+      int64_t r = idx / na, j = nl + idx % na;
+      Yc[r * sp + j] = (sig1 / e) * (Yc[r * sp + j] - c * Y[r * sp + j]);
+    }
     __syncthreads();
-    // Y: previous iterate, Yc: current iterate
+    // columns nl.. of Y: previous iterate, of Yc: current iterate
     for (int step = 2; step <= d; ++step) {
       const T sig_new = T(1) / (T(2) / sig1 - sig);
-      applyK(Yc, T1);
-      applyR(T1, Yb);
-      for (int64_t idx = threadIdx.x; idx < (int64_t)dim * sp; idx += NT)
-        Yb[idx] = T(2) * (sig_new / e) * (Yb[idx] - c * Yc[idx]) - (sig * sig_new) * Y[idx];
+      applyK(Yc, T1, nl, na);
+      applyR(T1, Yb, nl, na);
+      deflate(Yb, nl, na);
+      for (int64_t idx = threadIdx.x; idx < (int64_t)dim * na; idx += NT) {
+        int64_t r = idx / na, j = nl + idx % na;
+        Yb[r * sp + j] = T(2) * (sig_new / e) * (Yb[r * sp + j] - c * Yc[r * sp + j]) - (sig * sig_new) * Y[r * sp + j];
+      }
       __syncthreads();
-      swap(Y, Yc);   // previous <- current
-      swap(Yc, Yb);  // current  <- new
+      // rotate the active columns: previous <- current <- new (locked columns stay in Y)
+      for (int64_t idx = threadIdx.x; idx < (int64_t)dim * na; idx += NT) {
+        int64_t r = idx / na, j = nl + idx % na;
+        Y[r * sp + j] = Yc[r * sp + j];
+        Yc[r * sp + j] = Yb[r * sp + j];
+      }
+      __syncthreads();
       sig = sig_new;
     }
-    swap(Y, Yc);
+    for (int64_t idx = threadIdx.x; idx < (int64_t)dim * na; idx += NT) {
+      int64_t r = idx / na, j = nl + idx % na;
+      Y[r * sp + j] = Yc[r * sp + j];
+    }
+    __syncthreads();
     // near-null directions restart from fresh random vectors
     int first_null = s;
     for (int j = 0; j < s; ++j)
@@ -500,7 +565,7 @@ void run_eigen(Handle& h, cudaStream_t s) {
   CK(cudaMemcpyAsync(co.z_off, zo.data(), 8 * (N + 1), cudaMemcpyHostToDevice, s));
   size_t gemm_bytes = ((sizeof(T) * (GM * (GK + 1) + GK * GN) + 7) / 8) * 8;
   size_t smem = gemm_bytes + (size_t)2 * smax * smax * sizeof(double) +
-                (size_t)(3 * smax * smax + 2 * smax) * sizeof(T) + 64;
+                (size_t)(4 * smax * smax + 2 * smax) * sizeof(T) + 64;
   const double tol = h.opt.eig_tol > 0 ? h.opt.eig_tol : (h.fp32 ? 1e-3 : 1e-8);
   const int maxsw = h.opt.max_sweeps > 0 ? h.opt.max_sweeps : 40;
   const int degree = h.opt.filter_degree > 0 ? h.opt.filter_degree : 4;
