@@ -132,14 +132,25 @@ __device__ void mul_AII(int p, int pos0, const int32_t* __restrict__ omega, cons
 }
 
 // Cholesky of the s x s Gram matrix G (warp 0), then Minv = L^{-T} so that
-// Y <- Y Minv is orthonormal in the metric of G.
-__device__ void chol_inv_t(double* G, double* Minv, int s) {
+// Y <- Y Minv is orthonormal in the metric of G.  A pivot below `tiny` (the
+// diagonal of G is 1) marks column j as dependent in bad[j] and is replaced
+// by 1; returns the number of dependent columns.
+__device__ int chol_inv_t(double* G, double* Minv, int s, double tiny, int* bad, int* nbad) {
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x;
+    int nb = 0;
     for (int j = 0; j < s; ++j) {
       double d = G[j * s + j];
       for (int k = 0; k < j; ++k) d -= G[j * s + k] * G[j * s + k];
-      if (!(d > 0)) d = 1e-300;
+      const bool dep = !(d > tiny);
+      if (lane == 0) bad[j] = dep ? 1 : 0;
+      if (dep) {
+        ++nb;
+        d = 1.0;
+        for (int r = lane; r < s; r += 32) if (r != j) { G[r * s + j] = 0; }
+        __syncwarp();
+        for (int k = lane; k < j; k += 32) G[j * s + k] = 0;
+      }
       d = sqrt(d);
       __syncwarp();
       for (int r = j + 1 + lane; r < s; r += 32) {
@@ -168,8 +179,10 @@ __device__ void chol_inv_t(double* G, double* Minv, int s) {
         Minv[c * s + r] = a;
       }
     }
+    if (lane == 0) *nbad = nb;
   }
   __syncthreads();
+  return *nbad;
 }
 
 // Cyclic Jacobi on the symmetric s x s matrix H (shared); Q accumulates the
@@ -266,6 +279,8 @@ __global__ void __launch_bounds__(NT) k_subspace(
   COUNT_LAUNCH();
   extern __shared__ double shd[];
   __shared__ int perm[128];
+  __shared__ int badcol[128];
+  __shared__ int nbad;
   __shared__ T red[NT / 32];
   const int i = blockIdx.x;
   const int n = n_arr[i], m = m_arr[i], p = p_arr[i], ld = np_arr[i];
@@ -350,41 +365,58 @@ __global__ void __launch_bounds__(NT) k_subspace(
     cta_gemm<T, false, true>(dim, nc, c0, Y, sp, Pt, nc, W + c0, sp, gsm);
   };
   auto swap = [](T*& a, T*& b) { T* t = a; a = b; b = t; };
-  auto orthonormalize = [&]() {
-    // unit M-norm columns first, so the Gram matrix carries only the angles
-    for (int j = 0; j < s; ++j) {
-      T part = 0;
-      for (int r = threadIdx.x; r < dim; r += NT)
-        part += Y[(int64_t)r * sp + j] * (SPD ? MY[(int64_t)r * sp + j] : Y[(int64_t)r * sp + j]);
-      part = block_sum(part, red);
-      if (threadIdx.x == 0) Pbuf[j] = part > T(0) ? T(1) / sqrt(part) : T(1);
-    }
-    __syncthreads();
-    for (int64_t idx = threadIdx.x; idx < (int64_t)dim * sp; idx += NT) {
-      int j = (int)(idx % sp);
-      if (j < s) {
-        Y[idx] *= Pbuf[j];
-        if (SPD) MY[idx] *= Pbuf[j];
-      }
-    }
-    __syncthreads();
-    for (int pass = 0; pass < 2; ++pass) {
-      T* Gt = QS;  // s*s scratch in T
-      cta_gemm<T, true>(s, s, dim, Y, sp, SPD ? MY : Y, sp, Gt, s, gsm);
-      for (int idx = threadIdx.x; idx < s * s; idx += NT) {
-        int a = idx / s, b = idx % s;
-        G[idx] = 0.5 * ((double)Gt[a * s + b] + (double)Gt[b * s + a]);
+  // CholQR2 of column-normalised blocks; columns found dependent are
+  // replaced by fresh random vectors and the whole step is redone.
+  const double tiny = sizeof(T) == 8 ? 1e-10 : 1e-5;
+  auto orthonormalize = [&](uint64_t salt) {
+    for (int attempt = 0; attempt < 4; ++attempt) {
+      if (attempt > 0) applyM(Y, MY);
+      for (int j = 0; j < s; ++j) {
+        T part = 0;
+        for (int r = threadIdx.x; r < dim; r += NT)
+          part += Y[(int64_t)r * sp + j] * (SPD ? MY[(int64_t)r * sp + j] : Y[(int64_t)r * sp + j]);
+        part = block_sum(part, red);
+        if (threadIdx.x == 0) Pbuf[j] = part > T(0) ? T(1) / sqrt(part) : T(1);
       }
       __syncthreads();
-      chol_inv_t(G, Minv, s);
-      for (int idx = threadIdx.x; idx < s * s; idx += NT) QS[idx] = (T)Minv[idx];
-      __syncthreads();
-      cta_gemm<T, false>(dim, s, s, Y, sp, QS, s, Yb, sp, gsm);
-      swap(Y, Yb);
-      if (SPD) {
-        cta_gemm<T, false>(dim, s, s, MY, sp, QS, s, Yb, sp, gsm);
-        swap(MY, Yb);
+      for (int64_t idx = threadIdx.x; idx < (int64_t)dim * sp; idx += NT) {
+        int j = (int)(idx % sp);
+        if (j < s) {
+          Y[idx] *= Pbuf[j];
+          if (SPD) MY[idx] *= Pbuf[j];
+        }
       }
+      __syncthreads();
+      bool ok = true;
+      for (int pass = 0; pass < 2 && ok; ++pass) {
+        T* Gt = QS;  // s*s scratch in T
+        cta_gemm<T, true>(s, s, dim, Y, sp, SPD ? MY : Y, sp, Gt, s, gsm);
+        for (int idx = threadIdx.x; idx < s * s; idx += NT) {
+          int a = idx / s, b = idx % s;
+          G[idx] = 0.5 * ((double)Gt[a * s + b] + (double)Gt[b * s + a]);
+        }
+        __syncthreads();
+        if (chol_inv_t(G, Minv, s, tiny, badcol, &nbad) > 0) {
+          for (int64_t idx = threadIdx.x; idx < (int64_t)dim * s; idx += NT) {
+            int r = (int)(idx / s), j = (int)(idx % s);
+            if (badcol[j])
+              Y[(int64_t)r * sp + j] = (T)counter_normal(seed ^ 0x5DEECE66Dull,
+                                                         salt * 977u + attempt * 131u + (uint64_t)r * 131071u + j);
+          }
+          __syncthreads();
+          ok = false;
+          break;
+        }
+        for (int idx = threadIdx.x; idx < s * s; idx += NT) QS[idx] = (T)Minv[idx];
+        __syncthreads();
+        cta_gemm<T, false>(dim, s, s, Y, sp, QS, s, Yb, sp, gsm);
+        swap(Y, Yb);
+        if (SPD) {
+          cta_gemm<T, false>(dim, s, s, MY, sp, QS, s, Yb, sp, gsm);
+          swap(MY, Yb);
+        }
+      }
+      if (ok) return;
     }
   };
 
@@ -399,7 +431,7 @@ __global__ void __launch_bounds__(NT) k_subspace(
     __syncthreads();
   }
   applyM(Y, MY);
-  orthonormalize();
+  orthonormalize((uint64_t)i);
 
   int sweep = 0;
   for (;;) {
@@ -430,7 +462,10 @@ __global__ void __launch_bounds__(NT) k_subspace(
       part = block_sum(part, red);
       nrm = block_sum(nrm, red);
       if (threadIdx.x == 0) {
-        T den = (mu[j] > T(0) ? mu[j] : mu0) * sqrt(nrm);
+        // FP64: relative to the Ritz value; FP32: relative to the largest one
+        // (single precision cannot resolve values far below the top one)
+        T scale = (sizeof(T) == 8 && mu[j] > T(0)) ? mu[j] : mu0;
+        T den = scale * sqrt(nrm);
         rn[j] = (mu[j] <= T(1e-12) * mu0) ? T(0) : sqrt(part) / (den > T(0) ? den : T(1));
       }
     }
@@ -453,7 +488,7 @@ __global__ void __launch_bounds__(NT) k_subspace(
     const T e = bnd / 2, c = bnd / 2;
     const double rL = (2.0 * (double)a0 - (double)bnd) / (double)bnd;   // L(a0) >= 1
     const double gmax = sizeof(T) == 8 ? 1e8 : 1e3;
-    int d = max(degree, 1);
+    int d = sweep > 2 ? max(degree, 1) : 1;   // the first Ritz values are poor bounds
     if (rL > 1.0 + 1e-12) d = min(d, max(1, (int)floor(acosh(gmax) / acosh(rL))));
     else d = 1;
     const T sig1 = (rL > 1.0 + 1e-12) ? e / (a0 - c) : T(1);
@@ -496,7 +531,7 @@ __global__ void __launch_bounds__(NT) k_subspace(
       if (!(mu[j] > T(1e-10) * mu0)) { first_null = j; break; }
     if (first_null < s) fill_random(Y, dim, s, sp, first_null, seed ^ 0xA5A5A5A5ull, (uint64_t)i * 7919u + sweep * 104729u);
     applyM(Y, MY);
-    orthonormalize();
+    orthonormalize((uint64_t)i * 1000003u + sweep);
   }
   // ---- outputs
   int kept = 0;
