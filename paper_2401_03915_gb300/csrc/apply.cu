@@ -1,13 +1,13 @@
 // Two-level additive Schwarz apply (Remark in Section 4.3):
 //     z = sum_i R_i^T A_ii^{-1} R_i r  +  Z E^{-1} Z^T r.
 //
-// Local part: A_ii^{-1} = D^{-1/2} A^_ii^{-1} D^{-1/2} with the scaled inverse stored as TILE x TILE tiles (lower tiles only when
-// A is SPD).  One flat, load-balanced pass over all tiles of all subdomains
-// reads every tile once; an off-diagonal tile T of a symmetric inverse
-// contributes T x_J to row block I and T^T x_I to row block J.  Each
-// contribution goes to its own slot, and the pull kernel sums the slots of
-// every occurrence of a node in a fixed order: the overlapping sum is
-// deterministic without atomics.
+// Local part: A_ii^{-1} = D^{-1/2} A^_ii^{-1} D^{-1/2}.  SPD: A^_ii^{-1} = W^T W
+// with W = L^{-1} stored as its lower TILE x TILE tiles: a row pass t = W x
+// and a column pass y = W^T t, each one flat, load-balanced sweep over the
+// tiles of all subdomains.  General A: the explicit inverse, all tiles, one
+// row pass.  Every tile product goes to its own slot; a reduction sums the
+// slots of each row in a fixed order and the pull kernel sums the
+// occurrences of each node in a fixed order: deterministic, no atomics.
 // Coarse part: Z^T r per subdomain, the FP64 coarse solve, and Z y added in
 // the pull kernel (Z_i is supported on Omega_{I_i}).
 #include <algorithm>
@@ -35,17 +35,19 @@ __device__ __forceinline__ void load4<double>(const double* p, double (&v)[4]) {
 
 // Thread t of the block owns rows (t/16) + 16a, a = 0..3, and the four
 // columns 4 (t%16) .. 4 (t%16) + 3 of the tile.
-template <typename T, bool SYM>
+// ROW pass:    slot (I, J) <- T x_J    with x gathered from r (scaled) via Omega_i
+// COLUMN pass: slot (J, I) <- T^T x_I  with x read from the per-position array xpos
+template <typename T, bool ROW>
 __global__ void __launch_bounds__(NT) k_apply_tiles(const T* __restrict__ tiles, const int4* __restrict__ desc,
                                                     int64_t ntiles, const int32_t* __restrict__ omega,
                                                     const int32_t* __restrict__ sub_off,
                                                     const int32_t* __restrict__ n_arr, const int32_t* __restrict__ nt_arr,
                                                     const int64_t* __restrict__ part_off, const double* __restrict__ r,
-                                                    const double* __restrict__ ds, T* __restrict__ partials,
-                                                    const int32_t* __restrict__ done) {
+                                                    const double* __restrict__ ds, const double* __restrict__ xpos,
+                                                    T* __restrict__ partials, const int32_t* __restrict__ done) {
   COUNT_LAUNCH();
   if (done != nullptr && *done) return;
-  __shared__ T xI[TILE], xJ[TILE];
+  __shared__ T xv[TILE];
   __shared__ T colpart[NT / 32][TILE];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int cq = tid & 15, rg = tid >> 4;
@@ -55,36 +57,36 @@ __global__ void __launch_bounds__(NT) k_apply_tiles(const T* __restrict__ tiles,
     const int n = n_arr[i], nt = nt_arr[i], b0 = sub_off[i];
     __syncthreads();
     if (tid < TILE) {
-      int a = I * TILE + tid;
-      int v = a < n ? omega[b0 + a] : 0;
-      xI[tid] = a < n ? (T)(r[v] * ds[v]) : T(0);
-    } else if (tid < 2 * TILE) {
-      int a = J * TILE + tid - TILE;
-      int v = a < n ? omega[b0 + a] : 0;
-      xJ[tid - TILE] = a < n ? (T)(r[v] * ds[v]) : T(0);
+      if (ROW) {
+        int a = J * TILE + tid;
+        int v = a < n ? omega[b0 + a] : 0;
+        xv[tid] = a < n ? (T)(r[v] * ds[v]) : T(0);
+      } else {
+        int a = I * TILE + tid;
+        xv[tid] = a < n ? (T)xpos[b0 + a] : T(0);
+      }
     }
     __syncthreads();
     const T* tile = tiles + t * (TILE * TILE);
     T v[4][4];
 #pragma unroll
     for (int a = 0; a < 4; ++a) load4<T>(tile + (rg + 16 * a) * TILE + 4 * cq, v[a]);
-    // row partials: y_I[row] += sum_c T[row][c] x_J[c]
     T* P = partials + part_off[i];
+    if (ROW) {
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      T s = v[a][0] * xJ[4 * cq] + v[a][1] * xJ[4 * cq + 1] + v[a][2] * xJ[4 * cq + 2] + v[a][3] * xJ[4 * cq + 3];
-      s += __shfl_xor_sync(0xffffffffu, s, 8);
-      s += __shfl_xor_sync(0xffffffffu, s, 4);
-      s += __shfl_xor_sync(0xffffffffu, s, 2);
-      s += __shfl_xor_sync(0xffffffffu, s, 1);
-      if (cq == 0) P[((int64_t)I * nt + J) * TILE + rg + 16 * a] = s;
-    }
-    if (SYM && I != J) {
-      // column partials: y_J[col] += sum_row T[row][col] x_I[row]
+      for (int a = 0; a < 4; ++a) {
+        T s = v[a][0] * xv[4 * cq] + v[a][1] * xv[4 * cq + 1] + v[a][2] * xv[4 * cq + 2] + v[a][3] * xv[4 * cq + 3];
+        s += __shfl_xor_sync(0xffffffffu, s, 8);
+        s += __shfl_xor_sync(0xffffffffu, s, 4);
+        s += __shfl_xor_sync(0xffffffffu, s, 2);
+        s += __shfl_xor_sync(0xffffffffu, s, 1);
+        if (cq == 0) P[((int64_t)I * nt + J) * TILE + rg + 16 * a] = s;
+      }
+    } else {
       T c[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q)
-        c[q] = v[0][q] * xI[rg] + v[1][q] * xI[rg + 16] + v[2][q] * xI[rg + 32] + v[3][q] * xI[rg + 48];
+        c[q] = v[0][q] * xv[rg] + v[1][q] * xv[rg + 16] + v[2][q] * xv[rg + 32] + v[3][q] * xv[rg + 48];
 #pragma unroll
       for (int q = 0; q < 4; ++q) c[q] += __shfl_xor_sync(0xffffffffu, c[q], 16);
       if (lane < 16) {
@@ -135,23 +137,27 @@ __global__ void __launch_bounds__(NT) k_coarse_restrict(const double* __restrict
   }
 }
 
-// y_pos[k] = sum_J partial[i][a/TILE][J][a%TILE] for every omega position k = (i, a)
+// y_pos[k] = sum_J partial[i][a/TILE][J][a%TILE] for every omega position
+// k = (i, a), J over the written slots: all (tri 0), J <= a/TILE (tri 1),
+// J >= a/TILE (tri 2).
 template <typename T>
 __global__ void __launch_bounds__(NT) k_reduce_partials(int64_t m, const int32_t* __restrict__ pos_sub,
                                                         const int32_t* __restrict__ sub_off,
                                                         const int32_t* __restrict__ nt_arr,
                                                         const int64_t* __restrict__ part_off,
                                                         const T* __restrict__ partials, double* __restrict__ ypos,
-                                                        const int32_t* __restrict__ done) {
+                                                        int tri, const int32_t* __restrict__ done) {
   COUNT_LAUNCH();
   if (done != nullptr && *done) return;
   for (int64_t k = blockIdx.x * (int64_t)NT + threadIdx.x; k < m; k += (int64_t)gridDim.x * NT) {
     const int i = pos_sub[k];
     const int a = (int)(k - sub_off[i]);
     const int nt = nt_arr[i];
-    const T* P = partials + part_off[i] + (int64_t)(a / TILE) * nt * TILE + (a % TILE);
+    const int I = a / TILE;
+    const T* P = partials + part_off[i] + (int64_t)I * nt * TILE + (a % TILE);
+    const int j0 = tri == 2 ? I : 0, j1 = tri == 1 ? I + 1 : nt;
     double s = 0;
-    for (int J = 0; J < nt; ++J) s += (double)P[(int64_t)J * TILE];
+    for (int J = j0; J < j1; ++J) s += (double)P[(int64_t)J * TILE];
     ypos[k] = s;
   }
 }
@@ -196,17 +202,32 @@ __global__ void __launch_bounds__(NT) k_apply_pull(int n, const int32_t* __restr
 }
 
 template <typename T>
+void reduce_partials(Handle& h, double* out, int tri, cudaStream_t s, const int32_t* done) {
+  Dense& dn = h.dn;
+  unsigned gr = (unsigned)std::min<int64_t>(ceil_div(h.ov.sum_n, NT), 152 * 16);
+  k_reduce_partials<T><<<gr, NT, 0, s>>>(h.ov.sum_n, h.ov.pos_sub, h.ov.sub_off, dn.nt, dn.part_off,
+                                         (const T*)dn.partials, out, tri, done);
+}
+
+// Local part up to the per-position results in dn.ypos.
+// SPD: t = W x (row pass over the lower tiles of W), then y = W^T t (column
+// pass); general: y = A^_ii^{-1} x (row pass over all tiles).
+template <typename T>
 void apply_local(Handle& h, const double* r, cudaStream_t s, const int32_t* done) {
   Dense& dn = h.dn;
   unsigned gt = (unsigned)std::min<int64_t>(std::max<int64_t>(dn.n_tiles, 1), 152 * 8);
-  if (h.opt.spd)
-    k_apply_tiles<T, true><<<gt, NT, 0, s>>>((const T*)dn.tiles, dn.tile_desc, dn.n_tiles, h.ov.omega,
-                                             h.ov.sub_off, h.dev_n, dn.nt, dn.part_off, r, h.dscale,
-                                             (T*)dn.partials, done);
-  else
+  k_apply_tiles<T, true><<<gt, NT, 0, s>>>((const T*)dn.tiles, dn.tile_desc, dn.n_tiles, h.ov.omega, h.ov.sub_off,
+                                           h.dev_n, dn.nt, dn.part_off, r, h.dscale, nullptr, (T*)dn.partials,
+                                           done);
+  if (h.opt.spd) {
+    reduce_partials<T>(h, dn.tpos, 1, s, done);
     k_apply_tiles<T, false><<<gt, NT, 0, s>>>((const T*)dn.tiles, dn.tile_desc, dn.n_tiles, h.ov.omega,
-                                              h.ov.sub_off, h.dev_n, dn.nt, dn.part_off, r, h.dscale,
+                                              h.ov.sub_off, h.dev_n, dn.nt, dn.part_off, nullptr, nullptr, dn.tpos,
                                               (T*)dn.partials, done);
+    reduce_partials<T>(h, dn.ypos, 2, s, done);
+  } else {
+    reduce_partials<T>(h, dn.ypos, 0, s, done);
+  }
 }
 
 // Z^T r and the coarse solve; returns the coarse solution (or null).
@@ -225,9 +246,6 @@ template <typename T>
 void apply_pull(Handle& h, const double* yc, double* z, cudaStream_t s, const int32_t* done) {
   Dense& dn = h.dn;
   Coarse& co = h.co;
-  unsigned gr = (unsigned)std::min<int64_t>(ceil_div(h.ov.sum_n, NT), 152 * 16);
-  k_reduce_partials<T><<<gr, NT, 0, s>>>(h.ov.sum_n, h.ov.pos_sub, h.ov.sub_off, dn.nt, dn.part_off,
-                                         (const T*)dn.partials, dn.ypos, done);
   unsigned gp = (unsigned)std::min<int64_t>(ceil_div(h.n, NT), 152 * 16);
   k_apply_pull<<<gp, NT, 0, s>>>(h.n, h.ov.occ_ptr, h.ov.occ_pos, dn.ypos, h.part, h.ov.own_pos, h.ov.sub_off,
                                  co.Z, co.z_off, co.count, co.col_off, h.nev, yc, h.dscale, z, done);

@@ -5,9 +5,11 @@
 // S = G - C^T B^{-1} C and K = X_p^T A_{I_i,I_i} X_p, every eigenpair of
 // eq. gevpsvd with lambda^2 > 0 satisfies K y = lambda^2 S y with y = w_Gamma,
 // the A_ii-normalisation of w is the S-normalisation of y, and the coarse
-// vector R_i^T D_i Pi_i w is [X_p y; 0] on Omega_{I_i}.  The iteration runs on
-// OP = S^{-1} K (S^{-1} is the trailing block of A_ii^{-1} left by the sweep)
-// with S-orthonormal blocks and Rayleigh-Ritz on Y^T K Y.
+// vector R_i^T D_i Pi_i w is [X_p y; 0] on Omega_{I_i}.  With the Cholesky
+// factor A_ii = L L^T and W = L^{-1} = [W11 0; W21 W22] (blocks Omega', Gamma),
+// S = (W22^T W22)^{-1} and X W22^T = W21^T, so with z = W22^{-T} y and
+// U = W21[:, :p] the problem is the symmetric U A_II U^T z = lambda^2 z with
+// Euclidean-orthonormal z, and the coarse vector is X_p y = U^T z.
 //
 // General A (the paper's nonsymmetric extension).  D_i Pi_i is nonzero only
 // in rows I_i and columns Gamma_delta, where it equals X_p, so its left
@@ -295,9 +297,9 @@ __global__ void __launch_bounds__(NT) k_subspace(
     return;
   }
   const int sp = (s + 3) & ~3;
-  const T* XpT = XpT_all + xs_off[i];
-  const T* Smat = S_all + s_off[i];
-  const T* R = work + work_off[i] + (int64_t)m * ld + m;
+  const T* XpT = SPD ? nullptr : XpT_all + xs_off[i];
+  // SPD: U = W[Gamma_delta, I_i] (g x p block of W = L^{-1}, leading dimension ld)
+  const T* U = work + work_off[i] + (int64_t)m * ld;
   const int L = max(p, g);
   const int64_t blk = (int64_t)L * sp;
   T* base = scratch + scr_off[i];
@@ -306,9 +308,8 @@ __global__ void __launch_bounds__(NT) k_subspace(
   T* Yc = base + 2 * blk;
   T* T1 = base + 3 * blk;
   T* KY = base + 4 * blk; // K Y (dim x s)
-  T* MY = base + 5 * blk; // S Y (SPD)
-  T* V = base + 6 * blk;  // p x s
-  T* AV = base + 7 * blk; // p x s  (general: g x s)
+  T* V = base + 5 * blk;  // p x s
+  T* AV = base + 6 * blk; // p x s  (general: g x s)
   // shared memory: GEMM tiles, then the small dense matrices
   T* gsm = reinterpret_cast<T*>(shd);
   double* G = shd + (sizeof(T) * (GM * (GK + 1) + GK * GN) + 7) / 8;
@@ -326,9 +327,9 @@ __global__ void __launch_bounds__(NT) k_subspace(
   // Column c0.. c0+nc-1 of the blocks (stride sp).
   auto applyK = [&](const T* Yin, T* out, int c0, int nc) {
     if (SPD) {
-      cta_gemm<T, true>(p, nc, g, XpT, p, Yin + c0, sp, V + c0, sp, gsm);          // V = X_p Y
+      cta_gemm<T, true>(p, nc, g, U, ld, Yin + c0, sp, V + c0, sp, gsm);           // V = U^T Y
       mul_AII(p, pos0, omega, rp, ci, val, ds, ent_off, lcol, V + c0, AV + c0, nc, sp);
-      cta_gemm<T, false>(g, nc, p, XpT, p, AV + c0, sp, out + c0, sp, gsm);        // X_p^T (A V)
+      cta_gemm<T, false>(g, nc, p, U, ld, AV + c0, sp, out + c0, sp, gsm);         // U (A^_II V)
     } else {
       // W = X_p^T Y = S_G^{-1} X^_p^T S_I Y ; out = X_p W = S_I X^_p S_G^{-1} W
       cta_gemm<T, false>(g, nc, p, XpT, p, Yin + c0, sp, AV + c0, sp, gsm, Scale(), sI, false);
@@ -340,28 +341,20 @@ __global__ void __launch_bounds__(NT) k_subspace(
       cta_gemm<T, true>(p, nc, g, XpT, p, AV + c0, sp, out + c0, sp, gsm, sI, sG, true);
     }
   };
-  // OP given K y: SPD: S^{-1} (K y); general: K y itself
+  // the operator is K itself in both cases (Euclidean metric)
   auto applyR = [&](const T* KYin, T* out, int c0, int nc) {
-    if (SPD) {
-      cta_gemm<T, false>(g, nc, g, R, ld, KYin + c0, sp, out + c0, sp, gsm);
-    } else {
-      for (int64_t idx = threadIdx.x; idx < (int64_t)dim * nc; idx += NT) {
-        int64_t r = idx / nc, j = c0 + idx % nc;
-        out[r * sp + j] = KYin[r * sp + j];
-      }
-      __syncthreads();
+    for (int64_t idx = threadIdx.x; idx < (int64_t)dim * nc; idx += NT) {
+      int64_t r = idx / nc, j = c0 + idx % nc;
+      out[r * sp + j] = KYin[r * sp + j];
     }
+    __syncthreads();
   };
-  auto applyM = [&](const T* Yin, T* out) {
-    if (SPD) cta_gemm<T, false>(g, s, g, Smat, g, Yin, sp, out, sp, gsm);
-  };
-  // W[:, c0:] -= Y_L (MY_L^T W[:, c0:]) with Y_L = the first c0 columns of Y
-  // (S-orthonormal, MY_L = S Y_L): keeps the active block S-orthogonal to the
-  // locked Ritz vectors.
+  // W[:, c0:] -= Y_L (Y_L^T W[:, c0:]) with Y_L = the first c0 (orthonormal)
+  // columns of Y: keeps the active block orthogonal to the locked Ritz vectors.
   T* Pt = Pbuf;
   auto deflate = [&](T* W, int c0, int nc) {
     if (c0 == 0) return;
-    cta_gemm<T, true>(c0, nc, dim, SPD ? MY : Y, sp, W + c0, sp, Pt, nc, gsm);
+    cta_gemm<T, true>(c0, nc, dim, Y, sp, W + c0, sp, Pt, nc, gsm);
     cta_gemm<T, false, true>(dim, nc, c0, Y, sp, Pt, nc, W + c0, sp, gsm);
   };
   auto swap = [](T*& a, T*& b) { T* t = a; a = b; b = t; };
@@ -370,27 +363,23 @@ __global__ void __launch_bounds__(NT) k_subspace(
   const double tiny = sizeof(T) == 8 ? 1e-10 : 1e-5;
   auto orthonormalize = [&](uint64_t salt) {
     for (int attempt = 0; attempt < 4; ++attempt) {
-      if (attempt > 0) applyM(Y, MY);
       for (int j = 0; j < s; ++j) {
         T part = 0;
         for (int r = threadIdx.x; r < dim; r += NT)
-          part += Y[(int64_t)r * sp + j] * (SPD ? MY[(int64_t)r * sp + j] : Y[(int64_t)r * sp + j]);
+          part += Y[(int64_t)r * sp + j] * Y[(int64_t)r * sp + j];
         part = block_sum(part, red);
         if (threadIdx.x == 0) Pbuf[j] = part > T(0) ? T(1) / sqrt(part) : T(1);
       }
       __syncthreads();
       for (int64_t idx = threadIdx.x; idx < (int64_t)dim * sp; idx += NT) {
         int j = (int)(idx % sp);
-        if (j < s) {
-          Y[idx] *= Pbuf[j];
-          if (SPD) MY[idx] *= Pbuf[j];
-        }
+        if (j < s) Y[idx] *= Pbuf[j];
       }
       __syncthreads();
       bool ok = true;
       for (int pass = 0; pass < 2 && ok; ++pass) {
         T* Gt = QS;  // s*s scratch in T
-        cta_gemm<T, true>(s, s, dim, Y, sp, SPD ? MY : Y, sp, Gt, s, gsm);
+        cta_gemm<T, true>(s, s, dim, Y, sp, Y, sp, Gt, s, gsm);
         for (int idx = threadIdx.x; idx < s * s; idx += NT) {
           int a = idx / s, b = idx % s;
           G[idx] = 0.5 * ((double)Gt[a * s + b] + (double)Gt[b * s + a]);
@@ -411,10 +400,6 @@ __global__ void __launch_bounds__(NT) k_subspace(
         __syncthreads();
         cta_gemm<T, false>(dim, s, s, Y, sp, QS, s, Yb, sp, gsm);
         swap(Y, Yb);
-        if (SPD) {
-          cta_gemm<T, false>(dim, s, s, MY, sp, QS, s, Yb, sp, gsm);
-          swap(MY, Yb);
-        }
       }
       if (ok) return;
     }
@@ -430,7 +415,6 @@ __global__ void __launch_bounds__(NT) k_subspace(
     }
     __syncthreads();
   }
-  applyM(Y, MY);
   orthonormalize((uint64_t)i);
 
   int sweep = 0;
@@ -447,14 +431,13 @@ __global__ void __launch_bounds__(NT) k_subspace(
     sort_desc(H, Q, QS, mu, perm, s);
     cta_gemm<T, false>(dim, s, s, Y, sp, QS, s, Yb, sp, gsm); swap(Y, Yb);
     cta_gemm<T, false>(dim, s, s, KY, sp, QS, s, Yb, sp, gsm); swap(KY, Yb);
-    if (SPD) { cta_gemm<T, false>(dim, s, s, MY, sp, QS, s, Yb, sp, gsm); swap(MY, Yb); }
     // ---- residuals of the first k Ritz pairs
     const T mu0 = mu[0] > T(0) ? mu[0] : T(1);
     for (int j = 0; j < k; ++j) {
       T part = 0, nrm = 0;
       for (int r = threadIdx.x; r < dim; r += NT) {
         T a = KY[(int64_t)r * sp + j];
-        T b = SPD ? MY[(int64_t)r * sp + j] : Y[(int64_t)r * sp + j];
+        T b = Y[(int64_t)r * sp + j];
         T d = a - mu[j] * b;
         part += d * d;
         nrm += b * b;
@@ -530,7 +513,6 @@ __global__ void __launch_bounds__(NT) k_subspace(
     for (int j = 0; j < s; ++j)
       if (!(mu[j] > T(1e-10) * mu0)) { first_null = j; break; }
     if (first_null < s) fill_random(Y, dim, s, sp, first_null, seed ^ 0xA5A5A5A5ull, (uint64_t)i * 7919u + sweep * 104729u);
-    applyM(Y, MY);
     orthonormalize((uint64_t)i * 1000003u + sweep);
   }
   // ---- outputs
@@ -548,8 +530,8 @@ __global__ void __launch_bounds__(NT) k_subspace(
   }
   double* Zi = Z + z_off[i];
   if (SPD) {
-    // Z_i = S_I X^_p y (undo the diagonal scaling), FP64 output p x nev
-    cta_gemm<T, true>(p, s, g, XpT, p, Y, sp, V, sp, gsm);
+    // Z_i = S_I U^T z (undo the diagonal scaling), FP64 output p x nev
+    cta_gemm<T, true>(p, s, g, U, ld, Y, sp, V, sp, gsm);
     for (int64_t idx = threadIdx.x; idx < (int64_t)p * nev; idx += NT) {
       int r = (int)(idx / nev), j = (int)(idx % nev);
       Zi[idx] = j < kept ? (double)V[(int64_t)r * sp + j] * ds[omega[pos0 + r]] : 0.0;
@@ -580,7 +562,7 @@ void run_eigen(Handle& h, cudaStream_t s) {
     int sp = (sb + 3) & ~3;
     smax = std::max(smax, sb);
     scr[i] = tot;
-    tot += 8LL * std::max(p, g) * sp;
+    tot += 7LL * std::max(p, g) * sp;
     zo[i] = zt;
     zt += (int64_t)p * nev;
   }

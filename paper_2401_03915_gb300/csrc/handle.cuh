@@ -47,12 +47,15 @@ struct Dense {
   int64_t* tile_off = nullptr;
   int64_t* part_off = nullptr;
   int4* tile_desc = nullptr;          // (subdomain, I, J, 0) of every apply tile
-  void* work = nullptr;               // A_ii, then A_ii^{-1} (row-major, ld = np)
-  void* XpT = nullptr;                // X_p^T = -(B^{-1} C)[:p]^T   (g x p)
-  void* S = nullptr;                  // S = G - C^T B^{-1} C        (g x g)
+  void* work = nullptr;               // A^_ii, then W = L^{-1} (SPD) or A^_ii^{-1} (row-major, ld = np)
+  void* XpT = nullptr;                // general A: X_p^T = -(B^{-1} C)[:p]^T (g x p)
+  void* S = nullptr;                  // unused
+  void* dinv = nullptr;               // SPD: inverses of the diagonal 64x64 blocks of L
+  int64_t* dinv_off = nullptr;
   void* tiles = nullptr;              // apply tiles, TILE*TILE each
   void* partials = nullptr;           // per (subdomain, I, J) TILE partial sums
   double* ypos = nullptr;             // per omega position: local solution before the pull
+  double* tpos = nullptr;             // per omega position: W x (SPD apply, first pass)
   int64_t n_tiles = 0, n_work = 0, n_xs = 0, n_s = 0, n_part = 0;
   int32_t* err = nullptr;             // device error word
 };

@@ -1,6 +1,9 @@
-// Local dense stage: gather A_ii out of CSR A (Section 2.3), invert it in
-// place by a blocked Gauss-Jordan sweep, and pack the inverse into the tiles
-// the apply streams.
+// Local dense stage: gather A_ii out of CSR A (Section 2.3), factor it, and
+// pack the result into the tiles the apply streams.
+//
+// SPD A: blocked Cholesky and triangular inverse W = L^{-1} (k_chol_trtri);
+// the apply multiplies by W^T W and the eigen stage reads the block
+// W[Gamma_delta, I_i].  General A: blocked Gauss-Jordan sweep (k_sweep).
 //
 // What is gathered is the symmetrically scaled A^_ii = D^{-1/2} A_ii D^{-1/2},
 // D = diag(A): A_ii^{-1} = D^{-1/2} A^_ii^{-1} D^{-1/2}, and the scaling maps
@@ -11,14 +14,12 @@
 //
 // The sweep eliminates the unknowns of Omega_{i,1:delta-1} first.  At that
 // midpoint the working matrix holds
-//     [ B^{-1}         B^{-1} C          ]
-//     [ -C^T B^{-1}    G - C^T B^{-1} C  ]      (general A: -A_{Gamma,Omega'} B^{-1})
+//     [ B^{-1}                 B^{-1} C                  ]
+//     [ -A_{Gamma,Omega'} B^{-1}   G - A_{Gamma,Omega'} B^{-1} C ]
 // with B = A_{Omega_{1:delta-1}}, C = A_{Omega_{1:delta-1}, Gamma_delta} and
 // G = A_{Gamma_delta, Gamma_delta}: the block -B^{-1} C of the harmonic
-// operator Pi_i (eq. HOp) and the Schur complement S = G - C^T B^{-1} C.
-// Their first |I_i| rows X_p = -(B^{-1}C)[:p] and S are copied out; the sweep
-// then continues over Gamma_delta and leaves A_ii^{-1}, whose trailing block
-// is S^{-1}.
+// operator Pi_i (eq. HOp).  Its first |I_i| rows X_p = -(B^{-1}C)[:p] are
+// copied out; the sweep then continues over Gamma_delta and leaves A_ii^{-1}.
 #include <algorithm>
 
 #include "handle.cuh"
@@ -218,14 +219,199 @@ __global__ void __launch_bounds__(NT) k_sweep(T* __restrict__ work, const int64_
           }
         }
       }
-      T* Sg = Sout + s_off[i];
-      for (int64_t idx = tid; idx < (int64_t)g * g; idx += NT) {
-        int a = (int)(idx / g), b = (int)(idx % g);
-        Sg[idx] = M[(int64_t)(m + a) * ld + m + b];
-      }
       __syncthreads();
     }
     k0 = k1;
+  }
+}
+
+// SPD local factor: blocked Cholesky A^_ii = L L^T (right-looking) followed by
+// the blocked triangular inverse W = L^{-1}, both in place in the lower
+// triangle, one block per subdomain, 64 x 64 blocks.  The apply multiplies by
+// W^T W = A^_ii^{-1}: symmetric positive definite for any rounding of W, and
+// accurate to about cond(A^_ii) * eps (an explicitly inverted A^_ii^{-1} would
+// only be accurate to cond^2 * eps).  Dinv receives the inverses of the
+// diagonal blocks of L (which are the diagonal blocks of W).
+template <typename T>
+__device__ __forceinline__ void block_mma(T (&acc)[4][4], const T (*Am)[TILE + 1], const T (*Bm)[TILE + 1],
+                                          bool btrans, int tx, int ty) {
+  // acc += Am * (btrans ? Bm^T : Bm) on 64 x 64 blocks; thread owns rows ty+16a, cols tx+16b
+  for (int q = 0; q < TILE; ++q) {
+    T av[4], bv[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) av[a] = Am[ty + 16 * a][q];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) bv[b] = btrans ? Bm[tx + 16 * b][q] : Bm[q][tx + 16 * b];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] += av[a] * bv[b];
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT) k_chol_trtri(T* __restrict__ work, const int64_t* __restrict__ work_off,
+                                                   const int32_t* __restrict__ np_arr,
+                                                   const int32_t* __restrict__ n_arr, T* __restrict__ dinv_all,
+                                                   const int64_t* __restrict__ dinv_off, int32_t* err) {
+  COUNT_LAUNCH();
+  extern __shared__ unsigned char smraw[];
+  T (*Dm)[TILE + 1] = reinterpret_cast<T (*)[TILE + 1]>(smraw);
+  T (*Xm)[TILE + 1] = Dm + TILE;
+  T (*Ym)[TILE + 1] = Xm + TILE;
+  __shared__ int bad;
+  const int i = blockIdx.x;
+  const int n = n_arr[i], ld = np_arr[i];
+  T* M = work + work_off[i];
+  T* Dinv = dinv_all + dinv_off[i];
+  const int nt = (n + TILE - 1) / TILE;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  auto blk = [&](int rb, int cb) { return M + (int64_t)rb * TILE * ld + cb * TILE; };
+  auto load = [&](T (*S)[TILE + 1], int rb, int cb) {
+    const T* B = blk(rb, cb);
+    const int rw = min(TILE, n - rb * TILE), cw = min(TILE, n - cb * TILE);
+    for (int idx = tid; idx < TILE * TILE; idx += NT) {
+      int r = idx / TILE, c = idx % TILE;
+      S[r][c] = (r < rw && c < cw) ? B[(int64_t)r * ld + c] : T(0);
+    }
+  };
+  if (tid == 0) bad = 0;
+  // ---------------- phase 1: Cholesky
+  for (int kb = 0; kb < nt; ++kb) {
+    const int kw = min(TILE, n - kb * TILE);
+    __syncthreads();
+    {
+      const T* B = blk(kb, kb);
+      for (int idx = tid; idx < TILE * TILE; idx += NT) {
+        int r = idx / TILE, c = idx % TILE;
+        T v = (r < kw && c < kw) ? B[(int64_t)max(r, c) * ld + min(r, c)] : (r == c ? T(1) : T(0));
+        Dm[r][c] = v;
+      }
+    }
+    __syncthreads();
+    for (int j = 0; j < TILE; ++j) {
+      if (tid == 0) {
+        T d = Dm[j][j];
+        if (!(d > T(0)) || !isfinite((double)d)) { bad = 1; d = T(1); }
+        Dm[j][j] = sqrt(d);
+      }
+      __syncthreads();
+      if (bad) break;
+      for (int r = j + 1 + tid; r < TILE; r += NT) Dm[r][j] /= Dm[j][j];
+      __syncthreads();
+      for (int idx = tid; idx < TILE * TILE; idx += NT) {
+        int r = idx / TILE, c = idx % TILE;
+        if (c > j && r >= c) Dm[r][c] -= Dm[r][j] * Dm[c][j];
+      }
+      __syncthreads();
+    }
+    if (bad) {
+      if (tid == 0) atomicOr(err, DERR_NOT_SPD);
+      return;
+    }
+    // inverse of the lower diagonal block (column c by thread c)
+    if (tid < TILE) {
+      const int c = tid;
+      for (int r = 0; r < c; ++r) Xm[r][c] = 0;
+      for (int r = c; r < TILE; ++r) {
+        T v = r == c ? T(1) : T(0);
+        for (int t = c; t < r; ++t) v -= Dm[r][t] * Xm[t][c];
+        Xm[r][c] = v / Dm[r][r];
+      }
+    }
+    __syncthreads();
+    {
+      T* B = blk(kb, kb);
+      T* Dv = Dinv + (int64_t)kb * TILE * TILE;
+      for (int idx = tid; idx < TILE * TILE; idx += NT) {
+        int r = idx / TILE, c = idx % TILE;
+        if (r < kw && c < kw && c <= r) B[(int64_t)r * ld + c] = Dm[r][c];
+        Dv[idx] = Xm[r][c];
+      }
+    }
+    // panel: L_rk = A_rk Dinv^T
+    for (int rb = kb + 1; rb < nt; ++rb) {
+      __syncthreads();
+      load(Ym, rb, kb);
+      __syncthreads();
+      T acc[4][4] = {};
+      block_mma<T>(acc, Ym, Xm, true, tx, ty);
+      const int rw = min(TILE, n - rb * TILE);
+      T* B = blk(rb, kb);
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          int r = ty + 16 * a, c = tx + 16 * b;
+          if (r < rw && c < kw) B[(int64_t)r * ld + c] = acc[a][b];
+        }
+    }
+    // trailing update: A_rc -= L_rk L_ck^T, c <= r
+    for (int rb = kb + 1; rb < nt; ++rb) {
+      __syncthreads();
+      load(Ym, rb, kb);
+      for (int cb = kb + 1; cb <= rb; ++cb) {
+        __syncthreads();
+        load(Dm, cb, kb);
+        __syncthreads();
+        T acc[4][4] = {};
+        block_mma<T>(acc, Ym, Dm, true, tx, ty);
+        const int rw = min(TILE, n - rb * TILE), cw = min(TILE, n - cb * TILE);
+        T* B = blk(rb, cb);
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            int r = ty + 16 * a, c = tx + 16 * b;
+            if (r < rw && c < cw && (cb < rb || c <= r)) B[(int64_t)r * ld + c] -= acc[a][b];
+          }
+      }
+    }
+  }
+  // ---------------- phase 2: W = L^{-1}, block column by block column
+  for (int jb = 0; jb < nt; ++jb) {
+    const int jw = min(TILE, n - jb * TILE);
+    __syncthreads();
+    {
+      T* B = blk(jb, jb);
+      const T* Dv = Dinv + (int64_t)jb * TILE * TILE;
+      for (int idx = tid; idx < TILE * TILE; idx += NT) {
+        int r = idx / TILE, c = idx % TILE;
+        if (r < jw && c < jw) B[(int64_t)r * ld + c] = c <= r ? Dv[idx] : T(0);
+      }
+    }
+    for (int ib = jb + 1; ib < nt; ++ib) {
+      T acc[4][4] = {};
+      for (int kb = jb; kb < ib; ++kb) {
+        __syncthreads();
+        load(Ym, ib, kb);   // L_ik (kb >= jb: not yet overwritten)
+        load(Xm, kb, jb);   // W_kj (kb < ib: already computed)
+        __syncthreads();
+        block_mma<T>(acc, Ym, Xm, false, tx, ty);
+      }
+      __syncthreads();
+      // W_ij = -Dinv_i acc
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) Xm[ty + 16 * a][tx + 16 * b] = acc[a][b];
+      {
+        const T* Dv = Dinv + (int64_t)ib * TILE * TILE;
+        for (int idx = tid; idx < TILE * TILE; idx += NT) Ym[idx / TILE][idx % TILE] = Dv[idx];
+      }
+      __syncthreads();
+      T w[4][4] = {};
+      block_mma<T>(w, Ym, Xm, false, tx, ty);
+      const int rw = min(TILE, n - ib * TILE);
+      T* B = blk(ib, jb);
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          int r = ty + 16 * a, c = tx + 16 * b;
+          if (r < rw && c < jw) B[(int64_t)r * ld + c] = -w[a][b];
+        }
+    }
   }
 }
 
@@ -271,9 +457,12 @@ void run_local(Handle& h, cudaStream_t s) {
     dn.h_work_off[i] = w;
     w += (int64_t)np * np;
     dn.h_xs_off[i] = xs;
-    xs += (int64_t)h.h_g[i] * h.h_p[i];
     dn.h_s_off[i] = ss;
-    ss += (int64_t)h.h_g[i] * h.h_g[i];
+    if (spd) {
+      ss += (int64_t)nt * TILE * TILE;  // inverses of the diagonal blocks of L
+    } else {
+      xs += (int64_t)h.h_g[i] * h.h_p[i];
+    }
     dn.h_tile_off[i] = tl;
     for (int I = 0; I < nt; ++I)
       for (int J = 0; J < (spd ? I + 1 : nt); ++J) desc.push_back(make_int4(i, I, J, 0));
@@ -308,11 +497,13 @@ void run_local(Handle& h, cudaStream_t s) {
   CK(cudaMemcpyAsync(d_p, h.h_p.data(), 4 * N, cudaMemcpyHostToDevice, s));
   T* work = mem.alloc<T>(w);
   dn.work = work;
-  dn.XpT = mem.alloc<T>(xs);
-  dn.S = mem.alloc<T>(ss);
+  dn.XpT = mem.alloc<T>(std::max<int64_t>(xs, 1));
+  dn.dinv = mem.alloc<T>(std::max<int64_t>(ss, 1));
+  dn.dinv_off = dn.s_off;
   dn.tiles = mem.alloc<T>(tl * TILE * TILE);
   dn.partials = mem.alloc<T>(pt);
   dn.ypos = mem.alloc<double>(ov.sum_n);
+  dn.tpos = mem.alloc<double>(ov.sum_n);
   h.dev_n = d_n; h.dev_m = d_m; h.dev_p = d_p;
   // -- gather A_ii
   CK(cudaMemsetAsync(work, 0, sizeof(T) * w, s));
@@ -323,14 +514,16 @@ void run_local(Handle& h, cudaStream_t s) {
                                 ov.lcol, dn.work_off, dn.np, work);
   CK_LAUNCH("gather A_ii");
   if (h.events) CK(cudaEventRecord(h.ev[3], s));
-  // -- sweep
-  if (spd)
-    k_sweep<T, true><<<N, NT, 0, s>>>(work, dn.work_off, dn.np, d_n, d_m, d_p, (T*)dn.XpT, dn.xs_off,
-                                      (T*)dn.S, dn.s_off, dn.err);
-  else
+  // -- local factor
+  if (spd) {
+    const size_t sm3 = sizeof(T) * 3 * TILE * (TILE + 1);
+    CK(cudaFuncSetAttribute(k_chol_trtri<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3));
+    k_chol_trtri<T><<<N, NT, sm3, s>>>(work, dn.work_off, dn.np, d_n, (T*)dn.dinv, dn.dinv_off, dn.err);
+  } else {
     k_sweep<T, false><<<N, NT, 0, s>>>(work, dn.work_off, dn.np, d_n, d_m, d_p, (T*)dn.XpT, dn.xs_off,
                                        (T*)dn.S, dn.s_off, dn.err);
-  CK_LAUNCH("local sweep");
+  }
+  CK_LAUNCH("local factor");
   if (h.events) CK(cudaEventRecord(h.ev[4], s));
   // -- pack the apply tiles
   unsigned gp = (unsigned)std::min<int64_t>(std::max<int64_t>(tl, 1), 152 * 8);

@@ -254,9 +254,13 @@ def test_gevpsvd_structure_and_splitting(delta):
 
 
 def test_reduced_interface_form_matches_full_gevp():
-    """The CUDA path solves K y = mu S y on Gamma_delta with K = X_p^T A_II X_p,
-    X = -B^{-1} C, S = G - C^T B^{-1} C.  Its nonzero spectrum must equal the
-    nonzero spectrum of eq. gevpsvd, and [X_p y; 0] must span D Pi W^(1)."""
+    """The CUDA path reduces eq. gevpsvd to Gamma_delta.  With X = -B^{-1} C,
+    X_p its first |I_i| rows, S = G - C^T B^{-1} C and K = X_p^T A_II X_p, the
+    nonzero spectrum of eq. gevpsvd is that of K y = mu S y, and [X_p y; 0]
+    spans D Pi W^(1).  With A_ii = L L^T, W = L^{-1} and U = W[Gamma, I], the
+    same spectrum is that of the symmetric U A_II U^T z = mu z and X_p y = U^T z
+    (what the kernels compute).  Both forms are checked against the dense
+    full-size eigenproblem."""
     for delta in (1, 2):
         A = random_spd(90, 41)
         part = contiguous_part(90, 3)
@@ -273,13 +277,22 @@ def test_reduced_interface_form_matches_full_gevp():
             red = red[::-1]; Y = Y[:, ::-1]
             nz = int(np.sum(mu > 1e-10))
             np.testing.assert_allclose(red[:nz], mu[:nz], rtol=1e-9)
+            Linv = np.linalg.inv(np.linalg.cholesky(Aii))
+            U = Linv[m:, :p]
+            sym = U @ Aii[:p, :p] @ U.T
+            ev, Zs = np.linalg.eigh(0.5 * (sym + sym.T))
+            ev = ev[::-1]; Zs = Zs[:, ::-1]
+            np.testing.assert_allclose(ev[:nz], mu[:nz], rtol=1e-9)
             k = min(3, nz)
             Zfull = (np.diag(O.pou(ov)) @ Pi @ W[:, :k])[:p]
-            Zred = Xp @ Y[:, :k]
             if k and (mu[k - 1] - mu[k]) / mu[k - 1] > 1e-6:
                 P1 = Zfull @ np.linalg.pinv(Zfull)
-                P2 = Zred @ np.linalg.pinv(Zred)
-                np.testing.assert_allclose(P1, P2, atol=1e-8)
+                for Zred in (Xp @ Y[:, :k], U.T @ Zs[:, :k]):
+                    np.testing.assert_allclose(Zred @ np.linalg.pinv(Zred), P1, atol=1e-8)
+                # A_ii-normalised w and unit z give coarse vectors of A_II-energy mu
+                Zr = U.T @ Zs[:, :k]
+                np.testing.assert_allclose(np.einsum("ij,ij->j", Zr, Aii[:p, :p] @ Zr), ev[:k], rtol=1e-8)
+                np.testing.assert_allclose(np.einsum("ij,ij->j", Zfull, Aii[:p, :p] @ Zfull), mu[:k], rtol=1e-8)
 
 
 # ---------------------------------------------------------------------------
