@@ -251,10 +251,22 @@ void apply_pull(Handle& h, const double* yc, double* z, cudaStream_t s, const in
                                  co.Z, co.z_off, co.count, co.col_off, h.nev, yc, h.dscale, z, done);
 }
 
+// The coarse part (Z^T r, the level-by-level coarse solve) is independent of
+// the local part until the pull: it runs on the handle's side stream, forked
+// from and joined back into `s` with events (also inside a graph capture).
 template <typename T>
 void apply_impl(Handle& h, const double* r, double* z, cudaStream_t s, const int32_t* done) {
+  const double* yc = nullptr;
+  const bool fork = h.co.n_C > 0 && h.side != nullptr;
+  if (fork) {
+    CK(cudaEventRecord(h.ev_fork, s));
+    CK(cudaStreamWaitEvent(h.side, h.ev_fork, 0));
+    yc = apply_coarse(h, r, h.side, done);
+    CK(cudaEventRecord(h.ev_join, h.side));
+  }
   apply_local<T>(h, r, s, done);
-  const double* yc = apply_coarse(h, r, s, done);
+  if (fork) CK(cudaStreamWaitEvent(s, h.ev_join, 0));
+  else yc = apply_coarse(h, r, s, done);
   apply_pull<T>(h, yc, z, s, done);
 }
 

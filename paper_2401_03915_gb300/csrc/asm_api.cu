@@ -58,6 +58,9 @@ void free_handle_memory(Handle& h) {
   if (h.events)
     for (auto& e : h.ev) cudaEventDestroy(e);
   h.events = false;
+  if (h.side) { cudaStreamDestroy(h.side); h.side = nullptr; }
+  if (h.ev_fork) { cudaEventDestroy(h.ev_fork); h.ev_fork = nullptr; }
+  if (h.ev_join) { cudaEventDestroy(h.ev_join); h.ev_join = nullptr; }
   cudaGetLastError();
 }
 
@@ -150,6 +153,9 @@ asm_status asm_setup(const asm_csr* A, const int32_t* part, int32_t N, int32_t o
     h.mem.stream = s;
     for (auto& e : h.ev) CK(cudaEventCreate(&e));
     h.events = true;
+    CK(cudaStreamCreateWithFlags(&h.side, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&h.ev_fork, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&h.ev_join, cudaEventDisableTiming));
     CK(cudaEventRecord(h.ev[0], s));
     h.row_ptr = h.mem.alloc<int32_t>(h.n + 1);
     h.col_idx = h.mem.alloc<int32_t>(h.nnz);

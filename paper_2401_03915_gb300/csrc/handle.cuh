@@ -115,6 +115,8 @@ struct Handle {
   asm_setup_info info{};
   cudaEvent_t ev[16];
   bool events = false;
+  cudaStream_t side = nullptr;      // second stream: the coarse part of the apply runs beside the local part
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 // Stage entry points (each enqueues on `s`; host reads are explicit).
