@@ -89,6 +89,7 @@ struct Krylov {
   double* V = nullptr;      // FGMRES basis (restart+1) x n
   double* ZB = nullptr;     // FGMRES preconditioned basis restart x n
   double* H = nullptr;      // Hessenberg and rotations
+  double* mpart = nullptr;  // multi-dot partial sums
   int32_t restart = 0;
   double* bx = nullptr;     // device copies of b, x for host-pointer solves
   double* hpin = nullptr;   // pinned host staging

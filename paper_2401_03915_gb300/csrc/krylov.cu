@@ -300,10 +300,215 @@ void solve_pcg(Handle& h, const double* b, double* x, const asm_solve_opts& o, a
   info.solve_ms = ms;
 }
 
+namespace {
+
+constexpr int MAXV = 65;  // restart length + 1
+
+// part[b * MAXV + k] = partial sums of V_k . w over the block's rows, k < nvec
+__global__ void __launch_bounds__(NT) k_multidot(int n, const double* __restrict__ V, int nvec,
+                                                 const double* __restrict__ w, double* __restrict__ part) {
+  COUNT_LAUNCH();
+  __shared__ double red[NT / 32];
+  for (int k = 0; k < nvec; ++k) {
+    const double* v = V + (int64_t)k * n;
+    double s = 0;
+    for (int i = blockIdx.x * NT + threadIdx.x; i < n; i += gridDim.x * NT) s += v[i] * w[i];
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) part[blockIdx.x * MAXV + k] = s;
+  }
+}
+
+// out[k] = sum_b part[b * MAXV + k] (fixed order)
+__global__ void __launch_bounds__(NT) k_multidot_fin(const double* __restrict__ part, int nb, int nvec,
+                                                     double* __restrict__ out) {
+  COUNT_LAUNCH();
+  __shared__ double red[NT / 32];
+  for (int k = 0; k < nvec; ++k) {
+    double s = 0;
+    for (int b = threadIdx.x; b < nb; b += NT) s += part[b * MAXV + k];
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) out[k] = s;
+  }
+}
+
+// w -= sum_k V_k c_k
+__global__ void __launch_bounds__(NT) k_sub_vc(int n, const double* __restrict__ V, int nvec,
+                                               const double* __restrict__ c, double* __restrict__ w) {
+  COUNT_LAUNCH();
+  for (int i = blockIdx.x * NT + threadIdx.x; i < n; i += gridDim.x * NT) {
+    double s = 0;
+    for (int k = 0; k < nvec; ++k) s += V[(int64_t)k * n + i] * c[k];
+    w[i] -= s;
+  }
+}
+
+// x += sum_k Zb_k y_k
+__global__ void __launch_bounds__(NT) k_add_zy(int n, const double* __restrict__ Zb, int nvec,
+                                               const double* __restrict__ y, double* __restrict__ x) {
+  COUNT_LAUNCH();
+  for (int i = blockIdx.x * NT + threadIdx.x; i < n; i += gridDim.x * NT) {
+    double s = 0;
+    for (int k = 0; k < nvec; ++k) s += Zb[(int64_t)k * n + i] * y[k];
+    x[i] += s;
+  }
+}
+
+// out = a / nrm with nrm = sqrt(sum of partials); stores nrm in *dst
+__global__ void __launch_bounds__(NT) k_normalize(int n, const double* __restrict__ part, int nb,
+                                                  const double* __restrict__ a, double* __restrict__ out,
+                                                  double* __restrict__ dst) {
+  COUNT_LAUNCH();
+  double s = sum_partials(part, nb);
+  const double nrm = sqrt(s);
+  if (blockIdx.x == 0 && threadIdx.x == 0) *dst = nrm;
+  const double inv = nrm > 0 ? 1.0 / nrm : 0.0;
+  for (int i = blockIdx.x * NT + threadIdx.x; i < n; i += gridDim.x * NT) out[i] = a[i] * inv;
+}
+
+// Column j of the Hessenberg matrix (col[0..j+1]): apply the previous Givens
+// rotations, build the new one, update g; residual estimate |g[j+1]| / ||b||.
+// g[0] is set to beta at each restart.  flag: [0] done, [1] iterations.
+__global__ void k_givens(double* H, int ldh, int j, double* cs, double* sn, double* g, const double* scal,
+                         int32_t* flag, double* hist, int hist_len) {
+  COUNT_LAUNCH();
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (flag[0]) return;  // converged earlier in this chunk: the extra columns are ignored
+  double* col = H + (int64_t)j * ldh;
+  for (int k = 0; k < j; ++k) {
+    double t = cs[k] * col[k] + sn[k] * col[k + 1];
+    col[k + 1] = -sn[k] * col[k] + cs[k] * col[k + 1];
+    col[k] = t;
+  }
+  double den = hypot(col[j], col[j + 1]);
+  double c = den > 0 ? col[j] / den : 1.0, sv = den > 0 ? col[j + 1] / den : 0.0;
+  cs[j] = c; sn[j] = sv;
+  col[j] = den; col[j + 1] = 0;
+  g[j + 1] = -sv * g[j];
+  g[j] = c * g[j];
+  int it = ++flag[1];
+  double rel = fabs(g[j + 1]) / scal[5];
+  if (hist != nullptr && it < hist_len) hist[it] = rel;
+  if (rel <= scal[6]) flag[0] = 1;
+  else if (it >= flag[2] || !isfinite(rel)) flag[0] = 3;
+  if (flag[0]) flag[3] = j + 1;  // columns of this cycle that enter the update
+  // keep the estimate for the host
+  ((double*)scal)[7] = rel;
+}
+
+// y = H(0:k, 0:k)^{-1} g(0:k) (upper triangular); k from the device when the
+// cycle stopped on convergence, else the host's count
+__global__ void k_backsolve(const double* H, int ldh, int khost, const int32_t* flag, const double* g, double* y) {
+  COUNT_LAUNCH();
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int k = flag[0] ? flag[3] : khost;
+  for (int r = k; r < khost; ++r) y[r] = 0;
+  for (int r = k - 1; r >= 0; --r) {
+    double s = g[r];
+    for (int c = r + 1; c < k; ++c) s -= H[(int64_t)c * ldh + r] * y[c];
+    y[r] = s / H[(int64_t)r * ldh + r];
+  }
+}
+
+}  // namespace
+
 void solve_fgmres(Handle& h, const double* b, double* x, const asm_solve_opts& o, asm_solve_info& info,
                   cudaStream_t s) {
-  (void)h; (void)b; (void)x; (void)o; (void)info; (void)s;
-  fail(ASM_ERR_UNSUPPORTED, "FGMRES is not available in this build");
+  ensure_krylov(h);
+  Krylov& kr = h.kr;
+  const int n = h.n;
+  const int m = std::max(1, std::min(o.restart, MAXV - 1));
+  const int ldh = m + 1;
+  DevMem& mem = h.mem;
+  if (!kr.V || kr.restart != m) {
+    kr.V = mem.alloc<double>((int64_t)(m + 1) * n);
+    kr.ZB = mem.alloc<double>((int64_t)m * n);
+    kr.H = mem.alloc<double>((int64_t)ldh * m + 4 * ldh + 16);
+    kr.mpart = mem.alloc<double>((int64_t)NBLK * MAXV);
+    kr.restart = m;
+  }
+  double* H = kr.H;
+  double* cs = H + (int64_t)ldh * m;
+  double* sn = cs + ldh;
+  double* g = sn + ldh;
+  double* y = g + ldh;
+  double* tmp = kr.w;  // n
+  const unsigned vg = NBLK;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  CK(cudaEventRecord(e0, s));
+  k_dot<<<vg, NT, 0, s>>>(n, b, b, kr.part, nullptr);
+  k_init_scalars<<<1, NT, 0, s>>>(kr.scal, kr.flag, kr.part, NBLK, o.rtol, o.max_it, 0);
+  if (!o.use_x0) CK(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
+  int32_t* hflag = reinterpret_cast<int32_t*>(kr.hpin);
+  const int check = std::max(1, o.check_every > 0 ? o.check_every : 8);
+  int total = 0;
+  bool done = false;
+  while (!done) {
+    // restart: r = b - A x, beta, v_0, g = beta e_1
+    spmv_any(h, x, kr.q, nullptr, nullptr, false, s);
+    k_axpby<<<vgrid(n), NT, 0, s>>>(n, kr.r, b, kr.q, -1.0);
+    k_dot<<<vg, NT, 0, s>>>(n, kr.r, kr.r, kr.part, nullptr);
+    CK(cudaMemsetAsync(g, 0, sizeof(double) * ldh, s));
+    k_normalize<<<vg, NT, 0, s>>>(n, kr.part, NBLK, kr.r, kr.V, g);
+    int j = 0;
+    for (; j < m; ++j) {
+      double* vj = kr.V + (int64_t)j * n;
+      double* zj = kr.ZB + (int64_t)j * n;
+      double* col = H + (int64_t)j * ldh;
+      apply_preconditioner(h, vj, zj, s, nullptr);
+      spmv_any(h, zj, tmp, nullptr, nullptr, false, s);
+      // classical Gram-Schmidt, twice
+      k_multidot<<<vg, NT, 0, s>>>(n, kr.V, j + 1, tmp, kr.mpart);
+      k_multidot_fin<<<1, NT, 0, s>>>(kr.mpart, NBLK, j + 1, col);
+      k_sub_vc<<<vgrid(n), NT, 0, s>>>(n, kr.V, j + 1, col, tmp);
+      k_multidot<<<vg, NT, 0, s>>>(n, kr.V, j + 1, tmp, kr.mpart);
+      k_multidot_fin<<<1, NT, 0, s>>>(kr.mpart, NBLK, j + 1, y);
+      k_sub_vc<<<vgrid(n), NT, 0, s>>>(n, kr.V, j + 1, y, tmp);
+      k_axpby<<<1, NT, 0, s>>>(j + 1, col, col, y, 1.0);
+      k_dot<<<vg, NT, 0, s>>>(n, tmp, tmp, kr.part, nullptr);
+      k_normalize<<<vg, NT, 0, s>>>(n, kr.part, NBLK, tmp, kr.V + (int64_t)(j + 1) * n, col + j + 1);
+      k_givens<<<1, 1, 0, s>>>(H, ldh, j, cs, sn, g, kr.scal, kr.flag, nullptr, 0);
+      ++total;
+      if ((total % check) == 0 || j == m - 1) {
+        CK(cudaMemcpyAsync(hflag, kr.flag, sizeof(int32_t) * 2, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (hflag[0]) { ++j; done = true; break; }
+      }
+    }
+    if (!done && j == m) j = m;
+    k_backsolve<<<1, 1, 0, s>>>(H, ldh, j, kr.flag, g, y);
+    k_add_zy<<<vgrid(n), NT, 0, s>>>(n, kr.ZB, j, y, x);
+    CK_LAUNCH("fgmres cycle");
+    if (!done) {
+      CK(cudaMemcpyAsync(hflag, kr.flag, sizeof(int32_t) * 2, cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      if (hflag[0]) done = true;
+    }
+  }
+  CK(cudaEventRecord(e1, s));
+  // true residual
+  spmv_any(h, x, kr.q, nullptr, nullptr, false, s);
+  k_axpby<<<vgrid(n), NT, 0, s>>>(n, kr.w, b, kr.q, -1.0);
+  k_dot<<<vg, NT, 0, s>>>(n, kr.w, kr.w, kr.part, nullptr);
+  double sc[S_NSCAL];
+  int32_t fl[F_NFLAG];
+  std::vector<double> part(NBLK);
+  CK(cudaMemcpyAsync(sc, kr.scal, sizeof(sc), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(fl, kr.flag, sizeof(fl), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(part.data(), kr.part, sizeof(double) * NBLK, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  float ms = 0;
+  CK(cudaEventElapsedTime(&ms, e0, e1));
+  CK(cudaEventDestroy(e0));
+  CK(cudaEventDestroy(e1));
+  double tr = 0;
+  for (double v : part) tr += v;
+  info.iterations = fl[F_IT];
+  info.converged = fl[F_DONE] == 1;
+  info.final_relres = sc[S_RELRES];
+  info.true_relres = sc[S_BNORM] > 0 ? std::sqrt(tr) / sc[S_BNORM] : 0.0;
+  info.solve_ms = ms;
 }
 
 }  // namespace asmgpu

@@ -251,3 +251,35 @@ def test_coarse_correction_matches_its_definition(P, prec):
     ref = Z @ np.linalg.solve(0.5 * (E + E.T), Z.T @ r)
     np.testing.assert_allclose(zc, ref, rtol=0, atol=1e-9 * np.abs(ref).max())
     pre1.close(); pre2.close()
+
+
+# ---------------------------------------------------------------------------
+# general (nonsymmetric) path: SVD variant, LU-type sweep, FGMRES
+# ---------------------------------------------------------------------------
+def test_general_path_singular_values_and_fgmres(P):
+    prob = convdiff2d(48, (4, 4), peclet=1e3, delta=2, nev=4)
+    A = prob.csr()
+    st = O.setup(A, prob.part, prob.N, 2, 4, spd=False)
+    ref = O.solve(st, prob.b)
+    pre = make(P, A, prob.part, prob.N, 2, 4, spd=False, precision="fp64", eig_tol=1e-11, max_sweeps=200)
+    vals, cnt = P.asm_get_local_values(pre.h)
+    for i, loc in enumerate(st.locals):
+        k = len(loc.values)
+        assert cnt[i] == k
+        np.testing.assert_allclose(vals[i, :k], loc.values, rtol=1e-10)
+    x, info = pre.solve(torch.as_tensor(prob.b, device="cuda"))
+    xr = x.cpu().numpy()
+    rel = np.linalg.norm(prob.b - A @ xr) / np.linalg.norm(prob.b)
+    assert info.converged and rel <= 1e-7
+    assert abs(info.iterations - ref.iterations) <= max(2, 0.1 * ref.iterations)
+    pre.close()
+
+
+def test_general_path_fp32_local(P):
+    prob = convdiff2d(64, (4, 4), peclet=1e3, delta=2, nev=6)
+    A = prob.csr()
+    pre = make(P, A, prob.part, prob.N, 2, 6, spd=False, precision="fp32")
+    x, info = pre.solve(torch.as_tensor(prob.b, device="cuda"))
+    rel = np.linalg.norm(prob.b - A @ x.cpu().numpy()) / np.linalg.norm(prob.b)
+    assert info.converged and rel <= 1e-7
+    pre.close()
