@@ -186,6 +186,29 @@ asm_status asm_get_coarse_matrix(const asm_handle* h, double* E);
 void asm_destroy(asm_handle* h);
 const char* asm_last_error(void);
 
+/* Allocation-free y = A x together with the dot product x^T y (the paper has
+ * no counterpart; this is a service for callers that must not allocate).
+ * Some callers cannot call cudaMalloc while they run: code recording a CUDA
+ * stream capture, where allocation calls are not allowed; latency-critical
+ * host threads, for which cudaMalloc's implicit device synchronisation is
+ * unacceptable; applications whose device memory is owned by their own
+ * allocator.  This entry point allocates nothing and needs no handle.
+ *   n, row_ptr (n+1), col_idx, val: A in CSR, device pointers (as asm_csr).
+ *   x (n, device): input.  y (n, device): output A x.  xty (device, one
+ *   double): output x^T y, summed in a fixed order (deterministic).
+ * Scratch: one partial sum per 64 rows in a static device array built into
+ * the library (16384 doubles), so n is limited to 1,048,576 rows; larger n is
+ * rejected with ASM_ERR_UNSUPPORTED before any device work.  Every GPU that
+ * loads the library holds the array until the process exits.  All calls
+ * share the array and every call rewrites the slots it reads, so nothing
+ * carries over between calls; calls that overlap on the GPU (concurrent
+ * streams) race on it and must be serialised by the caller.  The first call
+ * on each device looks the array's device address up (cudaGetSymbolAddress,
+ * with that device current); make that first call before any stream capture.
+ * Errors: INVALID_ARG (null pointer, n < 0), UNSUPPORTED (n too large), CUDA. */
+asm_status asm_spmv_dot_noalloc(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const double* val,
+                                const double* x, double* y, double* xty, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

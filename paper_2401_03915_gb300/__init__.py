@@ -90,6 +90,8 @@ def load(path: str | None = None) -> C.CDLL:
     L.asm_kernel_launches.argtypes = []
     L.asm_time_apply.argtypes = [vp, vp, vp, i32, vp, C.POINTER(C.c_double)]
     L.asm_time_apply.restype = C.c_int
+    L.asm_spmv_dot_noalloc.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp]
+    L.asm_spmv_dot_noalloc.restype = C.c_int
     L.asm_destroy.argtypes = [vp]
     L.asm_destroy.restype = None
     L.asm_last_error.restype = C.c_char_p
@@ -227,6 +229,13 @@ def asm_time_apply(h: int, r, z, iters: int = 10, stream=None) -> dict:
     ms = (C.c_double * 4)()
     _check(load().asm_time_apply(h, _ptr(r), _ptr(z), iters, _stream(stream), ms))
     return {"local_tiles": ms[0], "coarse": ms[1], "pull": ms[2], "apply": ms[3]}
+
+
+def asm_spmv_dot_noalloc(row_ptr, col_idx, val, x, y, xty, stream=None) -> None:
+    """y = A x and xty[0] = x^T y without any device allocation (device tensors)."""
+    n = int(x.numel()) if hasattr(x, "numel") else len(x)
+    _check(load().asm_spmv_dot_noalloc(n, _ptr(row_ptr), _ptr(col_idx), _ptr(val), _ptr(x), _ptr(y), _ptr(xty),
+                                       _stream(stream)))
 
 
 def asm_destroy(h: int) -> None:

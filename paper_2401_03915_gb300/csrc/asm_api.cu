@@ -75,6 +75,8 @@ float elapsed(cudaEvent_t a, cudaEvent_t b) {
 }  // namespace
 
 namespace asmgpu {
+asm_status set_last_error(asm_status s, const std::string& msg) { return set_error(s, msg); }
+
 void check_device_error(Handle& h, cudaStream_t s, const char* stage) {
   int32_t e = 0;
   CK(cudaMemcpyAsync(&e, h.dn.err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));

@@ -22,6 +22,8 @@ struct AsmError {
 };
 
 [[noreturn]] void fail(asm_status s, const std::string& msg);
+// Record `msg` as the calling thread's asm_last_error() text; returns s.
+asm_status set_last_error(asm_status s, const std::string& msg);
 void cuda_check(cudaError_t e, const char* what, const char* file, int line);
 
 #define CK(call) ::asmgpu::cuda_check((call), #call, __FILE__, __LINE__)
