@@ -292,4 +292,6 @@ def config(name: str, seed: int = 0) -> Problem:
         return elasticity3d(32, (4, 8, 8), 0.3, delta=1, nev=24, seed=seed)
     if name == "c4":
         return convdiff2d(512, (32, 32), 1e3, delta=2, nev=16, seed=seed)
+    if name == "c2-40":  # the 64^3 recipe on a 40^3 grid (125 boxes of 8^3), for profiler captures
+        return diffusion3d(40, (5, 5, 5), 1e6, 0.10, delta=1, nev=16, seed=seed)
     raise KeyError(name)

@@ -156,8 +156,12 @@ asm_status asm_get_info(const asm_handle* h, asm_setup_info* info);
  * loaded (graph replays included), read from per-unit device counters;
  * synchronises the device.
  * asm_time_apply: runs the apply `iters` times on `stream` with CUDA events
- * around its parts and writes the mean milliseconds to ms[4]: local tiles,
- * coarse restriction + coarse solve, pull-sum, whole apply.  r, z: device. */
+ * around its parts and writes mean milliseconds to ms[6]: [0] one tile pass
+ * of the local part (k_apply_tiles, mean over its launches), [1] the whole
+ * local part (tile passes and reductions), [2] coarse restriction + coarse
+ * solve, [3] pull-sum, [4] the parts run one after the other, [5] the apply
+ * as asm_apply runs it (coarse part overlapped on a side stream).
+ * r, z: device. */
 uint64_t asm_kernel_launches(void);
 asm_status asm_time_apply(asm_handle* h, const double* r, double* z, int32_t iters, void* stream, double* ms);
 const char* asm_stage_name(int32_t stage);

@@ -226,9 +226,10 @@ def asm_kernel_launches() -> int:
 
 
 def asm_time_apply(h: int, r, z, iters: int = 10, stream=None) -> dict:
-    ms = (C.c_double * 4)()
+    ms = (C.c_double * 6)()
     _check(load().asm_time_apply(h, _ptr(r), _ptr(z), iters, _stream(stream), ms))
-    return {"local_tiles": ms[0], "coarse": ms[1], "pull": ms[2], "apply": ms[3]}
+    return {"tile_pass": ms[0], "local": ms[1], "coarse": ms[2], "pull": ms[3], "sequential": ms[4],
+            "apply": ms[5]}
 
 
 def asm_spmv_dot_noalloc(row_ptr, col_idx, val, x, y, xty, stream=None) -> None:

@@ -272,25 +272,51 @@ void apply_impl(Handle& h, const double* r, double* z, cudaStream_t s, const int
 
 template <typename T>
 void time_impl(Handle& h, const double* r, double* z, int iters, cudaStream_t s, double* ms) {
-  cudaEvent_t e[4];
+  Dense& dn = h.dn;
+  cudaEvent_t e[8];
   for (auto& x : e) CK(cudaEventCreate(&x));
-  double acc[4] = {0, 0, 0, 0};
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  const unsigned gt = (unsigned)std::min<int64_t>(std::max<int64_t>(dn.n_tiles, 1), 152 * 8);
+  const int passes = h.opt.spd ? 2 : 1;
   for (int it = 0; it < iters; ++it) {
     CK(cudaEventRecord(e[0], s));
-    apply_local<T>(h, r, s, nullptr);
+    k_apply_tiles<T, true><<<gt, NT, 0, s>>>((const T*)dn.tiles, dn.tile_desc, dn.n_tiles, h.ov.omega,
+                                             h.ov.sub_off, h.dev_n, dn.nt, dn.part_off, r, h.dscale, nullptr,
+                                             (T*)dn.partials, nullptr);
     CK(cudaEventRecord(e[1], s));
+    float t2 = 0;
+    if (h.opt.spd) {
+      reduce_partials<T>(h, dn.tpos, 1, s, nullptr);
+      CK(cudaEventRecord(e[2], s));
+      k_apply_tiles<T, false><<<gt, NT, 0, s>>>((const T*)dn.tiles, dn.tile_desc, dn.n_tiles, h.ov.omega,
+                                                h.ov.sub_off, h.dev_n, dn.nt, dn.part_off, nullptr, nullptr,
+                                                dn.tpos, (T*)dn.partials, nullptr);
+      CK(cudaEventRecord(e[3], s));
+      reduce_partials<T>(h, dn.ypos, 2, s, nullptr);
+    } else {
+      CK(cudaEventRecord(e[2], s));
+      CK(cudaEventRecord(e[3], s));
+      reduce_partials<T>(h, dn.ypos, 0, s, nullptr);
+    }
+    CK(cudaEventRecord(e[4], s));
     const double* yc = apply_coarse(h, r, s, nullptr);
-    CK(cudaEventRecord(e[2], s));
+    CK(cudaEventRecord(e[5], s));
     apply_pull<T>(h, yc, z, s, nullptr);
-    CK(cudaEventRecord(e[3], s));
-    CK(cudaEventSynchronize(e[3]));
-    float a, b, c;
+    CK(cudaEventRecord(e[6], s));
+    apply_impl<T>(h, r, z, s, nullptr);  // as the solver runs it (coarse part on the side stream)
+    CK(cudaEventRecord(e[7], s));
+    CK(cudaEventSynchronize(e[7]));
+    float a, b, c, d, f, g;
     CK(cudaEventElapsedTime(&a, e[0], e[1]));
-    CK(cudaEventElapsedTime(&b, e[1], e[2]));
-    CK(cudaEventElapsedTime(&c, e[2], e[3]));
-    acc[0] += a; acc[1] += b; acc[2] += c; acc[3] += a + b + c;
+    CK(cudaEventElapsedTime(&t2, e[2], e[3]));
+    CK(cudaEventElapsedTime(&b, e[0], e[4]));
+    CK(cudaEventElapsedTime(&c, e[4], e[5]));
+    CK(cudaEventElapsedTime(&d, e[5], e[6]));
+    CK(cudaEventElapsedTime(&f, e[0], e[6]));
+    CK(cudaEventElapsedTime(&g, e[6], e[7]));
+    acc[0] += (a + t2) / passes; acc[1] += b; acc[2] += c; acc[3] += d; acc[4] += f; acc[5] += g;
   }
-  for (int k = 0; k < 4; ++k) ms[k] = acc[k] / std::max(iters, 1);
+  for (int k = 0; k < 6; ++k) ms[k] = acc[k] / std::max(iters, 1);
   for (auto& x : e) CK(cudaEventDestroy(x));
 }
 
