@@ -215,7 +215,9 @@ void reduce_partials(Handle& h, double* out, int tri, cudaStream_t s, const int3
 template <typename T>
 void apply_local(Handle& h, const double* r, cudaStream_t s, const int32_t* done) {
   Dense& dn = h.dn;
-  unsigned gt = (unsigned)std::min<int64_t>(std::max<int64_t>(dn.n_tiles, 1), 152 * 8);
+  // six resident blocks per SM saturate HBM and leave room for the coarse
+  // kernels running beside this one on the side stream
+  unsigned gt = (unsigned)std::min<int64_t>(std::max<int64_t>(dn.n_tiles, 1), 152 * 6);
   k_apply_tiles<T, true><<<gt, NT, 0, s>>>((const T*)dn.tiles, dn.tile_desc, dn.n_tiles, h.ov.omega, h.ov.sub_off,
                                            h.dev_n, dn.nt, dn.part_off, r, h.dscale, nullptr, (T*)dn.partials,
                                            done);
@@ -276,7 +278,7 @@ void time_impl(Handle& h, const double* r, double* z, int iters, cudaStream_t s,
   cudaEvent_t e[8];
   for (auto& x : e) CK(cudaEventCreate(&x));
   double acc[6] = {0, 0, 0, 0, 0, 0};
-  const unsigned gt = (unsigned)std::min<int64_t>(std::max<int64_t>(dn.n_tiles, 1), 152 * 8);
+  const unsigned gt = (unsigned)std::min<int64_t>(std::max<int64_t>(dn.n_tiles, 1), 152 * 6);
   const int passes = h.opt.spd ? 2 : 1;
   for (int it = 0; it < iters; ++it) {
     CK(cudaEventRecord(e[0], s));

@@ -448,7 +448,7 @@ __global__ void __launch_bounds__(NT) k_subspace(
         // residual relative to the Ritz value, with a floor at the resolution
         // of the working precision relative to the largest Ritz value
         const T eps = sizeof(T) == 8 ? T(1.1e-16) : T(6e-8);
-        const T scale = max(mu[j], T(4) * eps * mu0 / (T)tol);
+        const T scale = max(mu[j], T(64) * eps * mu0 / (T)tol);
         T den = scale * sqrt(nrm);
         rn[j] = (mu[j] <= T(1e-12) * mu0) ? T(0) : sqrt(part) / (den > T(0) ? den : T(1));
       }
