@@ -57,13 +57,16 @@ __device__ void cta_gemm(int M, int N, int K, const T* __restrict__ A, int lda, 
                          T* __restrict__ C, int ldc, T* sm, Scale rs = Scale(), Scale ks = Scale(), bool kinv = false) {
   T* As = sm;                  // GM x (GK + 1)
   T* Bs = sm + GM * (GK + 1);  // GK x GN
-  const int t = threadIdx.x, row = t % GM, cg = t / GM;  // 2 column groups of 16
+  // thread owns rows tr + 32 a (a = 0..3) and columns 4 tc .. 4 tc + 3 of a GM x GN tile
+  const int t = threadIdx.x, tr = t & 31, tc = t >> 5;
   for (int n0 = 0; n0 < N; n0 += GN) {
     const int nw = min(GN, N - n0);
     for (int m0 = 0; m0 < M; m0 += GM) {
-      T acc[16];
+      T acc[4][4];
 #pragma unroll
-      for (int q = 0; q < 16; ++q) acc[q] = 0;
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[a][q] = 0;
       for (int k0 = 0; k0 < K; k0 += GK) {
         __syncthreads();
         if (!ACOL) {
@@ -88,20 +91,28 @@ __device__ void cta_gemm(int M, int N, int K, const T* __restrict__ A, int lda, 
         __syncthreads();
 #pragma unroll 4
         for (int kk = 0; kk < GK; ++kk) {
-          const T a = As[row * (GK + 1) + kk];
-          const T* b = Bs + kk * GN + cg * 16;
+          T av[4], bv[4];
 #pragma unroll
-          for (int q = 0; q < 16; ++q) acc[q] += a * b[q];
+          for (int a = 0; a < 4; ++a) av[a] = As[(tr + 32 * a) * (GK + 1) + kk];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) bv[q] = Bs[kk * GN + 4 * tc + q];
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[a][q] += av[a] * bv[q];
         }
       }
-      if (m0 + row < M) {
-        const T f = rs.on() ? (T)rs(m0 + row) : T(1);
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          int c = cg * 16 + q;
+      for (int a = 0; a < 4; ++a) {
+        const int row = m0 + tr + 32 * a;
+        if (row >= M) continue;
+        const T f = rs.on() ? (T)rs(row) : T(1);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          int c = 4 * tc + q;
           if (c < nw) {
-            T* cp = C + (int64_t)(m0 + row) * ldc + n0 + c;
-            if (SUB) *cp -= acc[q] * f; else *cp = acc[q] * f;
+            T* cp = C + (int64_t)row * ldc + n0 + c;
+            if (SUB) *cp -= acc[a][q] * f; else *cp = acc[a][q] * f;
           }
         }
       }
@@ -448,7 +459,7 @@ __global__ void __launch_bounds__(NT) k_subspace(
         // residual relative to the Ritz value, with a floor at the resolution
         // of the working precision relative to the largest Ritz value
         const T eps = sizeof(T) == 8 ? T(1.1e-16) : T(6e-8);
-        const T scale = max(mu[j], T(64) * eps * mu0 / (T)tol);
+        const T scale = max(mu[j], T(4) * eps * mu0 / (T)tol);
         T den = scale * sqrt(nrm);
         rn[j] = (mu[j] <= T(1e-12) * mu0) ? T(0) : sqrt(part) / (den > T(0) ? den : T(1));
       }
@@ -471,7 +482,7 @@ __global__ void __launch_bounds__(NT) k_subspace(
     if (!(bnd > floor_b)) bnd = floor_b;
     const T e = bnd / 2, c = bnd / 2;
     const double rL = (2.0 * (double)a0 - (double)bnd) / (double)bnd;   // L(a0) >= 1
-    const double gmax = sizeof(T) == 8 ? 1e8 : 1e3;
+    const double gmax = sizeof(T) == 8 ? 1e8 : 1e4;
     int d = sweep > 2 ? max(degree, 1) : 1;   // the first Ritz values are poor bounds
     if (rL > 1.0 + 1e-12) d = min(d, max(1, (int)floor(acosh(gmax) / acosh(rL))));
     else d = 1;
