@@ -163,11 +163,21 @@ def local_spsd_splitting(Aii: np.ndarray, ov: Overlap) -> np.ndarray:
     return At
 
 
+def _scaled_pencil_eigh(lhs: np.ndarray, Aii: np.ndarray):
+    """Eigenpairs of lhs u = lambda A_ii u through the congruent pencil
+    (S lhs S, S A_ii S) with S = diag(A_ii)^{-1/2}: identical eigenvalues,
+    u = S u^; LAPACK's error is then eps * cond(S A_ii S) instead of
+    eps * cond(A_ii), which matters for high-contrast coefficients."""
+    s = 1.0 / np.sqrt(np.abs(np.diag(Aii)))
+    lam, Uh = sla.eigh(s[:, None] * lhs * s[None, :], s[:, None] * Aii * s[None, :])
+    return lam, s[:, None] * Uh
+
+
 def lifting_gevp(Aii: np.ndarray, ov: Overlap):
     """Eigenpairs of D_i A_ii D_i u = lambda A_ii u (eq. uppergevp), eigenvalues
     descending, eigenvectors A_ii-orthonormal."""
     d = pou(ov)
-    lam, U = sla.eigh(d[:, None] * Aii * d[None, :], Aii)
+    lam, U = _scaled_pencil_eigh(d[:, None] * Aii * d[None, :], Aii)
     return lam[::-1], U[:, ::-1]
 
 
@@ -179,7 +189,7 @@ def gevp_svd(Aii: np.ndarray, ov: Overlap):
     DPi = d[:, None] * Pi
     lhs = DPi.T @ Aii @ DPi
     lhs = 0.5 * (lhs + lhs.T)
-    mu, W = sla.eigh(lhs, Aii)
+    mu, W = _scaled_pencil_eigh(lhs, Aii)
     return mu[::-1], W[:, ::-1], Pi
 
 
