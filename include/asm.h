@@ -35,6 +35,7 @@ extern "C" {
 #endif
 
 typedef struct asm_handle asm_handle;
+typedef struct asm_mlp asm_mlp;   /* warm-start network, see asm_mlp_create */
 
 typedef enum {
   ASM_OK = 0,
@@ -78,11 +79,16 @@ typedef struct {
   int32_t nev_lift;         /* at most this many eq. uppergevp vectors          */
   int32_t coarse;           /* 1: two-level; 0: one-level (eq. onelevelasm)     */
   uint64_t seed;            /* counter-based random start of the iteration     */
-  int32_t warm_start;       /* 1: predict the start block with the network set
-                               by asm_set_warm_start                           */
+  int32_t warm_start;       /* 1 (SPD only): the first columns of the start
+                               block are predicted by warm_net from per-node
+                               features; the rest stay random                 */
   int32_t filter_degree;    /* Chebyshev filter degree between Rayleigh-Ritz
                                steps of the subspace iteration (0: 4)          */
-  int32_t reserved[6];
+  int32_t record_warm;      /* 1 (SPD only): keep the network inputs and the
+                               converged start blocks for asm_get_warm_data   */
+  int32_t reserved[3];
+  asm_mlp* warm_net;        /* network for warm_start (borrowed: must stay
+                               alive and unused elsewhere during asm_setup)    */
 } asm_options;
 
 typedef struct {
@@ -115,8 +121,9 @@ typedef struct {
   double stage_ms[12];      /* device time per setup stage (see asm_stage_name) */
 } asm_setup_info;
 
-/* Fill *o with defaults: spd 1, FP64, oversample 8, max_sweeps 60, eig_tol
- * 1e-8, nu off, coarse on, seed 0, no warm start. */
+/* Fill *o with defaults: spd 1, FP64, oversample 8, max_sweeps 0 (= 40 in
+ * FP64, 12 in FP32), eig_tol 0 (= 1e-8 in FP64, 1e-3 in FP32), nu off, coarse
+ * on, seed 0, filter degree 0 (= 4), no warm start, nothing recorded. */
 void asm_default_options(asm_options* o);
 void asm_default_solve_opts(asm_solve_opts* o);
 
@@ -178,6 +185,11 @@ asm_status asm_get_overlap(const asm_handle* h, int32_t* sub_offsets, int32_t* l
  * values of D_i Pi_i (general); counts[i] = number kept.  Either may be NULL. */
 asm_status asm_get_local_values(const asm_handle* h, double* values, int32_t* counts);
 
+/* Subspace-iteration diagnostics, host outputs: resid (N*nev) the relative
+ * eigen-residual of each kept pair at exit (row i = subdomain i, 0 beyond the
+ * kept count), sweeps (N) the sweeps each subdomain ran.  Either may be NULL. */
+asm_status asm_get_eigen_stats(const asm_handle* h, double* resid, int32_t* sweeps);
+
 /* Coarse basis blocks, host output: for subdomain i a |I_i| x counts[i]
  * row-major FP64 block (rows in I_i order), concatenated over i; col_offsets
  * (N+1) gives the first coarse column of each subdomain.  Either may be NULL. */
@@ -189,6 +201,69 @@ asm_status asm_get_coarse_matrix(const asm_handle* h, double* E);
 
 void asm_destroy(asm_handle* h);
 const char* asm_last_error(void);
+
+/* ------------------------------------------------------------------------
+ * Learned warm start of the subspace iteration (the paper has no learned
+ * part; its randomized start, Section 5.1, stays the default and the
+ * fallback).  A per-node network maps ASM_WARM_FEATURES features of each
+ * node of Gamma_delta (the outermost overlap layer, whose nodes index the
+ * rows of the iteration's block) to `outputs` values: row v of the start
+ * block.  Architecture: 16 -> hidden -> hidden -> outputs, ReLU after the
+ * two hidden layers, FP16 operands with FP32 accumulation on the tensor
+ * cores, FP32 master weights, Adam.  Training loss per subdomain i with
+ * network output Y_i (g_i x k) and converged orthonormal vectors Z_i:
+ *   L_i = k - tr((Y_i^T Y_i)^{-1} Y_i^T Z_i Z_i^T Y_i),
+ * the sum of squared sines of the principal angles between span(Y_i) and
+ * span(Z_i); a batch's loss is the mean of L_i over its subdomains.
+ *
+ * Features of node v (A^ = D^{-1/2} A D^{-1/2}, la(v) = log10|a_vv|,
+ * K = the iteration's operator, 1 = ones/sqrt(g), t_r = r/(g-1) - 1/2 with
+ * r the node's row in Gamma_delta, R_i order):
+ *   0 (la(v) - mean over Gamma_delta)/6;  1 max over neighbours u inside
+ *   Omega_{1:delta-1} of (la(u) - la(v))/6;  2-4 sums of |A^_vu| over
+ *   neighbours inside Omega_{1:delta-1}, in Gamma_delta, outside Omega_i;
+ *   5-7 the counts of those neighbours / 6;  8 y = K1/max|K1|;
+ *   9 log10(1e-4 + |y|)/4 + 1;  10, 11 the same for K(K1);
+ *   12 Kt/max|Kt|;  13 t_r;  14 cos(2 pi (t_r + 1/2));  15 sin(2 pi (t_r + 1/2)).
+ * ---------------------------------------------------------------------- */
+#define ASM_WARM_FEATURES 16
+
+/* New network with He-normal weights drawn from `seed`, zero biases.
+ * hidden: multiple of 16 in 16..1024; outputs: 1..32. */
+asm_status asm_mlp_create(int32_t hidden, int32_t outputs, uint64_t seed, asm_mlp** out);
+void asm_mlp_destroy(asm_mlp* net);
+
+/* Parameter count and FP32 parameter vector (host), in this order:
+ * W1 (16 x hidden, row-major), b1 (hidden), W2 (hidden x hidden), b2 (hidden),
+ * W3 (hidden x kp, kp = outputs rounded up to 16; columns >= outputs are 0),
+ * b3 (kp).  A layer computes h_out = h_in W + b. */
+int64_t asm_mlp_num_params(const asm_mlp* net);
+asm_status asm_mlp_get_params(const asm_mlp* net, float* params);
+asm_status asm_mlp_set_params(asm_mlp* net, const float* params);
+
+/* Y (rows x outputs, device FP32) = network(X (rows x 16, device FP32)). */
+asm_status asm_mlp_forward(asm_mlp* net, const float* X, int32_t rows, float* Y, void* stream);
+
+/* Mean subspace loss and its gradient for one batch, without an update.
+ * X: rows x 16 features, T: rows x outputs targets (orthonormal columns per
+ * subdomain), both device FP32; seg: nseg+1 device int64 row offsets with
+ * seg[0] = 0 and seg[nseg] = rows.  loss (host, may be NULL); grad (host,
+ * asm_mlp_num_params floats, may be NULL) = d(mean loss)/d(params). */
+asm_status asm_mlp_loss_grad(asm_mlp* net, const float* X, int32_t rows, const float* T, const int64_t* seg,
+                             int32_t nseg, double* loss, float* grad, void* stream);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, step size lr) on the
+ * batch's mean loss; arguments as asm_mlp_loss_grad.  loss (host) may be
+ * NULL, which keeps the call free of host synchronisation. */
+asm_status asm_mlp_train_step(asm_mlp* net, const float* X, int32_t rows, const float* T, const int64_t* seg,
+                              int32_t nseg, float lr, double* loss, void* stream);
+
+/* Training data kept by a setup with record_warm = 1 (SPD): row_offsets
+ * (host, N+1 int64) gives subdomain i's rows; X (device, rows x 16) the
+ * features; T (device, rows x nev) the converged start blocks (zero columns
+ * beyond the kept count).  Any pointer may be NULL.  INVALID_ARG if nothing
+ * was recorded. */
+asm_status asm_get_warm_data(const asm_handle* h, int64_t* row_offsets, float* X, float* T, void* stream);
 
 /* Allocation-free y = A x together with the dot product x^T y (the paper has
  * no counterpart; this is a service for callers that must not allocate).

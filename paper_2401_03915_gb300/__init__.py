@@ -38,7 +38,8 @@ class asm_options(C.Structure):
     _fields_ = [("spd", C.c_int32), ("local_precision", C.c_int32), ("oversample", C.c_int32),
                 ("max_sweeps", C.c_int32), ("eig_tol", C.c_double), ("nu", C.c_double),
                 ("nev_lift", C.c_int32), ("coarse", C.c_int32), ("seed", C.c_uint64),
-                ("warm_start", C.c_int32), ("filter_degree", C.c_int32), ("reserved", C.c_int32 * 6)]
+                ("warm_start", C.c_int32), ("filter_degree", C.c_int32), ("record_warm", C.c_int32),
+                ("reserved", C.c_int32 * 3), ("warm_net", C.c_void_p)]
 
 
 class asm_solve_opts(C.Structure):
@@ -84,6 +85,7 @@ def load(path: str | None = None) -> C.CDLL:
     L.asm_get_info.argtypes = [vp, C.POINTER(asm_setup_info)]
     L.asm_get_overlap.argtypes = [vp, vp, vp, vp]
     L.asm_get_local_values.argtypes = [vp, vp, vp]
+    L.asm_get_eigen_stats.argtypes = [vp, vp, vp]
     L.asm_get_coarse_basis.argtypes = [vp, vp, vp]
     L.asm_get_coarse_matrix.argtypes = [vp, vp]
     L.asm_kernel_launches.restype = C.c_uint64
@@ -92,13 +94,27 @@ def load(path: str | None = None) -> C.CDLL:
     L.asm_time_apply.restype = C.c_int
     L.asm_spmv_dot_noalloc.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp]
     L.asm_spmv_dot_noalloc.restype = C.c_int
+    i64, f32 = C.c_int64, C.c_float
+    L.asm_mlp_create.argtypes = [i32, i32, C.c_uint64, pp]
+    L.asm_mlp_destroy.argtypes = [vp]
+    L.asm_mlp_destroy.restype = None
+    L.asm_mlp_num_params.argtypes = [vp]
+    L.asm_mlp_num_params.restype = i64
+    L.asm_mlp_get_params.argtypes = [vp, vp]
+    L.asm_mlp_set_params.argtypes = [vp, vp]
+    L.asm_mlp_forward.argtypes = [vp, vp, i32, vp, vp]
+    L.asm_mlp_loss_grad.argtypes = [vp, vp, i32, vp, vp, i32, C.POINTER(C.c_double), vp, vp]
+    L.asm_mlp_train_step.argtypes = [vp, vp, i32, vp, vp, i32, f32, C.POINTER(C.c_double), vp]
+    L.asm_get_warm_data.argtypes = [vp, vp, vp, vp, vp]
     L.asm_destroy.argtypes = [vp]
     L.asm_destroy.restype = None
     L.asm_last_error.restype = C.c_char_p
     L.asm_stage_name.restype = C.c_char_p
     L.asm_stage_name.argtypes = [i32]
     for f in ("asm_setup", "asm_apply", "asm_spmv", "asm_solve", "asm_get_info", "asm_get_overlap",
-              "asm_get_local_values", "asm_get_coarse_basis", "asm_get_coarse_matrix"):
+              "asm_get_local_values", "asm_get_eigen_stats", "asm_get_coarse_basis", "asm_get_coarse_matrix", "asm_mlp_create",
+              "asm_mlp_get_params", "asm_mlp_set_params", "asm_mlp_forward", "asm_mlp_loss_grad",
+              "asm_mlp_train_step", "asm_get_warm_data"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -197,6 +213,15 @@ def asm_get_local_values(h: int):
     return vals[:, :inf.nev], cnt
 
 
+def asm_get_eigen_stats(h: int):
+    """(residuals [N, nev], sweeps [N]) of the subspace iteration."""
+    inf = asm_get_info(h)
+    res = np.zeros((inf.N, max(inf.nev, 1)), dtype=np.float64)
+    sw = np.zeros(inf.N, dtype=np.int32)
+    _check(load().asm_get_eigen_stats(h, res.ctypes.data if inf.nev else None, sw.ctypes.data))
+    return res[:, :inf.nev], sw
+
+
 def asm_get_coarse_basis(h: int, p_sizes):
     """List of per-subdomain blocks Z_i (|I_i| x count_i) and the column offsets."""
     inf = asm_get_info(h)
@@ -242,6 +267,137 @@ def asm_spmv_dot_noalloc(row_ptr, col_idx, val, x, y, xty, stream=None) -> None:
 def asm_destroy(h: int) -> None:
     if h:
         load().asm_destroy(h)
+
+
+# ---------------------------------------------------------------------------
+# Learned warm start
+# ---------------------------------------------------------------------------
+WARM_FEATURES = 16
+
+
+def asm_mlp_create(hidden: int = 256, outputs: int = 16, seed: int = 0) -> int:
+    net = C.c_void_p()
+    _check(load().asm_mlp_create(hidden, outputs, seed, C.byref(net)))
+    return net.value
+
+
+def asm_mlp_destroy(net: int) -> None:
+    if net:
+        load().asm_mlp_destroy(net)
+
+
+def asm_mlp_num_params(net: int) -> int:
+    return int(load().asm_mlp_num_params(net))
+
+
+def asm_mlp_get_params(net: int) -> np.ndarray:
+    p = np.zeros(asm_mlp_num_params(net), dtype=np.float32)
+    _check(load().asm_mlp_get_params(net, p.ctypes.data))
+    return p
+
+
+def asm_mlp_set_params(net: int, params) -> None:
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    if p.size != asm_mlp_num_params(net):
+        raise ValueError("parameter vector has the wrong length")
+    _check(load().asm_mlp_set_params(net, p.ctypes.data))
+
+
+def asm_mlp_forward(net: int, X, Y, stream=None) -> None:
+    """Y (rows x outputs) = network(X (rows x 16)); device float32 tensors."""
+    _check(load().asm_mlp_forward(net, _ptr(X), int(X.shape[0]), _ptr(Y), _stream(stream)))
+
+
+def asm_mlp_loss_grad(net: int, X, T, seg, stream=None):
+    """(mean loss, gradient as a float32 NumPy vector); X, T float32 and seg
+    int64 (nseg+1, seg[0] = 0) device tensors."""
+    loss = C.c_double()
+    g = np.zeros(asm_mlp_num_params(net), dtype=np.float32)
+    _check(load().asm_mlp_loss_grad(net, _ptr(X), int(X.shape[0]), _ptr(T), _ptr(seg), int(seg.shape[0]) - 1,
+                                    C.byref(loss), g.ctypes.data, _stream(stream)))
+    return loss.value, g
+
+
+def asm_mlp_train_step(net: int, X, T, seg, lr: float, stream=None, want_loss: bool = True):
+    loss = C.c_double()
+    _check(load().asm_mlp_train_step(net, _ptr(X), int(X.shape[0]), _ptr(T), _ptr(seg), int(seg.shape[0]) - 1,
+                                     lr, C.byref(loss) if want_loss else None, _stream(stream)))
+    return loss.value if want_loss else None
+
+
+def asm_get_warm_data(h: int, stream=None):
+    """(row offsets [N+1] NumPy int64, features [rows x 16], targets [rows x nev])
+    of a handle set up with record_warm=1; the arrays are device tensors."""
+    import torch
+    inf = asm_get_info(h)
+    off = np.zeros(inf.N + 1, dtype=np.int64)
+    _check(load().asm_get_warm_data(h, off.ctypes.data, None, None, _stream(stream)))
+    rows = int(off[-1])
+    X = torch.empty((rows, WARM_FEATURES), dtype=torch.float32, device="cuda")
+    T = torch.empty((rows, inf.nev), dtype=torch.float32, device="cuda")
+    _check(load().asm_get_warm_data(h, None, _ptr(X), _ptr(T), _stream(stream)))
+    return off, X, T
+
+
+class WarmStartNet:
+    """Owns one warm-start network (C ABI ``asm_mlp_*``)."""
+
+    def __init__(self, hidden: int = 256, outputs: int = 16, seed: int = 0):
+        self.hidden, self.outputs = hidden, outputs
+        self.ptr = asm_mlp_create(hidden, outputs, seed)
+
+    def params(self) -> np.ndarray:
+        return asm_mlp_get_params(self.ptr)
+
+    def set_params(self, p) -> None:
+        asm_mlp_set_params(self.ptr, p)
+
+    def forward(self, X):
+        import torch
+        Y = torch.empty((X.shape[0], self.outputs), dtype=torch.float32, device=X.device)
+        asm_mlp_forward(self.ptr, X, Y)
+        return Y
+
+    def loss_grad(self, X, T, seg):
+        return asm_mlp_loss_grad(self.ptr, X, T, seg)
+
+    def train(self, X, T, offsets, steps: int, lr: float = 1e-3, batch: int = 64, seed: int = 0,
+              log_every: int = 0) -> list[float]:
+        """Adam on minibatches of `batch` consecutive subdomains (the batch
+        order reshuffled every epoch).  X, T: device tensors of all rows;
+        offsets: NumPy int64 row offsets of the subdomains.  Returns the loss of
+        every `log_every`-th step (none if 0)."""
+        import torch
+        nseg = len(offsets) - 1
+        starts = list(range(0, nseg, batch))
+        batches = []
+        for s0 in starts:
+            s1 = min(nseg, s0 + batch)
+            r0, r1 = int(offsets[s0]), int(offsets[s1])
+            seg = torch.as_tensor(offsets[s0:s1 + 1] - r0, dtype=torch.int64, device=X.device)
+            batches.append((X[r0:r1].contiguous(), T[r0:r1].contiguous(), seg))
+        rng = np.random.default_rng(seed)
+        order, losses = [], []
+        for step in range(steps):
+            if not order:
+                order = list(rng.permutation(len(batches)))
+            Xb, Tb, sb = batches[order.pop()]
+            want = log_every > 0 and step % log_every == 0
+            l = asm_mlp_train_step(self.ptr, Xb, Tb, sb, lr, want_loss=want)
+            if want:
+                losses.append(l)
+        return losses
+
+    def close(self):
+        if getattr(self, "ptr", None):
+            asm_mlp_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def stage_names() -> list[str]:

@@ -143,6 +143,8 @@ asm_status asm_setup(const asm_csr* A, const int32_t* part, int32_t N, int32_t o
   if (o.local_precision != ASM_PREC_FP64 && o.local_precision != ASM_PREC_FP32)
     return set_error(ASM_ERR_INVALID_ARG, "local_precision must be ASM_PREC_FP64 or ASM_PREC_FP32");
   if (o.oversample < 0 || o.oversample > 64) return set_error(ASM_ERR_INVALID_ARG, "oversample must be in 0..64");
+  if (o.warm_start && (!o.warm_net || !o.spd))
+    return set_error(ASM_ERR_INVALID_ARG, "warm_start needs warm_net and the SPD method");
   asm_handle* H = new (std::nothrow) asm_handle();
   if (!H) return set_error(ASM_ERR_OOM, "host allocation failed");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -310,6 +312,19 @@ asm_status asm_get_local_values(const asm_handle* H, double* values, int32_t* co
   });
 }
 
+asm_status asm_get_eigen_stats(const asm_handle* H, double* resid, int32_t* sweeps) {
+  if (!H) return set_error(ASM_ERR_INVALID_ARG, "null argument");
+  const Handle& h = H->h;
+  return guarded([&] {
+    if (resid) {
+      if (h.co.resid) CK(cudaMemcpy(resid, h.co.resid, sizeof(double) * h.N * h.nev, cudaMemcpyDeviceToHost));
+      else std::memset(resid, 0, sizeof(double) * h.N * h.nev);
+    }
+    if (sweeps)
+      for (int i = 0; i < h.N; ++i) sweeps[i] = i < (int)h.co.h_sweeps.size() ? h.co.h_sweeps[i] : 0;
+  });
+}
+
 asm_status asm_get_coarse_basis(const asm_handle* H, double* Z, int32_t* col_offsets) {
   if (!H) return set_error(ASM_ERR_INVALID_ARG, "null argument");
   const Handle& h = H->h;
@@ -341,6 +356,20 @@ asm_status asm_get_coarse_matrix(const asm_handle* H, double* E) {
     const int ld = (int)round_up(nC, 64);
     CK(cudaMemcpy2D(E, sizeof(double) * nC, h.co.E_copy, sizeof(double) * ld, sizeof(double) * nC, nC,
                     cudaMemcpyDeviceToHost));
+  });
+}
+
+asm_status asm_get_warm_data(const asm_handle* H, int64_t* row_offsets, float* X, float* T, void* stream) {
+  if (!H) return set_error(ASM_ERR_INVALID_ARG, "null argument");
+  const Handle& h = H->h;
+  if (!h.wfeat || (T && !h.wtgt))
+    return set_error(ASM_ERR_INVALID_ARG, "nothing recorded: set up with record_warm = 1 (SPD)");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  return guarded([&] {
+    if (row_offsets) std::memcpy(row_offsets, h.h_wseg.data(), sizeof(int64_t) * (h.N + 1));
+    if (X) CK(cudaMemcpyAsync(X, h.wfeat, sizeof(float) * h.warm_rows * WARM_FEATURES, cudaMemcpyDeviceToDevice, s));
+    if (T) CK(cudaMemcpyAsync(T, h.wtgt, sizeof(float) * h.warm_rows * h.nev, cudaMemcpyDeviceToDevice, s));
+    CK(cudaStreamSynchronize(s));
   });
 }
 

@@ -247,27 +247,6 @@ __device__ void jacobi(T* H, T* Q, int s) {
   __syncthreads();
 }
 
-// Sort eigenvalues (diag H) descending and permute Q's columns into QS.
-template <typename T>
-__device__ void sort_desc(const T* H, const T* Q, T* QS, T* mu, int* perm, int s) {
-  if (threadIdx.x == 0) {
-    for (int j = 0; j < s; ++j) { perm[j] = j; mu[j] = H[j * s + j]; }
-    for (int a = 0; a < s; ++a) {
-      int best = a;
-      for (int b = a + 1; b < s; ++b)
-        if (mu[b] > mu[best]) best = b;
-      T tv = mu[a]; mu[a] = mu[best]; mu[best] = tv;
-      int ti = perm[a]; perm[a] = perm[best]; perm[best] = ti;
-    }
-  }
-  __syncthreads();
-  for (int idx = threadIdx.x; idx < s * s; idx += NT) {
-    int l = idx / s, j = idx % s;
-    QS[idx] = Q[l * s + perm[j]];
-  }
-  __syncthreads();
-}
-
 template <typename T>
 __device__ void fill_random(T* Y, int L, int s, int sp, int j0, uint64_t seed, uint64_t salt) {
   for (int64_t idx = threadIdx.x; idx < (int64_t)L * (s - j0); idx += NT) {
@@ -286,7 +265,8 @@ __global__ void __launch_bounds__(NT) k_subspace(
     const int32_t* __restrict__ lcol, const int32_t* __restrict__ omega, const int32_t* __restrict__ rp,
     const int32_t* __restrict__ ci, const double* __restrict__ val, const double* __restrict__ ds, T* scratch,
     const int64_t* __restrict__ scr_off, int nev, int over, int max_sweeps, int degree, double tol, uint64_t seed,
-    const float* __restrict__ warm, const int64_t* __restrict__ warm_off, double* __restrict__ values,
+    const float* __restrict__ warm, int wld, int wk, const int64_t* __restrict__ wseg, float* __restrict__ tgt,
+    double* __restrict__ values,
     double* __restrict__ resid, int32_t* __restrict__ count, int32_t* __restrict__ sweeps_out,
     double* __restrict__ Z, const int64_t* __restrict__ z_off) {
   COUNT_LAUNCH();
@@ -419,10 +399,12 @@ __global__ void __launch_bounds__(NT) k_subspace(
   // ---- start block
   fill_random(Y, dim, s, sp, 0, seed, (uint64_t)i * 0x100000001ull);
   if (warm != nullptr && SPD) {
-    const float* wb = warm + warm_off[i];
-    for (int64_t idx = threadIdx.x; idx < (int64_t)dim * k; idx += NT) {
-      int r = (int)(idx / k), j = (int)(idx % k);
-      Y[(int64_t)r * sp + j] = (T)wb[idx];
+    // predicted start columns (rows = Gamma_delta nodes), random columns after them
+    const float* wb = warm + wseg[i] * wld;
+    const int kw = min(wk, k);
+    for (int64_t idx = threadIdx.x; idx < (int64_t)dim * kw; idx += NT) {
+      int r = (int)(idx / kw), j = (int)(idx % kw);
+      Y[(int64_t)r * sp + j] = (T)wb[(int64_t)r * wld + j];
     }
     __syncthreads();
   }
@@ -430,16 +412,32 @@ __global__ void __launch_bounds__(NT) k_subspace(
 
   int sweep = 0;
   for (;;) {
-    // ---- Rayleigh-Ritz
+    // ---- Rayleigh-Ritz (the small eigenproblem in FP64 in both precisions:
+    //      FP32 Jacobi could not separate Ritz values far below the top one)
     applyK(Y, KY, 0, s);
     cta_gemm<T, true>(s, s, dim, Y, sp, KY, sp, H, s, gsm);
     for (int idx = threadIdx.x; idx < s * s; idx += NT) {
       int a = idx / s, b = idx % s;
-      if (a < b) { T v = T(0.5) * (H[a * s + b] + H[b * s + a]); H[a * s + b] = v; H[b * s + a] = v; }
+      G[idx] = 0.5 * ((double)H[a * s + b] + (double)H[b * s + a]);
     }
     __syncthreads();
-    jacobi(H, Q, s);
-    sort_desc(H, Q, QS, mu, perm, s);
+    jacobi<double>(G, Minv, s);
+    if (threadIdx.x == 0) {
+      for (int j = 0; j < s; ++j) perm[j] = j;
+      for (int a = 0; a < s; ++a) {
+        int best = a;
+        for (int b = a + 1; b < s; ++b)
+          if (G[perm[b] * s + perm[b]] > G[perm[best] * s + perm[best]]) best = b;
+        int ti = perm[a]; perm[a] = perm[best]; perm[best] = ti;
+      }
+      for (int j = 0; j < s; ++j) mu[j] = (T)G[perm[j] * s + perm[j]];
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < s * s; idx += NT) {
+      int l = idx / s, j = idx % s;
+      QS[idx] = (T)Minv[l * s + perm[j]];
+    }
+    __syncthreads();
     cta_gemm<T, false>(dim, s, s, Y, sp, QS, s, Yb, sp, gsm); swap(Y, Yb);
     cta_gemm<T, false>(dim, s, s, KY, sp, QS, s, Yb, sp, gsm); swap(KY, Yb);
     // ---- residuals of the first k Ritz pairs
@@ -540,6 +538,14 @@ __global__ void __launch_bounds__(NT) k_subspace(
     values[(int64_t)i * nev + j] = v;
     resid[(int64_t)i * nev + j] = j < kept ? (double)rn[j] : 0.0;
   }
+  if (tgt != nullptr && SPD) {
+    // converged Ritz vectors z (Gamma_delta rows), the network's training targets
+    float* tb = tgt + wseg[i] * nev;
+    for (int64_t idx = threadIdx.x; idx < (int64_t)dim * nev; idx += NT) {
+      int r = (int)(idx / nev), j = (int)(idx % nev);
+      tb[idx] = j < kept ? (float)Y[(int64_t)r * sp + j] : 0.f;
+    }
+  }
   double* Zi = Z + z_off[i];
   if (SPD) {
     // Z_i = S_I U^T z (undo the diagonal scaling), FP64 output p x nev
@@ -553,6 +559,126 @@ __global__ void __launch_bounds__(NT) k_subspace(
       int r = (int)(idx / nev), j = (int)(idx % nev);
       Zi[idx] = j < kept ? (double)Y[(int64_t)r * sp + j] : 0.0;
     }
+  }
+}
+
+// max over the block of v (all threads get the result)
+__device__ double block_max(double v, double* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double r = sh[0];
+  for (int w = 1; w < NT / 32; ++w) r = fmax(r, sh[w]);
+  __syncthreads();
+  return r;
+}
+
+// Per-node input features of the warm-start network, one block per
+// subdomain, one row per Gamma_delta node (local row r = 0..g-1, in R_i
+// order).  With A^ = D^{-1/2} A D^{-1/2}, la(v) = log10 |a_vv|, and the
+// operator K = U A^_II U^T of the subspace iteration:
+//   0: (la(v) - mean of la over Gamma_delta) / 6
+//   1: max over neighbours u in Omega_{1:delta-1} of (la(u) - la(v)) / 6 (0 if none)
+//   2-4: sum of |A^_vu| over neighbours in Omega_{1:delta-1}, Gamma_delta, outside Omega_i
+//   5-7: the counts of those neighbours / 6
+//   8, 9: y = K 1 / max|K 1| (1 = ones / sqrt(g)): y, log10(1e-4 + |y|) / 4 + 1
+//   10, 11: the same for K (K 1)
+//   12: K t / max|K t| with t_r = r / (g - 1) - 1/2
+//   13-15: t_r, cos(2 pi (t_r + 1/2)), sin(2 pi (t_r + 1/2))
+template <typename T>
+__global__ void __launch_bounds__(NT) k_warm_features(
+    const T* __restrict__ work, const int64_t* __restrict__ work_off, const int32_t* __restrict__ np_arr,
+    const int32_t* __restrict__ n_arr, const int32_t* __restrict__ m_arr, const int32_t* __restrict__ p_arr,
+    const int32_t* __restrict__ sub_off, const int64_t* __restrict__ ent_off, const int32_t* __restrict__ lcol,
+    const int32_t* __restrict__ omega, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+    const double* __restrict__ val, const double* __restrict__ ds, T* scratch, const int64_t* __restrict__ scr_off,
+    const int64_t* __restrict__ wseg, float* __restrict__ feat) {
+  COUNT_LAUNCH();
+  extern __shared__ double shd[];
+  __shared__ double red[NT / 32];
+  const int i = blockIdx.x;
+  const int n = n_arr[i], m = m_arr[i], p = p_arr[i], ld = np_arr[i];
+  const int g = n - m, pos0 = sub_off[i];
+  if (g <= 0) return;
+  const int L = max(p, g);
+  T* gsm = reinterpret_cast<T*>(shd);
+  T* base = scratch + scr_off[i];
+  T* P = base;            // g x 2 probes
+  T* KP = base + 2 * L;   // K P
+  T* V = base + 4 * L;    // p x 2
+  T* AV = base + 6 * L;   // p x 2
+  T* KKP = base + 8 * L;  // K (K P)
+  const T* U = work + work_off[i] + (int64_t)m * ld;
+  const double tden = g > 1 ? (double)(g - 1) : 1.0;
+  for (int r = threadIdx.x; r < g; r += NT) {
+    P[2 * r] = (T)(1.0 / sqrt((double)g));
+    P[2 * r + 1] = (T)(r / tden - 0.5);
+  }
+  __syncthreads();
+  auto applyK2 = [&](const T* in, T* o) {
+    cta_gemm<T, true>(p, 2, g, U, ld, in, 2, V, 2, gsm);
+    mul_AII(p, pos0, omega, rp, ci, val, ds, ent_off, lcol, V, AV, 2, 2);
+    cta_gemm<T, false>(g, 2, p, U, ld, AV, 2, o, 2, gsm);
+  };
+  applyK2(P, KP);
+  applyK2(KP, KKP);
+  double a0 = 0, a1 = 0, a2 = 0, sla = 0;
+  for (int r = threadIdx.x; r < g; r += NT) {
+    a0 = fmax(a0, fabs((double)KP[2 * r]));
+    a1 = fmax(a1, fabs((double)KP[2 * r + 1]));
+    a2 = fmax(a2, fabs((double)KKP[2 * r]));
+    sla += -2.0 * log10(ds[omega[pos0 + m + r]]);
+  }
+  const double mx0 = block_max(a0, red), mx1 = block_max(a1, red), mx2 = block_max(a2, red);
+  const double mean_la = block_sum(sla, red) / g;
+  const double i0 = mx0 > 0 ? 1.0 / mx0 : 0.0, i1 = mx1 > 0 ? 1.0 / mx1 : 0.0, i2 = mx2 > 0 ? 1.0 / mx2 : 0.0;
+  float* out = feat + wseg[i] * WARM_FEATURES;
+  for (int r = threadIdx.x; r < g; r += NT) {
+    const int pos = pos0 + m + r, v = omega[pos];
+    const int b = rp[v], e = rp[v + 1];
+    const double sv = ds[v], la = -2.0 * log10(sv);
+    const int64_t e0 = ent_off[pos];
+    double s_in = 0, s_g = 0, s_out = 0, dmax = 0;
+    int c_in = 0, c_g = 0, c_out = 0;
+    for (int q = 0; q < e - b; ++q) {
+      const int u = ci[b + q];
+      if (u == v) continue;
+      const int lc = lcol[e0 + q];
+      const double w = fabs(val[b + q] * sv * ds[u]);
+      if (lc >= 0 && lc < m) {
+        const double d = -2.0 * log10(ds[u]) - la;
+        dmax = c_in == 0 ? d : fmax(dmax, d);
+        s_in += w;
+        ++c_in;
+      } else if (lc >= m) {
+        s_g += w;
+        ++c_g;
+      } else {
+        s_out += w;
+        ++c_out;
+      }
+    }
+    const double y0 = (double)KP[2 * r] * i0, y1 = (double)KKP[2 * r] * i2, y2 = (double)KP[2 * r + 1] * i1;
+    const double t = r / tden - 0.5;
+    float* f = out + (int64_t)r * WARM_FEATURES;
+    f[0] = (float)((la - mean_la) / 6.0);
+    f[1] = (float)(dmax / 6.0);
+    f[2] = (float)s_in;
+    f[3] = (float)s_g;
+    f[4] = (float)s_out;
+    f[5] = (float)(c_in / 6.0);
+    f[6] = (float)(c_g / 6.0);
+    f[7] = (float)(c_out / 6.0);
+    f[8] = (float)y0;
+    f[9] = (float)(log10(1e-4 + fabs(y0)) / 4.0 + 1.0);
+    f[10] = (float)y1;
+    f[11] = (float)(log10(1e-4 + fabs(y1)) / 4.0 + 1.0);
+    f[12] = (float)y2;
+    f[13] = (float)t;
+    f[14] = (float)cospi(2.0 * (t + 0.5));
+    f[15] = (float)sinpi(2.0 * (t + 0.5));
   }
 }
 
@@ -596,18 +722,47 @@ void run_eigen(Handle& h, cudaStream_t s) {
   size_t smem = gemm_bytes + (size_t)2 * smax * smax * sizeof(double) +
                 (size_t)(4 * smax * smax + 2 * smax) * sizeof(T) + 64;
   const double tol = h.opt.eig_tol > 0 ? h.opt.eig_tol : (h.fp32 ? 1e-3 : 1e-8);
-  const int maxsw = h.opt.max_sweeps > 0 ? h.opt.max_sweeps : 40;
+  // FP32 cannot resolve Ritz values ~1e5 below the top one to 1e-3: a cap
+  // keeps such subdomains from holding the launch
+  const int maxsw = h.opt.max_sweeps > 0 ? h.opt.max_sweeps : (h.fp32 ? 12 : 40);
   const int degree = h.opt.filter_degree > 0 ? h.opt.filter_degree : 4;
-  auto launch = [&](auto kern, const float* warm, const int64_t* woff) {
+  // learned warm start (SPD path): features per Gamma_delta node, the
+  // network's start blocks, and (when recorded) the converged blocks
+  const bool want_warm = spd && (h.opt.warm_start || h.opt.record_warm);
+  const float* warm = nullptr;
+  int wld = 0, wk = 0;
+  if (want_warm) {
+    h.h_wseg.assign(N + 1, 0);
+    for (int i = 0; i < N; ++i) h.h_wseg[i + 1] = h.h_wseg[i] + h.h_g[i];
+    h.warm_rows = h.h_wseg[N];
+    h.wseg = mem.alloc<int64_t>(N + 1);
+    CK(cudaMemcpyAsync(h.wseg, h.h_wseg.data(), 8 * (N + 1), cudaMemcpyHostToDevice, s));
+    h.wfeat = mem.alloc<float>(std::max<int64_t>(h.warm_rows, 1) * WARM_FEATURES);
+    if (h.opt.record_warm) h.wtgt = mem.alloc<float>(std::max<int64_t>(h.warm_rows, 1) * std::max(nev, 1));
+    const size_t fsm = gemm_bytes + 64;
+    CK(cudaFuncSetAttribute(k_warm_features<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm));
+    k_warm_features<T><<<N, NT, fsm, s>>>((const T*)dn.work, dn.work_off, dn.np, h.dev_n, h.dev_m, h.dev_p,
+                                          h.ov.sub_off, h.ov.ent_off, h.ov.lcol, h.ov.omega, h.row_ptr, h.col_idx,
+                                          h.val, h.dscale, (T*)co.scratch, co.scr_off, h.wseg, h.wfeat);
+    CK_LAUNCH("warm-start features");
+    if (h.opt.warm_start && h.warm_rows > 0) {
+      Mlp& net = h.opt.warm_net->net;
+      net.forward(h.wfeat, (int)h.warm_rows, s);
+      warm = net.Y32;
+      wld = net.Kp;
+      wk = net.K;
+    }
+  }
+  auto launch = [&](auto kern) {
     CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<N, NT, smem, s>>>((const T*)dn.XpT, dn.xs_off, (const T*)dn.S, dn.s_off, (const T*)dn.work, dn.work_off,
                              dn.np, h.dev_n, h.dev_m, h.dev_p, h.ov.sub_off, h.ov.ent_off, h.ov.lcol, h.ov.omega,
                              h.row_ptr, h.col_idx, h.val, h.dscale, (T*)co.scratch, co.scr_off, nev, over, maxsw,
-                             degree, tol, h.opt.seed, warm, woff, co.values, co.resid, co.count, co.sweeps, co.Z,
-                             co.z_off);
+                             degree, tol, h.opt.seed, warm, wld, wk, h.wseg, h.wtgt, co.values, co.resid, co.count,
+                             co.sweeps, co.Z, co.z_off);
   };
-  if (spd) launch(k_subspace<T, true>, h.warm, h.warm_off);
-  else launch(k_subspace<T, false>, nullptr, nullptr);
+  if (spd) launch(k_subspace<T, true>);
+  else launch(k_subspace<T, false>);
   CK_LAUNCH("subspace iteration");
 }
 

@@ -3,6 +3,7 @@
 
 #include "common.cuh"
 #include "coarse_nd.cuh"
+#include "mlp.cuh"
 
 namespace asmgpu {
 
@@ -105,8 +106,13 @@ struct Handle {
   double* val = nullptr;
   int32_t *dev_n = nullptr, *dev_m = nullptr, *dev_p = nullptr;  // |Omega_i|, |Omega_{1:d-1}|, |I_i|
   double* dscale = nullptr;         // 1/sqrt(|A_vv|): symmetric diagonal scaling of every A_ii
-  float* warm = nullptr;            // optional predicted start blocks (g_i x nev per subdomain)
-  int64_t* warm_off = nullptr;
+  // learned warm start (SPD path): one row per Gamma_delta node, subdomain i
+  // owning rows h_wseg[i] .. h_wseg[i+1]-1
+  int64_t warm_rows = 0;
+  std::vector<int64_t> h_wseg;
+  int64_t* wseg = nullptr;
+  float* wfeat = nullptr;           // warm_rows x WARM_FEATURES network inputs
+  float* wtgt = nullptr;            // warm_rows x nev converged start blocks (record_warm)
   std::vector<int32_t> h_n, h_p, h_m, h_g;
   Overlap ov;
   Dense dn;
