@@ -5,7 +5,10 @@ One step = asm_setup (overlap, local gather + inverse, subspace iteration,
 Z and E = Z^T A Z, FP64 coarse factorisation) + asm_solve (FP64 PCG to a
 relative residual of 1e-8) + asm_destroy on the 64^3 high-contrast diffusion
 workload (n = 262,144, 512 subdomains of 8^3, overlap 1, nev 16), with the
-local work in FP32 and everything else in FP64.  Inputs are generated on the
+local work in FP32, the subspace iteration warm-started by the per-node
+network (trained before any timing on subdomains of generated instances with
+other seeds), and everything else in FP64.  The same run also times the
+plain FP64 form and the FP32 form with the randomized start ("forms").  Inputs are generated on the
 host, copied to the device once, and are resident in HBM when the timed
 region starts.  The step's working set (0.8 GB of local inverses alone) is
 far larger than L2, so no explicit flush is done between steps.
@@ -48,6 +51,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--apply-iters", type=int, default=20)
+    ap.add_argument("--no-warm", action="store_true", help="randomized start only (no learned warm start)")
+    ap.add_argument("--no-forms", action="store_true", help="skip the FP64 / FP32 comparison forms")
+    ap.add_argument("--warm-instances", type=int, default=12)
+    ap.add_argument("--warm-steps", type=int, default=2000)
     ap.add_argument("--mode", default="step", choices=["step", "apply"],
                     help="apply: one setup, then --apply-iters applies (for profiler captures)")
     return ap.parse_args()
@@ -213,6 +220,38 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
+def train_warm_net(P, torch, n_instances: int, steps: int):
+    """Train the warm-start network on subdomains of generated 3D diffusion
+    instances (cube sides 24..48, contrast 1e2..1e6; generator seeds
+    disjoint from the benchmark workload's) with targets from FP32 setups;
+    returns the network and a summary.  Runs before any timed region."""
+    from asm_inputs import stream_instance
+    t0 = time.perf_counter()
+    Xs, Ts, offs, base = [], [], [0], 0
+    for k in range(n_instances):
+        prob = stream_instance(k, base_seed=1)
+        h = P.asm_setup(prob.indptr, prob.indices, prob.data, prob.part, prob.N, prob.delta, prob.nev,
+                        P.default_options(local_precision=P.PREC_FP32, record_warm=1), None, False)
+        off, X, T = P.asm_get_warm_data(h)
+        P.asm_destroy(h)
+        Xs.append(X)
+        Ts.append(T)
+        offs.extend((off[1:] + base).tolist())
+        base += int(off[-1])
+    X, T, off = torch.cat(Xs), torch.cat(Ts), np.asarray(offs, dtype=np.int64)
+    t1 = time.perf_counter()
+    net = P.WarmStartNet(256, 16, seed=1)
+    seg = torch.as_tensor(off, device=X.device)
+    loss0 = net.loss_grad(X, T, seg)[0]
+    net.train(X, T, off, steps=steps, lr=1e-3, batch=32)
+    loss1 = net.loss_grad(X, T, seg)[0]
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    return net, {"subdomains": len(off) - 1, "rows": int(off[-1]), "instances": n_instances, "adam_steps": steps,
+                 "collect_s": round(t1 - t0, 3), "train_s": round(t2 - t1, 3), "loss_before": round(loss0, 4),
+                 "loss_after": round(loss1, 4)}
+
+
 def run_ours(args):
     import torch
     rank = int(os.environ.get("RANK", "0"))
@@ -238,7 +277,10 @@ def run_ours(args):
     b = torch.as_tensor(prob.b, device=dev)
     x = torch.zeros_like(b)
     prec = P.PREC_FP32 if args.precision == "fp32" else P.PREC_FP64
-    opt = P.default_options(local_precision=prec)
+    net, warm_info = None, None
+    if not args.no_warm and args.mode == "step":
+        net, warm_info = train_warm_net(P, torch, args.warm_instances, args.warm_steps)
+    opt = P.default_options(local_precision=prec, warm_start=1 if net else 0, warm_net=net.ptr if net else None)
     sopt = P.default_solve_opts(rtol=1e-8, max_it=5000)
     stream = torch.cuda.current_stream()
 
@@ -314,6 +356,32 @@ def run_ours(args):
     apply_gbs = apply_bytes / (tap["apply"] * 1e-3) / 1e9
     P.asm_destroy(h_last)
 
+    # ---- the other forms on the same GPU: plain FP64, FP32 with the randomized start
+    forms = None
+    if not args.no_forms:
+        def time_form(o, n_steps=2):
+            hh = P.asm_setup(rp, ci, va, pa, prob.N, prob.delta, prob.nev, o, stream, True)
+            P.asm_solve(hh, b, x, sopt, stream)
+            P.asm_destroy(hh)
+            torch.cuda.synchronize()
+            f0 = torch.cuda.Event(enable_timing=True)
+            f1 = torch.cuda.Event(enable_timing=True)
+            f0.record(stream)
+            its = 0
+            for _ in range(n_steps):
+                hh = P.asm_setup(rp, ci, va, pa, prob.N, prob.delta, prob.nev, o, stream, True)
+                its = P.asm_solve(hh, b, x, sopt, stream).iterations
+                P.asm_destroy(hh)
+            f1.record(stream)
+            torch.cuda.synchronize()
+            return {"s_per_step": f0.elapsed_time(f1) / n_steps / 1e3, "iterations": its}
+        forms = {"fp64_random": time_form(P.default_options(local_precision=P.PREC_FP64)),
+                 "fp32_random": time_form(P.default_options(local_precision=P.PREC_FP32))}
+        if net:
+            forms["fp32_learned"] = {"s_per_step": ms / 1e3, "iterations": infos[-1].iterations}
+        forms["this_line"] = ("fp32" if args.precision == "fp32" else "fp64") + ("_learned" if net else "_random")
+        forms["speedup_vs_fp64"] = forms["fp64_random"]["s_per_step"] / (ms / 1e3)
+
     # ---- end to end through the C ABI with host buffers
     e2e = None
     if not args.no_e2e:
@@ -347,6 +415,7 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "config": args.config, "local_precision": args.precision,
+                       "start": "learned warm start (MLP 16-256-256-16)" if net else "randomized",
                        "outer": "FP64 PCG rtol 1e-8", "l2": "working set > L2 (no flush)",
                        "parallelism": f"replicas x{world}"},
             "iterations": infos[-1].iterations, "true_relres": infos[-1].true_relres,
@@ -357,6 +426,7 @@ def run_ours(args):
                          "peak_kind": peak_kind, "traffic": None,
                          "algorithmic_bytes_per_launch": pass_bytes},
             "clocks": clocks, "gpu_launches": launches, "e2e": e2e, "cpu_baseline": cpu,
+            "forms": forms, "warm_start": warm_info,
         }
         print(json.dumps(line), flush=True)
     if dist:

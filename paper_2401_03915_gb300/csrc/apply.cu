@@ -12,6 +12,10 @@
 // the pull kernel (Z_i is supported on Omega_{I_i}).
 #include <algorithm>
 
+#include <map>
+#include <mutex>
+#include <tuple>
+
 #include "handle.cuh"
 
 namespace asmgpu {
@@ -215,9 +219,9 @@ void reduce_partials(Handle& h, double* out, int tri, cudaStream_t s, const int3
 template <typename T>
 void apply_local(Handle& h, const double* r, cudaStream_t s, const int32_t* done) {
   Dense& dn = h.dn;
-  // six resident blocks per SM saturate HBM and leave room for the coarse
-  // kernels running beside this one on the side stream
-  unsigned gt = (unsigned)std::min<int64_t>(std::max<int64_t>(dn.n_tiles, 1), 152 * 6);
+  // resident blocks per SM chosen by tune_apply: enough to saturate HBM
+  // while leaving room for the coarse kernels on the side stream
+  unsigned gt = (unsigned)std::min<int64_t>(std::max<int64_t>(dn.n_tiles, 1), (int64_t)h.num_sms * h.tile_ctas);
   k_apply_tiles<T, true><<<gt, NT, 0, s>>>((const T*)dn.tiles, dn.tile_desc, dn.n_tiles, h.ov.omega, h.ov.sub_off,
                                            h.dev_n, dn.nt, dn.part_off, r, h.dscale, nullptr, (T*)dn.partials,
                                            done);
@@ -278,7 +282,7 @@ void time_impl(Handle& h, const double* r, double* z, int iters, cudaStream_t s,
   cudaEvent_t e[8];
   for (auto& x : e) CK(cudaEventCreate(&x));
   double acc[6] = {0, 0, 0, 0, 0, 0};
-  const unsigned gt = (unsigned)std::min<int64_t>(std::max<int64_t>(dn.n_tiles, 1), 152 * 6);
+  const unsigned gt = (unsigned)std::min<int64_t>(std::max<int64_t>(dn.n_tiles, 1), (int64_t)h.num_sms * h.tile_ctas);
   const int passes = h.opt.spd ? 2 : 1;
   for (int it = 0; it < iters; ++it) {
     CK(cudaEventRecord(e[0], s));
@@ -322,7 +326,55 @@ void time_impl(Handle& h, const double* r, double* z, int iters, cudaStream_t s,
   for (auto& x : e) CK(cudaEventDestroy(x));
 }
 
+// Autotuner of the apply's launch shape: the whole apply (local tile passes
+// with the coarse part beside them) is timed for each candidate number of
+// resident tile-pass blocks per SM and the fastest is kept.  Results are
+// cached per (device, tiles, subdomains, coarse size, precision), so only the
+// first setup of a given shape pays for the measurement.
+std::mutex g_tune_mutex;
+std::map<std::tuple<int, int64_t, int, int, int>, int> g_tune_cache;
+
+template <typename T>
+void tune_impl(Handle& h, cudaStream_t s) {
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  const auto key = std::make_tuple(dev, h.dn.n_tiles, h.N, h.co.n_C, h.fp32 ? 1 : 0);
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) { h.tile_ctas = it->second; return; }
+  }
+  double* rz = h.mem.alloc<double>(2 * (size_t)h.n);
+  CK(cudaMemsetAsync(rz, 0, sizeof(double) * 2 * h.n, s));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  const int cand[4] = {4, 6, 8, 12};
+  int best = h.tile_ctas;
+  float best_ms = 3.0e38f;
+  for (int c : cand) {
+    h.tile_ctas = c;
+    apply_impl<T>(h, rz, rz + h.n, s, nullptr);  // warm
+    CK(cudaEventRecord(e0, s));
+    for (int rep = 0; rep < 3; ++rep) apply_impl<T>(h, rz, rz + h.n, s, nullptr);
+    CK(cudaEventRecord(e1, s));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best_ms) { best_ms = ms; best = c; }
+  }
+  h.tile_ctas = best;
+  CK(cudaEventDestroy(e0));
+  CK(cudaEventDestroy(e1));
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  g_tune_cache[key] = best;
+}
+
 }  // namespace
+
+void tune_apply(Handle& h, cudaStream_t s) {
+  if (h.fp32) tune_impl<float>(h, s); else tune_impl<double>(h, s);
+}
 
 void apply_preconditioner(Handle& h, const double* r, double* z, cudaStream_t s, const int32_t* done) {
   if (h.fp32) apply_impl<float>(h, r, z, s, done); else apply_impl<double>(h, r, z, s, done);

@@ -154,6 +154,12 @@ asm_status asm_setup(const asm_csr* A, const int32_t* part, int32_t N, int32_t o
     h.n = A->n; h.nnz = A->nnz; h.N = N; h.delta = overlap; h.nev = nev; h.opt = o;
     h.host_io = A->on_device == 0;
     h.fp32 = o.local_precision == ASM_PREC_FP32;
+    {
+      int dev = 0, sms = 0;
+      CK(cudaGetDevice(&dev));
+      CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+      if (sms > 0) h.num_sms = sms;
+    }
     h.mem.stream = s;
     for (auto& e : h.ev) CK(cudaEventCreate(&e));
     h.events = true;
@@ -184,6 +190,7 @@ asm_status asm_setup(const asm_csr* A, const int32_t* part, int32_t N, int32_t o
     CK(cudaEventRecord(h.ev[7], s));
     build_coarse(h, s);
     CK(cudaEventRecord(h.ev[8], s));
+    tune_apply(h, s);
     CK(cudaStreamSynchronize(s));
     // info
     asm_setup_info& inf = h.info;

@@ -121,27 +121,41 @@ __device__ void cta_gemm(int M, int N, int K, const T* __restrict__ A, int lda, 
   __syncthreads();
 }
 
-// AV (p x s) = A^_{I,I} V from the local CSR (columns < p), scaled values.
+// AV (p x s) = A^_{I,I} V from the local CSR rows of I_i: aval holds the
+// scaled values a_vu / sqrt(|a_vv a_uu|) entry by entry (aligned with lcol),
+// lcol the local column (< 0 outside Omega_i; only columns < p are used).
 template <typename T>
-__device__ void mul_AII(int p, int pos0, const int32_t* __restrict__ omega, const int32_t* __restrict__ rp,
-                        const int32_t* __restrict__ ci, const double* __restrict__ val, const double* __restrict__ ds,
-                        const int64_t* __restrict__ ent_off, const int32_t* __restrict__ lcol, const T* __restrict__ V,
-                        T* __restrict__ AV, int s, int sp) {
+__device__ void mul_AII(int p, int pos0, const int64_t* __restrict__ ent_off, const int32_t* __restrict__ lcol,
+                        const T* __restrict__ aval, const T* __restrict__ V, T* __restrict__ AV, int s, int sp) {
   for (int idx = threadIdx.x; idx < p * s; idx += NT) {
     const int a = idx / s, j = idx % s;
-    const int v = omega[pos0 + a];
-    const int b = rp[v], e = rp[v + 1];
-    const double sv = ds[v];
-    const int64_t e0 = ent_off[pos0 + a];
+    const int64_t e0 = ent_off[pos0 + a], e1 = ent_off[pos0 + a + 1];
     T acc = 0;
-    for (int q = 0; q < e - b; ++q) {
-      const int lc = lcol[e0 + q];
+    for (int64_t e = e0; e < e1; ++e) {
+      const int lc = lcol[e];
       if (lc < 0 || lc >= p) continue;
-      acc += (T)(val[b + q] * sv * ds[ci[b + q]]) * V[(int64_t)lc * sp + j];
+      acc += aval[e] * V[(int64_t)lc * sp + j];
     }
     AV[(int64_t)a * sp + j] = acc;
   }
   __syncthreads();
+}
+
+// Scaled values of every local row (all positions of all Omega_i), in the
+// working precision: aval[e] = a_vu ds_v ds_u with ds = |diag A|^{-1/2}.
+template <typename T>
+__global__ void k_scaled_values(int64_t total, const int32_t* __restrict__ omega, const int64_t* __restrict__ ent_off,
+                                const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                const double* __restrict__ val, const double* __restrict__ ds, T* __restrict__ aval) {
+  COUNT_LAUNCH();
+  for (int64_t pos = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; pos < total;
+       pos += (int64_t)gridDim.x * blockDim.x) {
+    const int v = omega[pos];
+    const int b = rp[v], e = rp[v + 1];
+    const double sv = ds[v];
+    const int64_t o = ent_off[pos];
+    for (int q = 0; q < e - b; ++q) aval[o + q] = (T)(val[b + q] * sv * ds[ci[b + q]]);
+  }
 }
 
 // Cholesky of the s x s Gram matrix G (warp 0), then Minv = L^{-T} so that
@@ -257,13 +271,14 @@ __device__ void fill_random(T* Y, int L, int s, int sp, int j0, uint64_t seed, u
 }
 
 template <typename T, bool SPD>
-__global__ void __launch_bounds__(NT) k_subspace(
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 4 : 1) k_subspace(
     const T* __restrict__ XpT_all, const int64_t* __restrict__ xs_off, const T* __restrict__ S_all,
     const int64_t* __restrict__ s_off, const T* __restrict__ work, const int64_t* __restrict__ work_off,
     const int32_t* __restrict__ np_arr, const int32_t* __restrict__ n_arr, const int32_t* __restrict__ m_arr,
     const int32_t* __restrict__ p_arr, const int32_t* __restrict__ sub_off, const int64_t* __restrict__ ent_off,
     const int32_t* __restrict__ lcol, const int32_t* __restrict__ omega, const int32_t* __restrict__ rp,
-    const int32_t* __restrict__ ci, const double* __restrict__ val, const double* __restrict__ ds, T* scratch,
+    const int32_t* __restrict__ ci, const double* __restrict__ val, const double* __restrict__ ds,
+    const T* __restrict__ aval, T* scratch,
     const int64_t* __restrict__ scr_off, int nev, int over, int max_sweeps, int degree, double tol, uint64_t seed,
     const float* __restrict__ warm, int wld, int wk, const int64_t* __restrict__ wseg, float* __restrict__ tgt,
     double* __restrict__ values,
@@ -288,6 +303,7 @@ __global__ void __launch_bounds__(NT) k_subspace(
     return;
   }
   const int sp = (s + 3) & ~3;
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const T* XpT = SPD ? nullptr : XpT_all + xs_off[i];
   // SPD: U = W[Gamma_delta, I_i] (g x p block of W = L^{-1}, leading dimension ld)
   const T* U = work + work_off[i] + (int64_t)m * ld;
@@ -319,7 +335,7 @@ __global__ void __launch_bounds__(NT) k_subspace(
   auto applyK = [&](const T* Yin, T* out, int c0, int nc) {
     if (SPD) {
       cta_gemm<T, true>(p, nc, g, U, ld, Yin + c0, sp, V + c0, sp, gsm);           // V = U^T Y
-      mul_AII(p, pos0, omega, rp, ci, val, ds, ent_off, lcol, V + c0, AV + c0, nc, sp);
+      mul_AII(p, pos0, ent_off, lcol, aval, V + c0, AV + c0, nc, sp);
       cta_gemm<T, false>(g, nc, p, U, ld, AV + c0, sp, out + c0, sp, gsm);         // U (A^_II V)
     } else {
       // W = X_p^T Y = S_G^{-1} X^_p^T S_I Y ; out = X_p W = S_I X^_p S_G^{-1} W
@@ -354,12 +370,11 @@ __global__ void __launch_bounds__(NT) k_subspace(
   const double tiny = sizeof(T) == 8 ? 1e-10 : 1e-5;
   auto orthonormalize = [&](uint64_t salt) {
     for (int attempt = 0; attempt < 4; ++attempt) {
-      for (int j = 0; j < s; ++j) {
+      for (int j = wid; j < s; j += NT / 32) {
         T part = 0;
-        for (int r = threadIdx.x; r < dim; r += NT)
-          part += Y[(int64_t)r * sp + j] * Y[(int64_t)r * sp + j];
-        part = block_sum(part, red);
-        if (threadIdx.x == 0) Pbuf[j] = part > T(0) ? T(1) / sqrt(part) : T(1);
+        for (int r = lane; r < dim; r += 32) part += Y[(int64_t)r * sp + j] * Y[(int64_t)r * sp + j];
+        part = warp_sum(part);
+        if (lane == 0) Pbuf[j] = part > T(0) ? T(1) / sqrt(part) : T(1);
       }
       __syncthreads();
       for (int64_t idx = threadIdx.x; idx < (int64_t)dim * sp; idx += NT) {
@@ -410,50 +425,63 @@ __global__ void __launch_bounds__(NT) k_subspace(
   }
   orthonormalize((uint64_t)i);
 
-  int sweep = 0;
+  for (int j = threadIdx.x; j < s; j += NT) rn[j] = 0;
+  int sweep = 0, last_gain = 0;
+  T best = T(3.0e38);
   for (;;) {
-    // ---- Rayleigh-Ritz (the small eigenproblem in FP64 in both precisions:
-    //      FP32 Jacobi could not separate Ritz values far below the top one)
-    applyK(Y, KY, 0, s);
-    cta_gemm<T, true>(s, s, dim, Y, sp, KY, sp, H, s, gsm);
-    for (int idx = threadIdx.x; idx < s * s; idx += NT) {
-      int a = idx / s, b = idx % s;
-      G[idx] = 0.5 * ((double)H[a * s + b] + (double)H[b * s + a]);
-    }
-    __syncthreads();
-    jacobi<double>(G, Minv, s);
-    if (threadIdx.x == 0) {
-      for (int j = 0; j < s; ++j) perm[j] = j;
-      for (int a = 0; a < s; ++a) {
-        int best = a;
-        for (int b = a + 1; b < s; ++b)
-          if (G[perm[b] * s + perm[b]] > G[perm[best] * s + perm[best]]) best = b;
-        int ti = perm[a]; perm[a] = perm[best]; perm[best] = ti;
+    // ---- Rayleigh-Ritz on the whole block (Jacobi in the working precision).
+    //      Converged columns are only kept out of the filter ("soft" locking):
+    //      the projected problem keeps refining them, so their remaining error
+    //      does not put a floor under the residuals of the columns still active.
+    {
+      const int nl = 0, nr = s;
+      applyK(Y, KY, nl, nr);
+      cta_gemm<T, true>(nr, nr, dim, Y + nl, sp, KY + nl, sp, H, nr, gsm);
+      for (int idx = threadIdx.x; idx < nr * nr; idx += NT) {
+        int a = idx / nr, b = idx % nr;
+        Q[idx] = T(0.5) * (H[a * nr + b] + H[b * nr + a]);
       }
-      for (int j = 0; j < s; ++j) mu[j] = (T)G[perm[j] * s + perm[j]];
+      __syncthreads();
+      jacobi<T>(Q, Pbuf, nr);
+      if (threadIdx.x == 0) {
+        for (int j = 0; j < nr; ++j) perm[j] = j;
+        for (int a = 0; a < nr; ++a) {
+          int best = a;
+          for (int b = a + 1; b < nr; ++b)
+            if (Q[perm[b] * nr + perm[b]] > Q[perm[best] * nr + perm[best]]) best = b;
+          int ti = perm[a]; perm[a] = perm[best]; perm[best] = ti;
+        }
+        for (int j = 0; j < nr; ++j) mu[nl + j] = Q[perm[j] * nr + perm[j]];
+      }
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < nr * nr; idx += NT) {
+        int l = idx / nr, j = idx % nr;
+        QS[idx] = Pbuf[l * nr + perm[j]];
+      }
+      __syncthreads();
+      cta_gemm<T, false>(dim, nr, nr, Y + nl, sp, QS, nr, Yb + nl, sp, gsm);
+      cta_gemm<T, false>(dim, nr, nr, KY + nl, sp, QS, nr, Yc + nl, sp, gsm);
+      for (int64_t idx = threadIdx.x; idx < (int64_t)dim * nr; idx += NT) {
+        int64_t r = idx / nr, j = nl + idx % nr;
+        Y[r * sp + j] = Yb[r * sp + j];
+        KY[r * sp + j] = Yc[r * sp + j];
+      }
+      __syncthreads();
     }
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < s * s; idx += NT) {
-      int l = idx / s, j = idx % s;
-      QS[idx] = (T)Minv[l * s + perm[j]];
-    }
-    __syncthreads();
-    cta_gemm<T, false>(dim, s, s, Y, sp, QS, s, Yb, sp, gsm); swap(Y, Yb);
-    cta_gemm<T, false>(dim, s, s, KY, sp, QS, s, Yb, sp, gsm); swap(KY, Yb);
-    // ---- residuals of the first k Ritz pairs
+    // ---- residuals of the first k Ritz pairs (one warp per column)
     const T mu0 = mu[0] > T(0) ? mu[0] : T(1);
-    for (int j = 0; j < k; ++j) {
+    for (int j = wid; j < k; j += NT / 32) {
       T part = 0, nrm = 0;
-      for (int r = threadIdx.x; r < dim; r += NT) {
+      for (int r = lane; r < dim; r += 32) {
         T a = KY[(int64_t)r * sp + j];
         T b = Y[(int64_t)r * sp + j];
         T d = a - mu[j] * b;
         part += d * d;
         nrm += b * b;
       }
-      part = block_sum(part, red);
-      nrm = block_sum(nrm, red);
-      if (threadIdx.x == 0) {
+      part = warp_sum(part);
+      nrm = warp_sum(nrm);
+      if (lane == 0) {
         // residual relative to the Ritz value, with a floor at the resolution
         // of the working precision relative to the largest Ritz value
         const T eps = sizeof(T) == 8 ? T(1.1e-16) : T(6e-8);
@@ -467,6 +495,12 @@ __global__ void __launch_bounds__(NT) k_subspace(
     for (int j = 0; j < k; ++j) res_max = max(res_max, rn[j]);
     ++sweep;
     if ((double)res_max <= tol || sweep >= max_sweeps) break;
+    // single precision: stop once the residuals stall (no halving in three
+    // sweeps) at the precision's floor
+    if (sizeof(T) == 4) {
+      if (res_max < T(0.5) * best) { best = res_max; last_gain = sweep; }
+      else if (sweep - last_gain >= 3) break;
+    }
     // ---- lock the converged leading Ritz pairs; filter the rest
     int nl = 0;
     while (nl < k && rn[nl] <= (T)tol) ++nl;
@@ -520,30 +554,41 @@ __global__ void __launch_bounds__(NT) k_subspace(
     __syncthreads();
     // near-null directions restart from fresh random vectors
     int first_null = s;
-    for (int j = 0; j < s; ++j)
+    for (int j = nl; j < s; ++j)
       if (!(mu[j] > T(1e-10) * mu0)) { first_null = j; break; }
     if (first_null < s) fill_random(Y, dim, s, sp, first_null, seed ^ 0xA5A5A5A5ull, (uint64_t)i * 7919u + sweep * 104729u);
     orthonormalize((uint64_t)i * 1000003u + sweep);
   }
-  // ---- outputs
+  // ---- outputs, the first k Ritz pairs in descending order
+  if (threadIdx.x == 0) {
+    for (int j = 0; j < k; ++j) perm[j] = j;
+    for (int a = 0; a < k; ++a) {
+      int best = a;
+      for (int b = a + 1; b < k; ++b)
+        if (mu[perm[b]] > mu[perm[best]]) best = b;
+      int ti = perm[a]; perm[a] = perm[best]; perm[best] = ti;
+    }
+  }
+  __syncthreads();
   int kept = 0;
   {
-    const T mu0 = mu[0] > T(0) ? mu[0] : T(0);
+    const T mu0 = mu[perm[0]] > T(0) ? mu[perm[0]] : T(0);
     for (int j = 0; j < k; ++j)
-      if (mu[j] > T(sizeof(T) == 8 ? 1e-12 : 1e-6) * mu0) kept = j + 1;
+      if (mu[perm[j]] > T(sizeof(T) == 8 ? 1e-12 : 1e-6) * mu0) kept = j + 1;
   }
   if (threadIdx.x == 0) { count[i] = kept; sweeps_out[i] = sweep; }
   for (int j = threadIdx.x; j < nev; j += NT) {
-    double v = j < kept ? (SPD ? (double)mu[j] : sqrt(fmax((double)mu[j], 0.0))) : 0.0;
+    const int c = j < kept ? perm[j] : 0;
+    double v = j < kept ? (SPD ? (double)mu[c] : sqrt(fmax((double)mu[c], 0.0))) : 0.0;
     values[(int64_t)i * nev + j] = v;
-    resid[(int64_t)i * nev + j] = j < kept ? (double)rn[j] : 0.0;
+    resid[(int64_t)i * nev + j] = j < kept ? (double)rn[c] : 0.0;
   }
   if (tgt != nullptr && SPD) {
     // converged Ritz vectors z (Gamma_delta rows), the network's training targets
     float* tb = tgt + wseg[i] * nev;
     for (int64_t idx = threadIdx.x; idx < (int64_t)dim * nev; idx += NT) {
       int r = (int)(idx / nev), j = (int)(idx % nev);
-      tb[idx] = j < kept ? (float)Y[(int64_t)r * sp + j] : 0.f;
+      tb[idx] = j < kept ? (float)Y[(int64_t)r * sp + perm[j]] : 0.f;
     }
   }
   double* Zi = Z + z_off[i];
@@ -552,12 +597,12 @@ __global__ void __launch_bounds__(NT) k_subspace(
     cta_gemm<T, true>(p, s, g, U, ld, Y, sp, V, sp, gsm);
     for (int64_t idx = threadIdx.x; idx < (int64_t)p * nev; idx += NT) {
       int r = (int)(idx / nev), j = (int)(idx % nev);
-      Zi[idx] = j < kept ? (double)V[(int64_t)r * sp + j] * ds[omega[pos0 + r]] : 0.0;
+      Zi[idx] = j < kept ? (double)V[(int64_t)r * sp + perm[j]] * ds[omega[pos0 + r]] : 0.0;
     }
   } else {
     for (int64_t idx = threadIdx.x; idx < (int64_t)p * nev; idx += NT) {
       int r = (int)(idx / nev), j = (int)(idx % nev);
-      Zi[idx] = j < kept ? (double)Y[(int64_t)r * sp + j] : 0.0;
+      Zi[idx] = j < kept ? (double)Y[(int64_t)r * sp + perm[j]] : 0.0;
     }
   }
 }
@@ -593,8 +638,8 @@ __global__ void __launch_bounds__(NT) k_warm_features(
     const int32_t* __restrict__ n_arr, const int32_t* __restrict__ m_arr, const int32_t* __restrict__ p_arr,
     const int32_t* __restrict__ sub_off, const int64_t* __restrict__ ent_off, const int32_t* __restrict__ lcol,
     const int32_t* __restrict__ omega, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
-    const double* __restrict__ val, const double* __restrict__ ds, T* scratch, const int64_t* __restrict__ scr_off,
-    const int64_t* __restrict__ wseg, float* __restrict__ feat) {
+    const double* __restrict__ val, const double* __restrict__ ds, const T* __restrict__ aval, T* scratch,
+    const int64_t* __restrict__ scr_off, const int64_t* __restrict__ wseg, float* __restrict__ feat) {
   COUNT_LAUNCH();
   extern __shared__ double shd[];
   __shared__ double red[NT / 32];
@@ -619,7 +664,7 @@ __global__ void __launch_bounds__(NT) k_warm_features(
   __syncthreads();
   auto applyK2 = [&](const T* in, T* o) {
     cta_gemm<T, true>(p, 2, g, U, ld, in, 2, V, 2, gsm);
-    mul_AII(p, pos0, omega, rp, ci, val, ds, ent_off, lcol, V, AV, 2, 2);
+    mul_AII(p, pos0, ent_off, lcol, aval, V, AV, 2, 2);
     cta_gemm<T, false>(g, 2, p, U, ld, AV, 2, o, 2, gsm);
   };
   applyK2(P, KP);
@@ -726,6 +771,15 @@ void run_eigen(Handle& h, cudaStream_t s) {
   // keeps such subdomains from holding the launch
   const int maxsw = h.opt.max_sweeps > 0 ? h.opt.max_sweeps : (h.fp32 ? 12 : 40);
   const int degree = h.opt.filter_degree > 0 ? h.opt.filter_degree : 4;
+  // scaled local values in the working precision (SPD products with A^_II)
+  T* aval = nullptr;
+  if (spd) {
+    aval = mem.alloc<T>(std::max<int64_t>(h.ov.n_ent, 1));
+    const unsigned gsv = (unsigned)std::min<int64_t>(std::max<int64_t>(ceil_div(h.ov.sum_n, NT), 1), 152 * 16);
+    k_scaled_values<T><<<gsv, NT, 0, s>>>(h.ov.sum_n, h.ov.omega, h.ov.ent_off, h.row_ptr,
+                                                           h.col_idx, h.val, h.dscale, aval);
+    CK_LAUNCH("scaled local values");
+  }
   // learned warm start (SPD path): features per Gamma_delta node, the
   // network's start blocks, and (when recorded) the converged blocks
   const bool want_warm = spd && (h.opt.warm_start || h.opt.record_warm);
@@ -743,7 +797,7 @@ void run_eigen(Handle& h, cudaStream_t s) {
     CK(cudaFuncSetAttribute(k_warm_features<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm));
     k_warm_features<T><<<N, NT, fsm, s>>>((const T*)dn.work, dn.work_off, dn.np, h.dev_n, h.dev_m, h.dev_p,
                                           h.ov.sub_off, h.ov.ent_off, h.ov.lcol, h.ov.omega, h.row_ptr, h.col_idx,
-                                          h.val, h.dscale, (T*)co.scratch, co.scr_off, h.wseg, h.wfeat);
+                                          h.val, h.dscale, aval, (T*)co.scratch, co.scr_off, h.wseg, h.wfeat);
     CK_LAUNCH("warm-start features");
     if (h.opt.warm_start && h.warm_rows > 0) {
       Mlp& net = h.opt.warm_net->net;
@@ -757,7 +811,7 @@ void run_eigen(Handle& h, cudaStream_t s) {
     CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<N, NT, smem, s>>>((const T*)dn.XpT, dn.xs_off, (const T*)dn.S, dn.s_off, (const T*)dn.work, dn.work_off,
                              dn.np, h.dev_n, h.dev_m, h.dev_p, h.ov.sub_off, h.ov.ent_off, h.ov.lcol, h.ov.omega,
-                             h.row_ptr, h.col_idx, h.val, h.dscale, (T*)co.scratch, co.scr_off, nev, over, maxsw,
+                             h.row_ptr, h.col_idx, h.val, h.dscale, aval, (T*)co.scratch, co.scr_off, nev, over, maxsw,
                              degree, tol, h.opt.seed, warm, wld, wk, h.wseg, h.wtgt, co.values, co.resid, co.count,
                              co.sweeps, co.Z, co.z_off);
   };

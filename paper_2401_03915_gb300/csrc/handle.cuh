@@ -122,6 +122,8 @@ struct Handle {
   asm_setup_info info{};
   cudaEvent_t ev[16];
   bool events = false;
+  int num_sms = 152;                // multiprocessors of the device
+  int tile_ctas = 6;                // resident tile-pass blocks per SM (picked by tune_apply)
   cudaStream_t side = nullptr;      // second stream: the coarse part of the apply runs beside the local part
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
@@ -134,6 +136,7 @@ void build_coarse(Handle& h, cudaStream_t s);                  // coarse.cu: E a
 void apply_preconditioner(Handle& h, const double* r, double* z, cudaStream_t s,
                           const int32_t* done = nullptr);                         // apply.cu
 void time_apply(Handle& h, const double* r, double* z, int iters, cudaStream_t s, double* ms);
+void tune_apply(Handle& h, cudaStream_t s);                                       // apply.cu
 void spmv(Handle& h, const double* x, double* y, cudaStream_t s);                 // krylov.cu
 void coarse_solve(Handle& h, const double* c, double* y, cudaStream_t s,
                   const int32_t* done = nullptr);                                 // coarse.cu

