@@ -421,7 +421,7 @@ def run_ours(args):
             "iterations": infos[-1].iterations, "true_relres": infos[-1].true_relres,
             "setup_stages_ms": stages, "n_C": nC, "sweeps_max": setup_info.sweeps_max,
             "apply_ms": tap, "apply_gbs": apply_gbs,
-            "roofline": {"bound": "hbm", "kernel": "k_apply_tiles (one pass of the local part of the apply)",
+            "roofline": {"bound": "hbm", "kernel": "k_row_pass / k_col_pass (one pass over the local tiles of the apply)",
                          "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                          "peak_kind": peak_kind, "traffic": None,
                          "algorithmic_bytes_per_launch": pass_bytes},

@@ -3,10 +3,11 @@
 //
 // Local part: A_ii^{-1} = D^{-1/2} A^_ii^{-1} D^{-1/2}.  SPD: A^_ii^{-1} = W^T W
 // with W = L^{-1} stored as its lower TILE x TILE tiles: a row pass t = W x
-// and a column pass y = W^T t, each one flat, load-balanced sweep over the
-// tiles of all subdomains.  General A: the explicit inverse, all tiles, one
-// row pass.  Every tile product goes to its own slot; a reduction sums the
-// slots of each row in a fixed order and the pull kernel sums the
+// and a column pass y = W^T t.  General A: the explicit inverse, all tiles,
+// one row pass.  A block owns one row block (row pass) or one column block
+// (column pass) of one subdomain and streams its tiles, accumulating in
+// registers, so each output is summed in a fixed order by one block; the
+// blocks take the work items longest first.  The pull kernel sums the
 // occurrences of each node in a fixed order: deterministic, no atomics.
 // Coarse part: Z^T r per subdomain, the FP64 coarse solve, and Z y added in
 // the pull kernel (Z_i is supported on Omega_{I_i}).
@@ -37,73 +38,138 @@ __device__ __forceinline__ void load4<double>(const double* p, double (&v)[4]) {
   v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
 }
 
-// Thread t of the block owns rows (t/16) + 16a, a = 0..3, and the four
-// columns 4 (t%16) .. 4 (t%16) + 3 of the tile.
-// ROW pass:    slot (I, J) <- T x_J    with x gathered from r (scaled) via Omega_i
-// COLUMN pass: slot (J, I) <- T^T x_I  with x read from the per-position array xpos
-template <typename T, bool ROW>
-__global__ void __launch_bounds__(NT) k_apply_tiles(const T* __restrict__ tiles, const int4* __restrict__ desc,
-                                                    int64_t ntiles, const int32_t* __restrict__ omega,
-                                                    const int32_t* __restrict__ sub_off,
-                                                    const int32_t* __restrict__ n_arr, const int32_t* __restrict__ nt_arr,
-                                                    const int64_t* __restrict__ part_off, const double* __restrict__ r,
-                                                    const double* __restrict__ ds, const double* __restrict__ xpos,
-                                                    T* __restrict__ partials, const int32_t* __restrict__ done) {
+template <typename T>
+__device__ __forceinline__ void load_tile(const T* __restrict__ tile, int rg, int cq, T (&v)[4][4]) {
+#pragma unroll
+  for (int a = 0; a < 4; ++a) load4<T>(tile + (rg + 16 * a) * TILE + 4 * cq, v[a]);
+}
+
+// x in the padded position space of each subdomain (nt_i * TILE entries from
+// pad_off[i], zero beyond n_i): xs = (T)(r * s) gathered through Omega_i.
+template <typename T>
+__global__ void __launch_bounds__(NT) k_gather_x(const int32_t* __restrict__ omega, const int32_t* __restrict__ sub_off,
+                                                 const int32_t* __restrict__ n_arr, const int32_t* __restrict__ nt_arr,
+                                                 const int64_t* __restrict__ pad_off, const double* __restrict__ r,
+                                                 const double* __restrict__ ds, T* __restrict__ xs,
+                                                 const int32_t* __restrict__ done) {
   COUNT_LAUNCH();
   if (done != nullptr && *done) return;
-  __shared__ T xv[TILE];
-  __shared__ T colpart[NT / 32][TILE];
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const int cq = tid & 15, rg = tid >> 4;
-  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const int4 d = desc[t];
-    const int i = d.x, I = d.y, J = d.z;
-    const int n = n_arr[i], nt = nt_arr[i], b0 = sub_off[i];
-    __syncthreads();
-    if (tid < TILE) {
-      if (ROW) {
-        int a = J * TILE + tid;
-        int v = a < n ? omega[b0 + a] : 0;
-        xv[tid] = a < n ? (T)(r[v] * ds[v]) : T(0);
-      } else {
-        int a = I * TILE + tid;
-        xv[tid] = a < n ? (T)xpos[b0 + a] : T(0);
+  const int i = blockIdx.x;
+  const int n = n_arr[i], np = nt_arr[i] * TILE, b0 = sub_off[i];
+  T* out = xs + pad_off[i];
+  for (int a = threadIdx.x; a < np; a += NT) {
+    T v = 0;
+    if (a < n) {
+      const int g = omega[b0 + a];
+      v = (T)(r[g] * ds[g]);
+    }
+    out[a] = v;
+  }
+}
+
+// Row pass.  Item (i, I): out_I = sum_J T_IJ x_J over J <= I (SPD, lower
+// tiles) or all J (general).  Thread t owns rows (t/16) + 16a, a = 0..3, and
+// columns 4 (t%16) .. +3 of every tile; the next tile is loaded while the
+// current one is multiplied.  Output: the padded vector tout (SPD first
+// pass) or, per Omega position, ypos in FP64 (general).
+template <typename T, bool SPD>
+__global__ void __launch_bounds__(NT) k_row_pass(const T* __restrict__ tiles, const int64_t* __restrict__ tile_off,
+                                                 const int2* __restrict__ items, int nitems,
+                                                 const int32_t* __restrict__ sub_off, const int32_t* __restrict__ n_arr,
+                                                 const int32_t* __restrict__ nt_arr, const int64_t* __restrict__ pad_off,
+                                                 const T* __restrict__ xs, T* __restrict__ tout,
+                                                 double* __restrict__ ypos, const int32_t* __restrict__ done) {
+  COUNT_LAUNCH();
+  if (done != nullptr && *done) return;
+  const int tid = threadIdx.x, cq = tid & 15, rg = tid >> 4;
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const int2 w = items[it];
+    const int i = w.x, I = w.y, nt = nt_arr[i];
+    const int cnt = SPD ? I + 1 : nt;
+    const T* base = tiles + (tile_off[i] + (SPD ? (int64_t)I * (I + 1) / 2 : (int64_t)I * nt)) * (TILE * TILE);
+    const T* x = xs + pad_off[i] + 4 * cq;
+    T acc[4] = {0, 0, 0, 0};
+    T v[4][4], vn[4][4];
+    load_tile<T>(base, rg, cq, v);
+    for (int J = 0; J < cnt; ++J) {
+      if (J + 1 < cnt) load_tile<T>(base + (int64_t)(J + 1) * (TILE * TILE), rg, cq, vn);
+      T xv[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) xv[q] = x[J * TILE + q];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) acc[a] += v[a][0] * xv[0] + v[a][1] * xv[1] + v[a][2] * xv[2] + v[a][3] * xv[3];
+      if (J + 1 < cnt) {
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) v[a][q] = vn[a][q];
       }
     }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      T s = acc[a];
+      s += __shfl_xor_sync(0xffffffffu, s, 8);
+      s += __shfl_xor_sync(0xffffffffu, s, 4);
+      s += __shfl_xor_sync(0xffffffffu, s, 2);
+      s += __shfl_xor_sync(0xffffffffu, s, 1);
+      if (cq == 0) {
+        const int row = I * TILE + rg + 16 * a;
+        if (SPD) tout[pad_off[i] + row] = s;
+        else if (row < n_arr[i]) ypos[sub_off[i] + row] = (double)s;
+      }
+    }
+  }
+}
+
+// Column pass (SPD).  Item (i, J): y_J = sum_{I >= J} T_IJ^T t_I, written
+// per Omega position to ypos in FP64.
+template <typename T>
+__global__ void __launch_bounds__(NT) k_col_pass(const T* __restrict__ tiles, const int64_t* __restrict__ tile_off,
+                                                 const int2* __restrict__ items, int nitems,
+                                                 const int32_t* __restrict__ sub_off, const int32_t* __restrict__ n_arr,
+                                                 const int32_t* __restrict__ nt_arr, const int64_t* __restrict__ pad_off,
+                                                 const T* __restrict__ tin, double* __restrict__ ypos,
+                                                 const int32_t* __restrict__ done) {
+  COUNT_LAUNCH();
+  if (done != nullptr && *done) return;
+  __shared__ T colpart[NT / 32][TILE];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, cq = tid & 15, rg = tid >> 4;
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const int2 w = items[it];
+    const int i = w.x, J = w.y, nt = nt_arr[i];
+    const int64_t t0 = tile_off[i];
+    const T* t = tin + pad_off[i];
+    T c[4] = {0, 0, 0, 0};
+    T v[4][4], vn[4][4];
+    load_tile<T>(tiles + (t0 + (int64_t)J * (J + 1) / 2 + J) * (TILE * TILE), rg, cq, v);
+    for (int I = J; I < nt; ++I) {
+      if (I + 1 < nt) load_tile<T>(tiles + (t0 + (int64_t)(I + 1) * (I + 2) / 2 + J) * (TILE * TILE), rg, cq, vn);
+      T tv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) tv[a] = t[I * TILE + rg + 16 * a];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) c[q] += v[0][q] * tv[0] + v[1][q] * tv[1] + v[2][q] * tv[2] + v[3][q] * tv[3];
+      if (I + 1 < nt) {
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) v[a][q] = vn[a][q];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) c[q] += __shfl_xor_sync(0xffffffffu, c[q], 16);
     __syncthreads();
-    const T* tile = tiles + t * (TILE * TILE);
-    T v[4][4];
+    if (lane < 16) {
 #pragma unroll
-    for (int a = 0; a < 4; ++a) load4<T>(tile + (rg + 16 * a) * TILE + 4 * cq, v[a]);
-    T* P = partials + part_off[i];
-    if (ROW) {
+      for (int q = 0; q < 4; ++q) colpart[wid][4 * cq + q] = c[q];
+    }
+    __syncthreads();
+    if (tid < TILE) {
+      T s = 0;
 #pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        T s = v[a][0] * xv[4 * cq] + v[a][1] * xv[4 * cq + 1] + v[a][2] * xv[4 * cq + 2] + v[a][3] * xv[4 * cq + 3];
-        s += __shfl_xor_sync(0xffffffffu, s, 8);
-        s += __shfl_xor_sync(0xffffffffu, s, 4);
-        s += __shfl_xor_sync(0xffffffffu, s, 2);
-        s += __shfl_xor_sync(0xffffffffu, s, 1);
-        if (cq == 0) P[((int64_t)I * nt + J) * TILE + rg + 16 * a] = s;
-      }
-    } else {
-      T c[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-        c[q] = v[0][q] * xv[rg] + v[1][q] * xv[rg + 16] + v[2][q] * xv[rg + 32] + v[3][q] * xv[rg + 48];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) c[q] += __shfl_xor_sync(0xffffffffu, c[q], 16);
-      if (lane < 16) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) colpart[wid][4 * cq + q] = c[q];
-      }
-      __syncthreads();
-      if (tid < TILE) {
-        T s = 0;
-#pragma unroll
-        for (int w = 0; w < NT / 32; ++w) s += colpart[w][tid];
-        P[((int64_t)J * nt + I) * TILE + tid] = s;
-      }
+      for (int w2 = 0; w2 < NT / 32; ++w2) s += colpart[w2][tid];
+      const int col = J * TILE + tid;
+      if (col < n_arr[i]) ypos[sub_off[i] + col] = (double)s;
     }
   }
 }
@@ -138,31 +204,6 @@ __global__ void __launch_bounds__(NT) k_coarse_restrict(const double* __restrict
       c[col_off[i] + j0 + threadIdx.x] = s;
     }
     __syncthreads();
-  }
-}
-
-// y_pos[k] = sum_J partial[i][a/TILE][J][a%TILE] for every omega position
-// k = (i, a), J over the written slots: all (tri 0), J <= a/TILE (tri 1),
-// J >= a/TILE (tri 2).
-template <typename T>
-__global__ void __launch_bounds__(NT) k_reduce_partials(int64_t m, const int32_t* __restrict__ pos_sub,
-                                                        const int32_t* __restrict__ sub_off,
-                                                        const int32_t* __restrict__ nt_arr,
-                                                        const int64_t* __restrict__ part_off,
-                                                        const T* __restrict__ partials, double* __restrict__ ypos,
-                                                        int tri, const int32_t* __restrict__ done) {
-  COUNT_LAUNCH();
-  if (done != nullptr && *done) return;
-  for (int64_t k = blockIdx.x * (int64_t)NT + threadIdx.x; k < m; k += (int64_t)gridDim.x * NT) {
-    const int i = pos_sub[k];
-    const int a = (int)(k - sub_off[i]);
-    const int nt = nt_arr[i];
-    const int I = a / TILE;
-    const T* P = partials + part_off[i] + (int64_t)I * nt * TILE + (a % TILE);
-    const int j0 = tri == 2 ? I : 0, j1 = tri == 1 ? I + 1 : nt;
-    double s = 0;
-    for (int J = j0; J < j1; ++J) s += (double)P[(int64_t)J * TILE];
-    ypos[k] = s;
   }
 }
 
@@ -205,35 +246,48 @@ __global__ void __launch_bounds__(NT) k_apply_pull(int n, const int32_t* __restr
   }
 }
 
-template <typename T>
-void reduce_partials(Handle& h, double* out, int tri, cudaStream_t s, const int32_t* done) {
-  Dense& dn = h.dn;
-  unsigned gr = (unsigned)std::min<int64_t>(ceil_div(h.ov.sum_n, NT), 152 * 16);
-  k_reduce_partials<T><<<gr, NT, 0, s>>>(h.ov.sum_n, h.ov.pos_sub, h.ov.sub_off, dn.nt, dn.part_off,
-                                         (const T*)dn.partials, out, tri, done);
-}
-
 // Local part up to the per-position results in dn.ypos.
 // SPD: t = W x (row pass over the lower tiles of W), then y = W^T t (column
 // pass); general: y = A^_ii^{-1} x (row pass over all tiles).
 template <typename T>
-void apply_local(Handle& h, const double* r, cudaStream_t s, const int32_t* done) {
-  Dense& dn = h.dn;
+unsigned tile_grid(const Handle& h, int nitems) {
   // resident blocks per SM chosen by tune_apply: enough to saturate HBM
   // while leaving room for the coarse kernels on the side stream
-  unsigned gt = (unsigned)std::min<int64_t>(std::max<int64_t>(dn.n_tiles, 1), (int64_t)h.num_sms * h.tile_ctas);
-  k_apply_tiles<T, true><<<gt, NT, 0, s>>>((const T*)dn.tiles, dn.tile_desc, dn.n_tiles, h.ov.omega, h.ov.sub_off,
-                                           h.dev_n, dn.nt, dn.part_off, r, h.dscale, nullptr, (T*)dn.partials,
-                                           done);
-  if (h.opt.spd) {
-    reduce_partials<T>(h, dn.tpos, 1, s, done);
-    k_apply_tiles<T, false><<<gt, NT, 0, s>>>((const T*)dn.tiles, dn.tile_desc, dn.n_tiles, h.ov.omega,
-                                              h.ov.sub_off, h.dev_n, dn.nt, dn.part_off, nullptr, nullptr, dn.tpos,
-                                              (T*)dn.partials, done);
-    reduce_partials<T>(h, dn.ypos, 2, s, done);
-  } else {
-    reduce_partials<T>(h, dn.ypos, 0, s, done);
-  }
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(nitems, (int64_t)h.num_sms * h.tile_ctas));
+}
+
+template <typename T>
+void gather_x(Handle& h, const double* r, cudaStream_t s, const int32_t* done) {
+  Dense& dn = h.dn;
+  k_gather_x<T><<<h.N, NT, 0, s>>>(h.ov.omega, h.ov.sub_off, h.dev_n, dn.nt, dn.pad_off, r, h.dscale, (T*)dn.xpad,
+                                   done);
+}
+
+template <typename T>
+void row_pass(Handle& h, cudaStream_t s, const int32_t* done) {
+  Dense& dn = h.dn;
+  const unsigned g = tile_grid<T>(h, dn.n_row_items);
+  if (h.opt.spd)
+    k_row_pass<T, true><<<g, NT, 0, s>>>((const T*)dn.tiles, dn.tile_off, dn.row_items, dn.n_row_items, h.ov.sub_off,
+                                         h.dev_n, dn.nt, dn.pad_off, (const T*)dn.xpad, (T*)dn.tpad, dn.ypos, done);
+  else
+    k_row_pass<T, false><<<g, NT, 0, s>>>((const T*)dn.tiles, dn.tile_off, dn.row_items, dn.n_row_items, h.ov.sub_off,
+                                          h.dev_n, dn.nt, dn.pad_off, (const T*)dn.xpad, (T*)dn.tpad, dn.ypos, done);
+}
+
+template <typename T>
+void col_pass(Handle& h, cudaStream_t s, const int32_t* done) {
+  Dense& dn = h.dn;
+  const unsigned g = tile_grid<T>(h, dn.n_col_items);
+  k_col_pass<T><<<g, NT, 0, s>>>((const T*)dn.tiles, dn.tile_off, dn.col_items, dn.n_col_items, h.ov.sub_off, h.dev_n,
+                                 dn.nt, dn.pad_off, (const T*)dn.tpad, dn.ypos, done);
+}
+
+template <typename T>
+void apply_local(Handle& h, const double* r, cudaStream_t s, const int32_t* done) {
+  gather_x<T>(h, r, s, done);
+  row_pass<T>(h, s, done);
+  if (h.opt.spd) col_pass<T>(h, s, done);
 }
 
 // Z^T r and the coarse solve; returns the coarse solution (or null).
@@ -278,32 +332,18 @@ void apply_impl(Handle& h, const double* r, double* z, cudaStream_t s, const int
 
 template <typename T>
 void time_impl(Handle& h, const double* r, double* z, int iters, cudaStream_t s, double* ms) {
-  Dense& dn = h.dn;
   cudaEvent_t e[8];
   for (auto& x : e) CK(cudaEventCreate(&x));
   double acc[6] = {0, 0, 0, 0, 0, 0};
-  const unsigned gt = (unsigned)std::min<int64_t>(std::max<int64_t>(dn.n_tiles, 1), (int64_t)h.num_sms * h.tile_ctas);
   const int passes = h.opt.spd ? 2 : 1;
   for (int it = 0; it < iters; ++it) {
     CK(cudaEventRecord(e[0], s));
-    k_apply_tiles<T, true><<<gt, NT, 0, s>>>((const T*)dn.tiles, dn.tile_desc, dn.n_tiles, h.ov.omega,
-                                             h.ov.sub_off, h.dev_n, dn.nt, dn.part_off, r, h.dscale, nullptr,
-                                             (T*)dn.partials, nullptr);
+    gather_x<T>(h, r, s, nullptr);
     CK(cudaEventRecord(e[1], s));
-    float t2 = 0;
-    if (h.opt.spd) {
-      reduce_partials<T>(h, dn.tpos, 1, s, nullptr);
-      CK(cudaEventRecord(e[2], s));
-      k_apply_tiles<T, false><<<gt, NT, 0, s>>>((const T*)dn.tiles, dn.tile_desc, dn.n_tiles, h.ov.omega,
-                                                h.ov.sub_off, h.dev_n, dn.nt, dn.part_off, nullptr, nullptr,
-                                                dn.tpos, (T*)dn.partials, nullptr);
-      CK(cudaEventRecord(e[3], s));
-      reduce_partials<T>(h, dn.ypos, 2, s, nullptr);
-    } else {
-      CK(cudaEventRecord(e[2], s));
-      CK(cudaEventRecord(e[3], s));
-      reduce_partials<T>(h, dn.ypos, 0, s, nullptr);
-    }
+    row_pass<T>(h, s, nullptr);
+    CK(cudaEventRecord(e[2], s));
+    if (h.opt.spd) col_pass<T>(h, s, nullptr);
+    CK(cudaEventRecord(e[3], s));
     CK(cudaEventRecord(e[4], s));
     const double* yc = apply_coarse(h, r, s, nullptr);
     CK(cudaEventRecord(e[5], s));
@@ -312,8 +352,8 @@ void time_impl(Handle& h, const double* r, double* z, int iters, cudaStream_t s,
     apply_impl<T>(h, r, z, s, nullptr);  // as the solver runs it (coarse part on the side stream)
     CK(cudaEventRecord(e[7], s));
     CK(cudaEventSynchronize(e[7]));
-    float a, b, c, d, f, g;
-    CK(cudaEventElapsedTime(&a, e[0], e[1]));
+    float a, t2, b, c, d, f, g;
+    CK(cudaEventElapsedTime(&a, e[1], e[2]));
     CK(cudaEventElapsedTime(&t2, e[2], e[3]));
     CK(cudaEventElapsedTime(&b, e[0], e[4]));
     CK(cudaEventElapsedTime(&c, e[4], e[5]));

@@ -163,7 +163,13 @@ asm_status asm_setup(const asm_csr* A, const int32_t* part, int32_t N, int32_t o
     h.mem.stream = s;
     for (auto& e : h.ev) CK(cudaEventCreate(&e));
     h.events = true;
-    CK(cudaStreamCreateWithFlags(&h.side, cudaStreamNonBlocking));
+    {
+      // the coarse part of the apply is a chain of short FP64 kernels: at the
+      // highest priority they take SM slots as soon as the tile passes free them
+      int least = 0, greatest = 0;
+      CK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+      CK(cudaStreamCreateWithPriority(&h.side, cudaStreamNonBlocking, greatest));
+    }
     CK(cudaEventCreateWithFlags(&h.ev_fork, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&h.ev_join, cudaEventDisableTiming));
     CK(cudaEventRecord(h.ev[0], s));
@@ -220,6 +226,11 @@ asm_status asm_setup(const asm_csr* A, const int32_t* part, int32_t N, int32_t o
     inf.stage_ms[5] = h.co.n_C > 0 ? elapsed(h.ev[6], h.ev[7]) : 0.f;
     inf.stage_ms[6] = h.co.n_C > 0 ? elapsed(h.ev[7], h.ev[8]) : 0.f;
     inf.stage_ms[7] = elapsed(h.ev[0], h.ev[8]);
+    inf.coarse_levels = h.nd.nlevels;
+    inf.coarse_fronts = h.nd.nfronts;
+    inf.coarse_front_entries = h.nd.n_mat;
+    inf.coarse_max_front = h.nd.max_m;
+    inf.tile_ctas = h.tile_ctas;
   });
   if (st != ASM_OK) {
     free_handle_memory(H->h);

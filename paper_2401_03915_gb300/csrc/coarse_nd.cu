@@ -30,6 +30,10 @@ namespace {
 
 constexpr int NT = 256;
 constexpr int FB = 64;  // block size of the fronts
+// Blocks per 64-row task of the forward/backward solve: one row per warp.
+// The solve is bound by GB300's FP64 FMA rate (2 per cycle per SM), so every
+// level is spread over as many SMs as it has rows to give.
+constexpr int SPLIT = FB / (NT / 32);
 
 // ---------------------------------------------------------------------------
 // device kernels
@@ -203,11 +207,14 @@ __global__ void __launch_bounds__(NT) k_front_colpanel(const FrontDev* __restric
   }
 }
 
-// Front right-hand side f (first nvp entries: V, then B) into shared memory.
+// Entries of the front right-hand side f (first nvp entries: V, then B) into
+// shared memory: [0, nvp) and, if nb > 0, [nvp + b0, nvp + b0 + nb).
 __device__ void assemble_rhs(const FrontDev& f, const FrontDev* __restrict__ fr, const int32_t* __restrict__ dof,
                              const int32_t* __restrict__ children, const int32_t* __restrict__ invmap,
-                             const double* __restrict__ vecs, const double* __restrict__ c, double* sf) {
-  for (int a = threadIdx.x; a < f.m; a += NT) {
+                             const double* __restrict__ vecs, const double* __restrict__ c, double* sf, int b0,
+                             int nb) {
+  for (int t = threadIdx.x; t < f.nvp + nb; t += NT) {
+    const int a = t < f.nvp ? t : f.nvp + b0 + (t - f.nvp);
     double v = 0;
     if (a < f.nvp) {
       int d = dof[a];
@@ -224,7 +231,7 @@ __device__ void assemble_rhs(const FrontDev& f, const FrontDev* __restrict__ fr,
 }
 
 // Forward: task (front, B row tile) computes u rows; tile -1 stores f_V.
-// Four blocks per task, 16 rows each; a warp reads a row contiguously.
+// SPLIT blocks per task, one row per warp; a warp reads its row contiguously.
 __global__ void __launch_bounds__(NT) k_front_forward(const FrontDev* __restrict__ fr, const int2* __restrict__ tasks,
                                                       const int32_t* __restrict__ dofs,
                                                       const int32_t* __restrict__ children,
@@ -234,11 +241,13 @@ __global__ void __launch_bounds__(NT) k_front_forward(const FrontDev* __restrict
   COUNT_LAUNCH();
   if (done != nullptr && *done) return;
   extern __shared__ double sf[];
-  const int2 tk = tasks[blockIdx.x >> 2];
-  const int quarter = blockIdx.x & 3;
+  const int2 tk = tasks[blockIdx.x / SPLIT];
+  const int quarter = blockIdx.x % SPLIT;
   const FrontDev f = fr[tk.x];
   if (tk.y < 0 && quarter != 0) return;
-  assemble_rhs(f, fr, dofs + f.dof_off, children, invmap, vecs, c, sf);
+  // f_V and this block's own B rows only
+  const int b0 = tk.y * FB + quarter * (FB / SPLIT);
+  assemble_rhs(f, fr, dofs + f.dof_off, children, invmap, vecs, c, sf, b0, tk.y < 0 ? 0 : FB / SPLIT);
   double* vec = vecs + f.vec_off;
   if (tk.y < 0) {
     for (int a = threadIdx.x; a < f.nvp; a += NT) vec[a] = sf[a];
@@ -246,8 +255,8 @@ __global__ void __launch_bounds__(NT) k_front_forward(const FrontDev* __restrict
   }
   const double* F = M + f.mat_off;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int rr = wid; rr < FB / 4; rr += NT / 32) {
-    const int r = tk.y * FB + quarter * (FB / 4) + rr;
+  for (int rr = wid; rr < FB / SPLIT; rr += NT / 32) {
+    const int r = tk.y * FB + quarter * (FB / SPLIT) + rr;
     const double* row = F + (int64_t)(f.nvp + r) * f.m;
     double acc = 0;
     for (int q = lane; q < f.nvp; q += 32) acc += row[q] * sf[q];
@@ -256,7 +265,7 @@ __global__ void __launch_bounds__(NT) k_front_forward(const FrontDev* __restrict
   }
 }
 
-// Backward: task (front, V row tile): y_V = M_VV f_V - M_VB y_B; four blocks per task.
+// Backward: task (front, V row tile): y_V = M_VV f_V - M_VB y_B; SPLIT blocks per task.
 __global__ void __launch_bounds__(NT) k_front_backward(const FrontDev* __restrict__ fr, const int2* __restrict__ tasks,
                                                        const int32_t* __restrict__ dofs, const double* __restrict__ M,
                                                        const double* __restrict__ vecs, double* __restrict__ y,
@@ -264,8 +273,8 @@ __global__ void __launch_bounds__(NT) k_front_backward(const FrontDev* __restric
   COUNT_LAUNCH();
   if (done != nullptr && *done) return;
   extern __shared__ double sx[];  // [f_V ; -y_B]
-  const int2 tk = tasks[blockIdx.x >> 2];
-  const int quarter = blockIdx.x & 3;
+  const int2 tk = tasks[blockIdx.x / SPLIT];
+  const int quarter = blockIdx.x % SPLIT;
   const FrontDev f = fr[tk.x];
   const int32_t* dof = dofs + f.dof_off;
   const double* vec = vecs + f.vec_off;
@@ -276,8 +285,8 @@ __global__ void __launch_bounds__(NT) k_front_backward(const FrontDev* __restric
   __syncthreads();
   const double* F = M + f.mat_off;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int rr = wid; rr < FB / 4; rr += NT / 32) {
-    const int r = tk.y * FB + quarter * (FB / 4) + rr;
+  for (int rr = wid; rr < FB / SPLIT; rr += NT / 32) {
+    const int r = tk.y * FB + quarter * (FB / SPLIT) + rr;
     const double* row = F + (int64_t)r * f.m;
     double acc = 0;
     for (int q = lane; q < f.m; q += 32) acc += row[q] * sx[q];
@@ -592,12 +601,12 @@ void nd_solve(Handle& h, const double* c, double* y, cudaStream_t s, const int32
   const size_t smem = sizeof(double) * std::max(nd.max_m, 1);
   for (int L = 0; L < nd.nlevels; ++L) {
     int nf = nd.lv_fwd[L + 1] - nd.lv_fwd[L];
-    if (nf) k_front_forward<<<4 * nf, NT, smem, s>>>(nd.fr, nd.t_fwd + nd.lv_fwd[L], nd.dofs, nd.children, nd.invmap,
+    if (nf) k_front_forward<<<SPLIT * nf, NT, smem, s>>>(nd.fr, nd.t_fwd + nd.lv_fwd[L], nd.dofs, nd.children, nd.invmap,
                                                  nd.M, nd.vecs, c, done);
   }
   for (int L = nd.nlevels - 1; L >= 0; --L) {
     int nb = nd.lv_bwd[L + 1] - nd.lv_bwd[L];
-    if (nb) k_front_backward<<<4 * nb, NT, smem, s>>>(nd.fr, nd.t_bwd + nd.lv_bwd[L], nd.dofs, nd.M, nd.vecs, y, done);
+    if (nb) k_front_backward<<<SPLIT * nb, NT, smem, s>>>(nd.fr, nd.t_bwd + nd.lv_bwd[L], nd.dofs, nd.M, nd.vecs, y, done);
   }
 }
 

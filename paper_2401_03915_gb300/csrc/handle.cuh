@@ -39,14 +39,12 @@ struct Dense {
   std::vector<int64_t> h_s_off;       // element offset of S (g x g)
   std::vector<int32_t> h_nt;          // tiles per side
   std::vector<int64_t> h_tile_off;    // first apply tile of subdomain i
-  std::vector<int64_t> h_part_off;    // partial-sum slots offset (elements)
   int64_t* work_off = nullptr;
   int64_t* xs_off = nullptr;
   int64_t* s_off = nullptr;
   int32_t* np = nullptr;
   int32_t* nt = nullptr;
   int64_t* tile_off = nullptr;
-  int64_t* part_off = nullptr;
   int4* tile_desc = nullptr;          // (subdomain, I, J, 0) of every apply tile
   void* work = nullptr;               // A^_ii, then W = L^{-1} (SPD) or A^_ii^{-1} (row-major, ld = np)
   void* XpT = nullptr;                // general A: X_p^T = -(B^{-1} C)[:p]^T (g x p)
@@ -54,10 +52,14 @@ struct Dense {
   void* dinv = nullptr;               // SPD: inverses of the diagonal 64x64 blocks of L
   int64_t* dinv_off = nullptr;
   void* tiles = nullptr;              // apply tiles, TILE*TILE each
-  void* partials = nullptr;           // per (subdomain, I, J) TILE partial sums
+  int64_t* pad_off = nullptr;         // start of subdomain i in the padded position space (nt_i * TILE each)
+  void* xpad = nullptr;               // apply: gathered, scaled r in the padded space (local precision)
+  void* tpad = nullptr;               // apply: t = W x (SPD first pass), padded space
+  int2* row_items = nullptr;          // (subdomain, row block), most tiles first
+  int2* col_items = nullptr;          // (subdomain, column block), most tiles first (SPD)
+  int n_row_items = 0, n_col_items = 0;
   double* ypos = nullptr;             // per omega position: local solution before the pull
-  double* tpos = nullptr;             // per omega position: W x (SPD apply, first pass)
-  int64_t n_tiles = 0, n_work = 0, n_xs = 0, n_s = 0, n_part = 0;
+  int64_t n_tiles = 0, n_work = 0, n_xs = 0, n_s = 0, n_pad = 0;
   int32_t* err = nullptr;             // device error word
 };
 

@@ -445,7 +445,8 @@ void run_local(Handle& h, cudaStream_t s) {
   const bool spd = h.opt.spd != 0;
   // -- sizes and offsets
   dn.h_np.resize(N); dn.h_work_off.resize(N); dn.h_xs_off.resize(N); dn.h_s_off.resize(N);
-  dn.h_nt.resize(N); dn.h_tile_off.resize(N + 1); dn.h_part_off.resize(N + 1);
+  dn.h_nt.resize(N); dn.h_tile_off.resize(N + 1);
+  std::vector<int64_t> h_pad_off(N + 1);
   int64_t w = 0, xs = 0, ss = 0, tl = 0, pt = 0;
   std::vector<int4> desc;
   for (int i = 0; i < N; ++i) {
@@ -467,19 +468,39 @@ void run_local(Handle& h, cudaStream_t s) {
     for (int I = 0; I < nt; ++I)
       for (int J = 0; J < (spd ? I + 1 : nt); ++J) desc.push_back(make_int4(i, I, J, 0));
     tl = (int64_t)desc.size();
-    dn.h_part_off[i] = pt;
-    pt += (int64_t)nt * nt * TILE;
+    h_pad_off[i] = pt;
+    pt += (int64_t)nt * TILE;
   }
   dn.h_tile_off[N] = tl;
-  dn.h_part_off[N] = pt;
-  dn.n_work = w; dn.n_xs = xs; dn.n_s = ss; dn.n_tiles = tl; dn.n_part = pt;
+  h_pad_off[N] = pt;
+  dn.n_work = w; dn.n_xs = xs; dn.n_s = ss; dn.n_tiles = tl; dn.n_pad = pt;
+  // apply work items, longest first: row blocks (SPD: row I has I+1 tiles;
+  // general: nt) and column blocks (SPD: column J has nt-J tiles)
+  std::vector<std::pair<int, int2>> ri, ci;
+  for (int i = 0; i < N; ++i) {
+    const int nt = dn.h_nt[i];
+    for (int b = 0; b < nt; ++b) {
+      ri.push_back({spd ? b + 1 : nt, make_int2(i, b)});
+      if (spd) ci.push_back({nt - b, make_int2(i, b)});
+    }
+  }
+  auto longest_first = [](const std::pair<int, int2>& a, const std::pair<int, int2>& b) { return a.first > b.first; };
+  std::stable_sort(ri.begin(), ri.end(), longest_first);
+  std::stable_sort(ci.begin(), ci.end(), longest_first);
+  std::vector<int2> rv, cv;
+  for (auto& e : ri) rv.push_back(e.second);
+  for (auto& e : ci) cv.push_back(e.second);
+  dn.n_row_items = (int)rv.size();
+  dn.n_col_items = (int)cv.size();
   dn.np = mem.alloc<int32_t>(N);
   dn.nt = mem.alloc<int32_t>(N);
   dn.work_off = mem.alloc<int64_t>(N);
   dn.xs_off = mem.alloc<int64_t>(N);
   dn.s_off = mem.alloc<int64_t>(N);
   dn.tile_off = mem.alloc<int64_t>(N + 1);
-  dn.part_off = mem.alloc<int64_t>(N + 1);
+  dn.pad_off = mem.alloc<int64_t>(N + 1);
+  dn.row_items = mem.alloc<int2>(std::max(dn.n_row_items, 1));
+  dn.col_items = mem.alloc<int2>(std::max(dn.n_col_items, 1));
   dn.tile_desc = mem.alloc<int4>(tl);
   int32_t* d_n = mem.alloc<int32_t>(N);
   int32_t* d_m = mem.alloc<int32_t>(N);
@@ -490,7 +511,9 @@ void run_local(Handle& h, cudaStream_t s) {
   CK(cudaMemcpyAsync(dn.xs_off, dn.h_xs_off.data(), 8 * N, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(dn.s_off, dn.h_s_off.data(), 8 * N, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(dn.tile_off, dn.h_tile_off.data(), 8 * (N + 1), cudaMemcpyHostToDevice, s));
-  CK(cudaMemcpyAsync(dn.part_off, dn.h_part_off.data(), 8 * (N + 1), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(dn.pad_off, h_pad_off.data(), 8 * (N + 1), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(dn.row_items, rv.data(), sizeof(int2) * rv.size(), cudaMemcpyHostToDevice, s));
+  if (!cv.empty()) CK(cudaMemcpyAsync(dn.col_items, cv.data(), sizeof(int2) * cv.size(), cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(dn.tile_desc, desc.data(), sizeof(int4) * tl, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(d_n, h.h_n.data(), 4 * N, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(d_m, h.h_m.data(), 4 * N, cudaMemcpyHostToDevice, s));
@@ -501,9 +524,9 @@ void run_local(Handle& h, cudaStream_t s) {
   dn.dinv = mem.alloc<T>(std::max<int64_t>(ss, 1));
   dn.dinv_off = dn.s_off;
   dn.tiles = mem.alloc<T>(tl * TILE * TILE);
-  dn.partials = mem.alloc<T>(pt);
+  dn.xpad = mem.alloc<T>(pt);
+  dn.tpad = mem.alloc<T>(pt);
   dn.ypos = mem.alloc<double>(ov.sum_n);
-  dn.tpos = mem.alloc<double>(ov.sum_n);
   h.dev_n = d_n; h.dev_m = d_m; h.dev_p = d_p;
   // -- gather A_ii
   CK(cudaMemsetAsync(work, 0, sizeof(T) * w, s));
