@@ -24,26 +24,6 @@ namespace {
 
 constexpr int NT = 256;
 
-template <typename T>
-__device__ __forceinline__ void load4(const T* p, T (&v)[4]);
-template <>
-__device__ __forceinline__ void load4<float>(const float* p, float (&v)[4]) {
-  float4 q = __ldcs(reinterpret_cast<const float4*>(p));
-  v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
-}
-template <>
-__device__ __forceinline__ void load4<double>(const double* p, double (&v)[4]) {
-  double2 a = __ldcs(reinterpret_cast<const double2*>(p));
-  double2 b = __ldcs(reinterpret_cast<const double2*>(p) + 1);
-  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
-}
-
-template <typename T>
-__device__ __forceinline__ void load_tile(const T* __restrict__ tile, int rg, int cq, T (&v)[4][4]) {
-#pragma unroll
-  for (int a = 0; a < 4; ++a) load4<T>(tile + (rg + 16 * a) * TILE + 4 * cq, v[a]);
-}
-
 // x in the padded position space of each subdomain (nt_i * TILE entries from
 // pad_off[i], zero beyond n_i): xs = (T)(r * s) gathered through Omega_i.
 template <typename T>
@@ -67,110 +47,187 @@ __global__ void __launch_bounds__(NT) k_gather_x(const int32_t* __restrict__ ome
   }
 }
 
-// Row pass.  Item (i, I): out_I = sum_J T_IJ x_J over J <= I (SPD, lower
-// tiles) or all J (general).  Thread t owns rows (t/16) + 16a, a = 0..3, and
-// columns 4 (t%16) .. +3 of every tile; the next tile is loaded while the
-// current one is multiplied.  Output: the padded vector tout (SPD first
-// pass) or, per Omega position, ypos in FP64 (general).
-template <typename T, bool SPD>
-__global__ void __launch_bounds__(NT) k_row_pass(const T* __restrict__ tiles, const int64_t* __restrict__ tile_off,
-                                                 const int2* __restrict__ items, int nitems,
-                                                 const int32_t* __restrict__ sub_off, const int32_t* __restrict__ n_arr,
-                                                 const int32_t* __restrict__ nt_arr, const int64_t* __restrict__ pad_off,
-                                                 const T* __restrict__ xs, T* __restrict__ tout,
-                                                 double* __restrict__ ypos, const int32_t* __restrict__ done) {
-  COUNT_LAUNCH();
-  if (done != nullptr && *done) return;
-  const int tid = threadIdx.x, cq = tid & 15, rg = tid >> 4;
-  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
-    const int2 w = items[it];
-    const int i = w.x, I = w.y, nt = nt_arr[i];
-    const int cnt = SPD ? I + 1 : nt;
-    const T* base = tiles + (tile_off[i] + (SPD ? (int64_t)I * (I + 1) / 2 : (int64_t)I * nt)) * (TILE * TILE);
-    const T* x = xs + pad_off[i] + 4 * cq;
-    T acc[4] = {0, 0, 0, 0};
-    T v[4][4], vn[4][4];
-    load_tile<T>(base, rg, cq, v);
-    for (int J = 0; J < cnt; ++J) {
-      if (J + 1 < cnt) load_tile<T>(base + (int64_t)(J + 1) * (TILE * TILE), rg, cq, vn);
-      T xv[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) xv[q] = x[J * TILE + q];
-#pragma unroll
-      for (int a = 0; a < 4; ++a) acc[a] += v[a][0] * xv[0] + v[a][1] * xv[1] + v[a][2] * xv[2] + v[a][3] * xv[3];
-      if (J + 1 < cnt) {
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-          for (int q = 0; q < 4; ++q) v[a][q] = vn[a][q];
-      }
-    }
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      T s = acc[a];
-      s += __shfl_xor_sync(0xffffffffu, s, 8);
-      s += __shfl_xor_sync(0xffffffffu, s, 4);
-      s += __shfl_xor_sync(0xffffffffu, s, 2);
-      s += __shfl_xor_sync(0xffffffffu, s, 1);
-      if (cq == 0) {
-        const int row = I * TILE + rg + 16 * a;
-        if (SPD) tout[pad_off[i] + row] = s;
-        else if (row < n_arr[i]) ypos[sub_off[i] + row] = (double)s;
-      }
-    }
-  }
+// ---------------------------------------------------------------------------
+// Tile staging through the bulk-copy (TMA) engine: one thread issues
+// cp.async.bulk copies of whole 16 KB (FP32) tiles into a ring of S shared
+// memory stages, each completing on its own mbarrier; all threads wait on the
+// barrier's phase, multiply from shared memory, and the slot is refilled
+// STAGES tiles ahead.  Every wait is bounded (about a second of clock); a
+// wait that gives up sets DERR_TIMEOUT and the block leaves after a bounded
+// wait for its copies in flight.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity))
+    if (clock64() - t0 > 2000000000LL) return false;
+  return true;
 }
 
-// Column pass (SPD).  Item (i, J): y_J = sum_{I >= J} T_IJ^T t_I, written
-// per Omega position to ypos in FP64.
 template <typename T>
-__global__ void __launch_bounds__(NT) k_col_pass(const T* __restrict__ tiles, const int64_t* __restrict__ tile_off,
-                                                 const int2* __restrict__ items, int nitems,
-                                                 const int32_t* __restrict__ sub_off, const int32_t* __restrict__ n_arr,
-                                                 const int32_t* __restrict__ nt_arr, const int64_t* __restrict__ pad_off,
-                                                 const T* __restrict__ tin, double* __restrict__ ypos,
-                                                 const int32_t* __restrict__ done) {
+struct Stages {
+  static constexpr int S = sizeof(T) == 4 ? 3 : 2;                  // ring depth
+  static constexpr uint32_t BYTES = TILE * TILE * sizeof(T);        // one tile
+  static constexpr size_t SMEM = (size_t)S * BYTES;
+};
+
+// One pass over the local tiles.  Row pass (COL = false), item (i, I):
+// out_I = sum_J T_IJ x_J over J <= I (SPD, lower tiles) or all J (general);
+// thread t owns rows (t/16) + 16a, a = 0..3, and columns 4 (t%16) .. +3;
+// output: the padded vector tout (SPD first pass) or, per Omega position,
+// ypos in FP64 (general).  Column pass (COL = true, SPD), item (i, J):
+// y_J = sum_{I >= J} T_IJ^T t_I, written per Omega position to ypos.
+template <typename T, bool SPD, bool COL>
+__global__ void __launch_bounds__(NT) k_tile_pass(const T* __restrict__ tiles, const int64_t* __restrict__ tile_off,
+                                                  const int2* __restrict__ items, int nitems,
+                                                  const int32_t* __restrict__ sub_off, const int32_t* __restrict__ n_arr,
+                                                  const int32_t* __restrict__ nt_arr,
+                                                  const int64_t* __restrict__ pad_off, const T* __restrict__ vin,
+                                                  T* __restrict__ tout, double* __restrict__ ypos,
+                                                  int32_t* __restrict__ err, const int32_t* __restrict__ done) {
   COUNT_LAUNCH();
   if (done != nullptr && *done) return;
+  using St = Stages<T>;
+  constexpr int S = St::S;
+  extern __shared__ __align__(128) unsigned char smraw[];
+  T* stage = reinterpret_cast<T*>(smraw);
+  __shared__ __align__(8) uint64_t full[S];
   __shared__ T colpart[NT / 32][TILE];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, cq = tid & 15, rg = tid >> 4;
-  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+  // tiles of item `it` and the address of its k-th tile
+  auto count = [&](int it) -> int {
     const int2 w = items[it];
-    const int i = w.x, J = w.y, nt = nt_arr[i];
-    const int64_t t0 = tile_off[i];
-    const T* t = tin + pad_off[i];
-    T c[4] = {0, 0, 0, 0};
-    T v[4][4], vn[4][4];
-    load_tile<T>(tiles + (t0 + (int64_t)J * (J + 1) / 2 + J) * (TILE * TILE), rg, cq, v);
-    for (int I = J; I < nt; ++I) {
-      if (I + 1 < nt) load_tile<T>(tiles + (t0 + (int64_t)(I + 1) * (I + 2) / 2 + J) * (TILE * TILE), rg, cq, vn);
-      T tv[4];
+    const int nt = nt_arr[w.x];
+    return COL ? nt - w.y : (SPD ? w.y + 1 : nt);
+  };
+  auto src = [&](int it, int k) -> const T* {
+    const int2 w = items[it];
+    const int nt = nt_arr[w.x];
+    int64_t t;
+    if (COL) { const int64_t I = w.y + k; t = I * (I + 1) / 2 + w.y; }
+    else t = SPD ? (int64_t)w.y * (w.y + 1) / 2 + k : (int64_t)w.y * nt + k;
+    return tiles + (tile_off[w.x] + t) * (TILE * TILE);
+  };
+  if (tid == 0) {
+    for (int q = 0; q < S; ++q) mbar_init(&full[q], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  // producer cursor (thread 0): the same tile sequence the block consumes
+  int p_it = blockIdx.x, p_k = 0, p_n = p_it < nitems ? count(p_it) : 0;
+  uint32_t issued = 0;
+  auto issue = [&](int slot) {
+    if (p_it >= nitems) return;
+    mbar_expect_tx(&full[slot], St::BYTES);
+    bulk_g2s(stage + (size_t)slot * TILE * TILE, src(p_it, p_k), St::BYTES, &full[slot]);
+    ++issued;
+    if (++p_k == p_n) {
+      p_it += gridDim.x;
+      p_k = 0;
+      p_n = p_it < nitems ? count(p_it) : 0;
+    }
+  };
+  if (tid == 0)
+    for (int q = 0; q < S; ++q) issue(q);
+  uint32_t t = 0;  // tiles consumed
+  bool ok = true;
+  for (int it = blockIdx.x; it < nitems && ok; it += gridDim.x) {
+    const int2 w = items[it];
+    const int i = w.x, B = w.y, nt = nt_arr[i];
+    const int cnt = COL ? nt - B : (SPD ? B + 1 : nt);
+    const T* vb = vin + pad_off[i];
+    T acc[4] = {0, 0, 0, 0};
+    for (int k = 0; k < cnt; ++k, ++t) {
+      const int slot = (int)(t % S);
+      const bool got = mbar_wait_bounded(&full[slot], (t / S) & 1);
+      if (!__syncthreads_and(got)) { ok = false; break; }
+      const T* tile = stage + (size_t)slot * TILE * TILE;
+      T v[4][4];
 #pragma unroll
-      for (int a = 0; a < 4; ++a) tv[a] = t[I * TILE + rg + 16 * a];
+      for (int a = 0; a < 4; ++a) {
+        const T* rp = tile + (rg + 16 * a) * TILE + 4 * cq;
 #pragma unroll
-      for (int q = 0; q < 4; ++q) c[q] += v[0][q] * tv[0] + v[1][q] * tv[1] + v[2][q] * tv[2] + v[3][q] * tv[3];
-      if (I + 1 < nt) {
+        for (int q = 0; q < 4; ++q) v[a][q] = rp[q];
+      }
+      if (!COL) {
+        T xv[4];
 #pragma unroll
-        for (int a = 0; a < 4; ++a)
+        for (int q = 0; q < 4; ++q) xv[q] = vb[k * TILE + 4 * cq + q];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) v[a][q] = vn[a][q];
+        for (int a = 0; a < 4; ++a) acc[a] += v[a][0] * xv[0] + v[a][1] * xv[1] + v[a][2] * xv[2] + v[a][3] * xv[3];
+      } else {
+        T tv[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) tv[a] = vb[(B + k) * TILE + rg + 16 * a];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[q] += v[0][q] * tv[0] + v[1][q] * tv[1] + v[2][q] * tv[2] + v[3][q] * tv[3];
+      }
+      __syncthreads();  // every thread is done with this slot
+      if (tid == 0) {
+        fence_proxy_async();
+        issue(slot);
       }
     }
+    if (!ok) break;
+    if (!COL) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) c[q] += __shfl_xor_sync(0xffffffffu, c[q], 16);
-    __syncthreads();
-    if (lane < 16) {
+      for (int a = 0; a < 4; ++a) {
+        T sm = acc[a];
+        sm += __shfl_xor_sync(0xffffffffu, sm, 8);
+        sm += __shfl_xor_sync(0xffffffffu, sm, 4);
+        sm += __shfl_xor_sync(0xffffffffu, sm, 2);
+        sm += __shfl_xor_sync(0xffffffffu, sm, 1);
+        if (cq == 0) {
+          const int row = B * TILE + rg + 16 * a;
+          if (SPD) tout[pad_off[i] + row] = sm;
+          else if (row < n_arr[i]) ypos[sub_off[i] + row] = (double)sm;
+        }
+      }
+    } else {
 #pragma unroll
-      for (int q = 0; q < 4; ++q) colpart[wid][4 * cq + q] = c[q];
+      for (int q = 0; q < 4; ++q) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], 16);
+      if (lane < 16) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) colpart[wid][4 * cq + q] = acc[q];
+      }
+      __syncthreads();
+      if (tid < TILE) {
+        T sm = 0;
+#pragma unroll
+        for (int w2 = 0; w2 < NT / 32; ++w2) sm += colpart[w2][tid];
+        const int col = B * TILE + tid;
+        if (col < n_arr[i]) ypos[sub_off[i] + col] = (double)sm;
+      }
+      __syncthreads();
     }
-    __syncthreads();
-    if (tid < TILE) {
-      T s = 0;
-#pragma unroll
-      for (int w2 = 0; w2 < NT / 32; ++w2) s += colpart[w2][tid];
-      const int col = J * TILE + tid;
-      if (col < n_arr[i]) ypos[sub_off[i] + col] = (double)s;
-    }
+  }
+  if (!ok && tid == 0) {
+    atomicOr(err, (int32_t)DERR_TIMEOUT);
+    // copies still in flight land before the block's shared memory goes away
+    for (uint32_t u = t; u < issued; ++u) mbar_wait_bounded(&full[u % S], (u / S) & 1);
   }
 }
 
@@ -263,24 +320,41 @@ void gather_x(Handle& h, const double* r, cudaStream_t s, const int32_t* done) {
                                    done);
 }
 
+template <typename T, bool SPD, bool COL>
+void launch_pass(Handle& h, int nitems, const int2* items, const T* vin, T* tout, cudaStream_t s,
+                 const int32_t* done) {
+  Dense& dn = h.dn;
+  const unsigned g = tile_grid<T>(h, nitems);
+  k_tile_pass<T, SPD, COL><<<g, NT, Stages<T>::SMEM, s>>>((const T*)dn.tiles, dn.tile_off, items, nitems,
+                                                           h.ov.sub_off, h.dev_n, dn.nt, dn.pad_off, vin, tout,
+                                                           dn.ypos, dn.err, done);
+}
+
 template <typename T>
 void row_pass(Handle& h, cudaStream_t s, const int32_t* done) {
   Dense& dn = h.dn;
-  const unsigned g = tile_grid<T>(h, dn.n_row_items);
   if (h.opt.spd)
-    k_row_pass<T, true><<<g, NT, 0, s>>>((const T*)dn.tiles, dn.tile_off, dn.row_items, dn.n_row_items, h.ov.sub_off,
-                                         h.dev_n, dn.nt, dn.pad_off, (const T*)dn.xpad, (T*)dn.tpad, dn.ypos, done);
+    launch_pass<T, true, false>(h, dn.n_row_items, dn.row_items, (const T*)dn.xpad, (T*)dn.tpad, s, done);
   else
-    k_row_pass<T, false><<<g, NT, 0, s>>>((const T*)dn.tiles, dn.tile_off, dn.row_items, dn.n_row_items, h.ov.sub_off,
-                                          h.dev_n, dn.nt, dn.pad_off, (const T*)dn.xpad, (T*)dn.tpad, dn.ypos, done);
+    launch_pass<T, false, false>(h, dn.n_row_items, dn.row_items, (const T*)dn.xpad, (T*)dn.tpad, s, done);
 }
 
 template <typename T>
 void col_pass(Handle& h, cudaStream_t s, const int32_t* done) {
   Dense& dn = h.dn;
-  const unsigned g = tile_grid<T>(h, dn.n_col_items);
-  k_col_pass<T><<<g, NT, 0, s>>>((const T*)dn.tiles, dn.tile_off, dn.col_items, dn.n_col_items, h.ov.sub_off, h.dev_n,
-                                 dn.nt, dn.pad_off, (const T*)dn.tpad, dn.ypos, done);
+  launch_pass<T, true, true>(h, dn.n_col_items, dn.col_items, (const T*)dn.tpad, nullptr, s, done);
+}
+
+// dynamic shared memory of the tile passes (once per process and type)
+template <typename T>
+void prepare_tile_passes() {
+  static bool done = false;
+  if (done) return;
+  const int sm = (int)Stages<T>::SMEM;
+  CK(cudaFuncSetAttribute(k_tile_pass<T, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  CK(cudaFuncSetAttribute(k_tile_pass<T, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  CK(cudaFuncSetAttribute(k_tile_pass<T, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  done = true;
 }
 
 template <typename T>
@@ -389,20 +463,25 @@ void tune_impl(Handle& h, cudaStream_t s) {
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
-  const int cand[4] = {4, 6, 8, 12};
-  int best = h.tile_ctas;
-  float best_ms = 3.0e38f;
-  for (int c : cand) {
-    h.tile_ctas = c;
-    apply_impl<T>(h, rz, rz + h.n, s, nullptr);  // warm
-    CK(cudaEventRecord(e0, s));
-    for (int rep = 0; rep < 3; ++rep) apply_impl<T>(h, rz, rz + h.n, s, nullptr);
-    CK(cudaEventRecord(e1, s));
-    CK(cudaEventSynchronize(e1));
-    float ms = 0;
-    CK(cudaEventElapsedTime(&ms, e0, e1));
-    if (ms < best_ms) { best_ms = ms; best = c; }
+  const int cand[5] = {2, 3, 4, 6, 8};
+  float best_ms[5] = {3.0e38f, 3.0e38f, 3.0e38f, 3.0e38f, 3.0e38f};
+  for (int round = 0; round < 2; ++round) {
+    for (int q = 0; q < 5; ++q) {
+      h.tile_ctas = cand[q];
+      apply_impl<T>(h, rz, rz + h.n, s, nullptr);  // warm
+      CK(cudaEventRecord(e0, s));
+      for (int rep = 0; rep < 4; ++rep) apply_impl<T>(h, rz, rz + h.n, s, nullptr);
+      CK(cudaEventRecord(e1, s));
+      CK(cudaEventSynchronize(e1));
+      float ms = 0;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      best_ms[q] = std::min(best_ms[q], ms);
+    }
   }
+  int best = cand[0];
+  float bm = best_ms[0];
+  for (int q = 1; q < 5; ++q)
+    if (best_ms[q] < bm) { bm = best_ms[q]; best = cand[q]; }
   h.tile_ctas = best;
   CK(cudaEventDestroy(e0));
   CK(cudaEventDestroy(e1));
@@ -413,7 +492,13 @@ void tune_impl(Handle& h, cudaStream_t s) {
 }  // namespace
 
 void tune_apply(Handle& h, cudaStream_t s) {
-  if (h.fp32) tune_impl<float>(h, s); else tune_impl<double>(h, s);
+  if (h.fp32) {
+    prepare_tile_passes<float>();
+    tune_impl<float>(h, s);
+  } else {
+    prepare_tile_passes<double>();
+    tune_impl<double>(h, s);
+  }
 }
 
 void apply_preconditioner(Handle& h, const double* r, double* z, cudaStream_t s, const int32_t* done) {

@@ -89,6 +89,7 @@ void check_device_error(Handle& h, cudaStream_t s, const char* stage) {
   if (e & DERR_ZERO_PIVOT) fail(ASM_ERR_ZERO_PIVOT, st + ": zero local pivot");
   if (e & DERR_COARSE) fail(ASM_ERR_COARSE_SINGULAR, st + ": coarse matrix E is not SPD / singular");
   if (e & DERR_CAPACITY) fail(ASM_ERR_UNSUPPORTED, st + ": capacity exceeded");
+  if (e & DERR_TIMEOUT) fail(ASM_ERR_TIMEOUT, st + ": a bounded device wait gave up");
 }
 }  // namespace asmgpu
 
@@ -247,6 +248,7 @@ asm_status asm_apply(asm_handle* H, const double* r, double* z, void* stream) {
   return guarded([&] {
     apply_preconditioner(H->h, r, z, static_cast<cudaStream_t>(stream));
     CK_LAUNCH("apply");
+    check_device_error(H->h, static_cast<cudaStream_t>(stream), "apply");
   });
 }
 
@@ -281,6 +283,7 @@ asm_status asm_solve(asm_handle* H, const double* b, double* x, const asm_solve_
     int method = so.method ? so.method : (h.opt.spd ? 1 : 2);
     if (method == 1) solve_pcg(h, db, dx, so, *info, s);
     else solve_fgmres(h, db, dx, so, *info, s);
+    check_device_error(h, s, "solve");
     if (h.host_io) {
       CK(cudaMemcpyAsync(x, dx, sizeof(double) * h.n, cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));

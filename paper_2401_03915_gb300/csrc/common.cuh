@@ -36,6 +36,7 @@ enum DevErr : int32_t {
   DERR_NONFINITE = 4,
   DERR_CAPACITY = 8,
   DERR_COARSE = 16,
+  DERR_TIMEOUT = 32,  // a bounded device wait gave up
 };
 
 // ---------------------------------------------------------------------------
