@@ -162,6 +162,10 @@ __global__ void __launch_bounds__(NT) k_tile_pass(const T* __restrict__ tiles, c
     T acc[4] = {0, 0, 0, 0};
     for (int k = 0; k < cnt; ++k, ++t) {
       const int slot = (int)(t % S);
+      // the vector entries this tile needs are loaded while its copy lands
+      T xv[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) xv[q] = COL ? vb[(B + k) * TILE + rg + 16 * q] : vb[k * TILE + 4 * cq + q];
       const bool got = mbar_wait_bounded(&full[slot], (t / S) & 1);
       if (!__syncthreads_and(got)) { ok = false; break; }
       const T* tile = stage + (size_t)slot * TILE * TILE;
@@ -173,17 +177,11 @@ __global__ void __launch_bounds__(NT) k_tile_pass(const T* __restrict__ tiles, c
         for (int q = 0; q < 4; ++q) v[a][q] = rp[q];
       }
       if (!COL) {
-        T xv[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) xv[q] = vb[k * TILE + 4 * cq + q];
 #pragma unroll
         for (int a = 0; a < 4; ++a) acc[a] += v[a][0] * xv[0] + v[a][1] * xv[1] + v[a][2] * xv[2] + v[a][3] * xv[3];
       } else {
-        T tv[4];
 #pragma unroll
-        for (int a = 0; a < 4; ++a) tv[a] = vb[(B + k) * TILE + rg + 16 * a];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) acc[q] += v[0][q] * tv[0] + v[1][q] * tv[1] + v[2][q] * tv[2] + v[3][q] * tv[3];
+        for (int q = 0; q < 4; ++q) acc[q] += v[0][q] * xv[0] + v[1][q] * xv[1] + v[2][q] * xv[2] + v[3][q] * xv[3];
       }
       __syncthreads();  // every thread is done with this slot
       if (tid == 0) {

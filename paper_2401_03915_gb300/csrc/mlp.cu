@@ -350,7 +350,7 @@ void Mlp::ensure(int rows) {
   dY16 = (half*)al(sizeof(half) * (size_t)cap * Kp);
   dH2 = (half*)al(sizeof(half) * (size_t)cap * H);
   dH1 = (half*)al(sizeof(half) * (size_t)cap * H);
-  const int nz = std::max(1, std::min(64, (int)ceil_div(cap, 2048)));
+  const int nz = 64;  // split-K partials of the weight gradients (see weight_grad)
   const int64_t wmax = std::max<int64_t>({(int64_t)H * H, (int64_t)Fp * H, (int64_t)H * Kp});
   part = (float*)al(sizeof(float) * (size_t)nz * (size_t)wmax);
 }
@@ -372,7 +372,8 @@ void Mlp::forward(const float* X, int rows, cudaStream_t s) {
 // split over rows, partial sums added in a fixed order
 void Mlp::weight_grad(const half* Aact, int Kin, const half* dO, int Nout, int rows, float scale, float* out,
                       cudaStream_t s) {
-  const int nz = std::max(1, std::min(64, (int)ceil_div(rows, 2048)));
+  // enough row chunks to fill the GPU: the output is only Kin x Nout
+  const int nz = std::max(1, std::min(64, (int)ceil_div(rows, 256)));
   const int chunk = (int)round_up(ceil_div(rows, nz), TK);
   k_hgemm<true, false><<<ggrid(Kin, Nout, nz), GT, 0, s>>>(Kin, Nout, rows, Aact, Kin, dO, Nout, nullptr, nullptr,
                                                            0, 0, part, Nout, nullptr, 0, chunk);
