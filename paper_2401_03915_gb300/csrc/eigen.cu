@@ -19,9 +19,11 @@
 // scaling of the local sweep, so the scaling is undone inside the products
 // with X_p.
 //
-// One sweep: Rayleigh-Ritz (cyclic Jacobi on the projected s x s matrix,
-// Golub & Van Loan Alg. 8.5.3), relative eigen-residual test, locking of the
-// converged leading Ritz pairs, then a degree-d Chebyshev polynomial in OP
+// One sweep: Rayleigh-Ritz on the whole block (cyclic Jacobi on the projected
+// s x s matrix in the working precision, Golub & Van Loan Alg. 8.5.3),
+// relative eigen-residual test, soft locking of the converged leading Ritz
+// pairs (they leave the filter, not the Rayleigh-Ritz step), then a degree-d
+// Chebyshev polynomial in OP
 // applied to the remaining columns (scaled three-term recurrence of Zhou &
 // Saad, 2007) that damps the spectrum below the smallest Ritz value, with the
 // locked vectors projected out after every application of OP and the degree
