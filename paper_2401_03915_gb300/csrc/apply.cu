@@ -272,9 +272,11 @@ __global__ void __launch_bounds__(NT) k_apply_pull(int n, const int32_t* __restr
                                                    const int64_t* __restrict__ z_off, const int32_t* __restrict__ count,
                                                    const int32_t* __restrict__ col_off, int nev,
                                                    const double* __restrict__ yc, const double* __restrict__ ds,
-                                                   double* __restrict__ z, const int32_t* __restrict__ done) {
+                                                   double* __restrict__ z, const int32_t* __restrict__ done,
+                                                   ApplyDot dot) {
   COUNT_LAUNCH();
   if (done != nullptr && *done) return;
+  double rz = 0;
   for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
     double acc = 0;
     for (int t = occ_ptr[v]; t < occ_ptr[v + 1]; ++t) acc += ypos[occ_pos[t]];
@@ -298,6 +300,14 @@ __global__ void __launch_bounds__(NT) k_apply_pull(int n, const int32_t* __restr
       }
     }
     z[v] = acc;
+    if (dot.r != nullptr) rz += dot.r[v] * acc;
+  }
+  if (dot.r != nullptr) {
+    // PCG: rz_new = r.z, beta = rz_new / rz_old
+    grid_sum_last(rz, dot.gs, [&](double tot) {
+      *dot.beta = tot / *dot.rz;
+      *dot.rz = tot;
+    });
   }
 }
 
@@ -375,19 +385,22 @@ const double* apply_coarse(Handle& h, const double* r, cudaStream_t s, const int
 }
 
 template <typename T>
-void apply_pull(Handle& h, const double* yc, double* z, cudaStream_t s, const int32_t* done) {
+void apply_pull(Handle& h, const double* yc, double* z, cudaStream_t s, const int32_t* done,
+                const ApplyDot* dot = nullptr) {
   Dense& dn = h.dn;
   Coarse& co = h.co;
   unsigned gp = (unsigned)std::min<int64_t>(ceil_div(h.n, NT), 152 * 16);
   k_apply_pull<<<gp, NT, 0, s>>>(h.n, h.ov.occ_ptr, h.ov.occ_pos, dn.ypos, h.part, h.ov.own_pos, h.ov.sub_off,
-                                 co.Z, co.z_off, co.count, co.col_off, h.nev, yc, h.dscale, z, done);
+                                 co.Z, co.z_off, co.count, co.col_off, h.nev, yc, h.dscale, z, done,
+                                 dot ? *dot : ApplyDot());
 }
 
 // The coarse part (Z^T r, the level-by-level coarse solve) is independent of
 // the local part until the pull: it runs on the handle's side stream, forked
 // from and joined back into `s` with events (also inside a graph capture).
 template <typename T>
-void apply_impl(Handle& h, const double* r, double* z, cudaStream_t s, const int32_t* done) {
+void apply_impl(Handle& h, const double* r, double* z, cudaStream_t s, const int32_t* done,
+                const ApplyDot* dot = nullptr) {
   const double* yc = nullptr;
   const bool fork = h.co.n_C > 0 && h.side != nullptr;
   if (fork) {
@@ -399,7 +412,7 @@ void apply_impl(Handle& h, const double* r, double* z, cudaStream_t s, const int
   apply_local<T>(h, r, s, done);
   if (fork) CK(cudaStreamWaitEvent(s, h.ev_join, 0));
   else yc = apply_coarse(h, r, s, done);
-  apply_pull<T>(h, yc, z, s, done);
+  apply_pull<T>(h, yc, z, s, done, dot);
 }
 
 template <typename T>
@@ -499,8 +512,9 @@ void tune_apply(Handle& h, cudaStream_t s) {
   }
 }
 
-void apply_preconditioner(Handle& h, const double* r, double* z, cudaStream_t s, const int32_t* done) {
-  if (h.fp32) apply_impl<float>(h, r, z, s, done); else apply_impl<double>(h, r, z, s, done);
+void apply_preconditioner(Handle& h, const double* r, double* z, cudaStream_t s, const int32_t* done,
+                          const ApplyDot* dot) {
+  if (h.fp32) apply_impl<float>(h, r, z, s, done, dot); else apply_impl<double>(h, r, z, s, done, dot);
 }
 
 void time_apply(Handle& h, const double* r, double* z, int iters, cudaStream_t s, double* ms) {

@@ -68,6 +68,15 @@ struct DevMem {
 __host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 __host__ __device__ inline int64_t round_up(int64_t a, int64_t b) { return ceil_div(a, b) * b; }
 
+// Grid-wide deterministic reduction without a second launch: every block
+// stores its partial, the last block to arrive (atomic ticket) adds the
+// partials in block order and runs fin(total) on thread 0, then re-arms the
+// ticket.  No block waits for another.
+struct GridSum {
+  double* part;       // one slot per block of the launch
+  unsigned* ticket;   // zero between launches
+};
+
 constexpr int TILE = 64;  // tile edge of the local dense matrices and of the apply
 
 // ---------------------------------------------------------------------------
@@ -98,6 +107,32 @@ __device__ T block_sum(T v, T* sh) {
   t = sh[0];
   __syncthreads();
   return t;
+}
+
+// The block partial v goes to gs.part[blockIdx.x]; the last block of the
+// launch adds all partials in block order and calls fin(total) on thread 0.
+// All threads of every block must call it (it contains block barriers).
+template <typename F>
+__device__ void grid_sum_last(double v, GridSum gs, F&& fin) {
+  __shared__ double red_gs[32];
+  __shared__ int last_gs;
+  v = block_sum(v, red_gs);
+  if (threadIdx.x == 0) {
+    gs.part[blockIdx.x] = v;
+    __threadfence();
+    last_gs = atomicAdd(gs.ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last_gs) {
+    __threadfence();
+    double t = 0;
+    for (int k = threadIdx.x; k < (int)gridDim.x; k += blockDim.x) t += __ldcg(gs.part + k);
+    t = block_sum(t, red_gs);
+    if (threadIdx.x == 0) {
+      fin(t);
+      *gs.ticket = 0;
+    }
+  }
 }
 
 // Binary search for `key` in sorted a[lo, hi); returns index or -1.

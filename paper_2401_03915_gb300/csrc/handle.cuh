@@ -93,6 +93,8 @@ struct Krylov {
   double* ZB = nullptr;     // FGMRES preconditioned basis restart x n
   double* H = nullptr;      // Hessenberg and rotations
   double* mpart = nullptr;  // multi-dot partial sums
+  double* gpart = nullptr;  // PCG: partials of the fused reductions (3 x RBLK)
+  unsigned* ticket = nullptr;  // PCG: tickets of the fused reductions (3)
   int32_t restart = 0;
   double* bx = nullptr;     // device copies of b, x for host-pointer solves
   double* hpin = nullptr;   // pinned host staging
@@ -135,8 +137,16 @@ void build_overlap(Handle& h, cudaStream_t s);                 // overlap.cu
 void build_local(Handle& h, cudaStream_t s);                   // local.cu: gather + sweep + pack
 void build_eigen(Handle& h, cudaStream_t s);                   // eigen.cu
 void build_coarse(Handle& h, cudaStream_t s);                  // coarse.cu: E assembly + factor
+// Optional dot product r.z fused into the last kernel of the apply (PCG):
+// fin receives r.z through scal/flag (see krylov.cu).
+struct ApplyDot {
+  const double* r = nullptr;
+  GridSum gs{};
+  double* rz = nullptr;    // in: r.z of the previous iteration; out: the new one
+  double* beta = nullptr;  // out: new r.z / previous r.z
+};
 void apply_preconditioner(Handle& h, const double* r, double* z, cudaStream_t s,
-                          const int32_t* done = nullptr);                         // apply.cu
+                          const int32_t* done = nullptr, const ApplyDot* dot = nullptr);   // apply.cu
 void time_apply(Handle& h, const double* r, double* z, int iters, cudaStream_t s, double* ms);
 void tune_apply(Handle& h, cudaStream_t s);                                       // apply.cu
 void spmv(Handle& h, const double* x, double* y, cudaStream_t s);                 // krylov.cu

@@ -16,6 +16,7 @@ namespace {
 
 constexpr int NT = 256;
 constexpr int NBLK = 608;  // fixed reduction grid: 4 blocks per SM on 152 SMs
+constexpr int RBLK = 152 * 16;  // most blocks of a fused-reduction launch
 
 enum Scal { S_RZ = 0, S_PQ, S_ALPHA, S_BETA, S_RR, S_BNORM, S_RTOL, S_RELRES, S_TMP, S_NSCAL = 16 };
 enum Flag { F_DONE = 0, F_IT, F_MAXIT, F_NFLAG = 4 };
@@ -71,69 +72,75 @@ __device__ double sum_partials(const double* part, int nb) {
   return block_sum(s, red);
 }
 
-// x += alpha p; r -= alpha q; partial ||r||^2
-__global__ void __launch_bounds__(NT) k_pcg_update(int n, double* __restrict__ x, double* __restrict__ r,
-                                                   const double* __restrict__ p, const double* __restrict__ q,
-                                                   const double* __restrict__ scal, double* __restrict__ part,
-                                                   const int32_t* __restrict__ done) {
+// ---------------------------------------------------------------------------
+// Fused PCG iteration: three launches plus the apply, no reduction kernels.
+//   (1) q = A p, alpha = rz / p.q
+//   (2) x += alpha p, r -= alpha q, ||r|| and the stopping test
+//   (3) z = M r; r.z and beta are finished by the apply's last kernel
+//   (4) p = z + beta p
+// Each dot product is finished by the last block of its launch (GridSum).
+// ---------------------------------------------------------------------------
+template <int VW>
+__global__ void __launch_bounds__(NT) k_pcg_spmv(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                                 const double* __restrict__ val, const double* __restrict__ p,
+                                                 double* __restrict__ q, double* __restrict__ scal,
+                                                 int32_t* __restrict__ flag, GridSum gs) {
   COUNT_LAUNCH();
-  if (done[F_DONE]) return;
-  __shared__ double red[NT / 32];
+  if (flag[F_DONE]) return;
+  const int lane = threadIdx.x % VW;
+  const int rows_per_block = NT / VW;
+  double dsum = 0;
+  for (int base = blockIdx.x * rows_per_block; base < n; base += gridDim.x * rows_per_block) {
+    const int r = base + threadIdx.x / VW;
+    double acc = 0;
+    if (r < n) {
+      const int b = rp[r], e = rp[r + 1];
+      for (int k = b + lane; k < e; k += VW) acc += val[k] * p[ci[k]];
+    }
+#pragma unroll
+    for (int o = VW / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (r < n && lane == 0) {
+      q[r] = acc;
+      dsum += acc * p[r];
+    }
+  }
+  grid_sum_last(dsum, gs, [&](double pq) {
+    scal[S_PQ] = pq;
+    scal[S_ALPHA] = scal[S_RZ] / pq;
+    if (!(pq > 0) || !isfinite(pq)) { scal[S_ALPHA] = 0; flag[F_DONE] = 2; }
+  });
+}
+
+// p = z + beta p
+__global__ void __launch_bounds__(NT) k_pcg_p(int n, double* __restrict__ p, const double* __restrict__ z,
+                                              const double* __restrict__ scal, const int32_t* __restrict__ flag) {
+  COUNT_LAUNCH();
+  if (flag[F_DONE]) return;
+  const double beta = scal[S_BETA];
+  for (int i = blockIdx.x * NT + threadIdx.x; i < n; i += gridDim.x * NT) p[i] = z[i] + beta * p[i];
+}
+
+__global__ void __launch_bounds__(NT) k_pcg_xr(int n, double* __restrict__ x, double* __restrict__ r,
+                                               const double* __restrict__ p, const double* __restrict__ q,
+                                               double* __restrict__ scal, int32_t* __restrict__ flag, GridSum gs) {
+  COUNT_LAUNCH();
+  if (flag[F_DONE]) return;
   const double alpha = scal[S_ALPHA];
   double s = 0;
   for (int i = blockIdx.x * NT + threadIdx.x; i < n; i += gridDim.x * NT) {
     x[i] += alpha * p[i];
-    double ri = r[i] - alpha * q[i];
+    const double ri = r[i] - alpha * q[i];
     r[i] = ri;
     s += ri * ri;
   }
-  s = block_sum(s, red);
-  if (threadIdx.x == 0) part[blockIdx.x] = s;
-}
-
-__global__ void __launch_bounds__(NT) k_fin_alpha(const double* part, int nb, double* scal, int32_t* flag) {
-  COUNT_LAUNCH();
-  if (flag[F_DONE]) return;
-  double pq = sum_partials(part, nb);
-  if (threadIdx.x == 0) {
-    scal[S_PQ] = pq;
-    scal[S_ALPHA] = scal[S_RZ] / pq;
-    if (!(pq > 0) || !isfinite(pq)) { scal[S_ALPHA] = 0; flag[F_DONE] = 2; }
-  }
-}
-
-__global__ void __launch_bounds__(NT) k_fin_res(const double* part, int nb, double* scal, int32_t* flag,
-                                                double* hist, int hist_len) {
-  COUNT_LAUNCH();
-  if (flag[F_DONE]) return;
-  double rr = sum_partials(part, nb);
-  if (threadIdx.x == 0) {
-    int it = ++flag[F_IT];
-    double rel = sqrt(rr) / scal[S_BNORM];
+  grid_sum_last(s, gs, [&](double rr) {
+    const int it = ++flag[F_IT];
+    const double rel = sqrt(rr) / scal[S_BNORM];
     scal[S_RR] = rr;
     scal[S_RELRES] = rel;
-    if (hist != nullptr && it < hist_len) hist[it] = rel;
     if (rel <= scal[S_RTOL]) flag[F_DONE] = 1;
     else if (it >= flag[F_MAXIT] || !isfinite(rel)) flag[F_DONE] = 3;
-  }
-}
-
-__global__ void __launch_bounds__(NT) k_fin_beta(const double* part, int nb, double* scal, int32_t* flag) {
-  COUNT_LAUNCH();
-  if (flag[F_DONE]) return;
-  double rz = sum_partials(part, nb);
-  if (threadIdx.x == 0) {
-    scal[S_BETA] = rz / scal[S_RZ];
-    scal[S_RZ] = rz;
-  }
-}
-
-__global__ void __launch_bounds__(NT) k_update_p(int n, double* __restrict__ p, const double* __restrict__ z,
-                                                 const double* __restrict__ scal, const int32_t* __restrict__ done) {
-  COUNT_LAUNCH();
-  if (done[F_DONE]) return;
-  const double beta = scal[S_BETA];
-  for (int i = blockIdx.x * NT + threadIdx.x; i < n; i += gridDim.x * NT) p[i] = z[i] + beta * p[i];
+  });
 }
 
 // generic: out = a + alpha * b  (alpha from scal[ia] times sgn)
@@ -186,7 +193,7 @@ void spmv_any(Handle& h, const double* x, double* y, double* part, const int32_t
   else spmv_launch<32>(h, x, y, part, done, dot, s);
 }
 
-void ensure_krylov(Handle& h) {
+void ensure_krylov(Handle& h, cudaStream_t s) {
   Krylov& kr = h.kr;
   if (kr.r) return;
   DevMem& mem = h.mem;
@@ -197,6 +204,9 @@ void ensure_krylov(Handle& h) {
   kr.q = mem.alloc<double>(n);
   kr.w = mem.alloc<double>(n);
   kr.part = mem.alloc<double>(NBLK);
+  kr.gpart = mem.alloc<double>(3 * RBLK);
+  kr.ticket = mem.alloc<unsigned>(3);
+  CK(cudaMemsetAsync(kr.ticket, 0, 3 * sizeof(unsigned), s));
   kr.scal = mem.alloc<double>(S_NSCAL);
   kr.flag = mem.alloc<int32_t>(F_NFLAG);
   kr.bx = mem.alloc<double>(2LL * n);
@@ -212,7 +222,7 @@ void spmv(Handle& h, const double* x, double* y, cudaStream_t s) {
 
 void solve_pcg(Handle& h, const double* b, double* x, const asm_solve_opts& o, asm_solve_info& info,
                cudaStream_t s) {
-  ensure_krylov(h);
+  ensure_krylov(h, s);
   Krylov& kr = h.kr;
   const int n = h.n;
   const unsigned vg = NBLK;
@@ -235,19 +245,32 @@ void solve_pcg(Handle& h, const double* b, double* x, const asm_solve_opts& o, a
   apply_preconditioner(h, kr.r, kr.z, s, nullptr);
   k_dot<<<vg, NT, 0, s>>>(n, kr.r, kr.z, kr.part, nullptr);
   k_init_scalars<<<1, NT, 0, s>>>(kr.scal, kr.flag, kr.part, NBLK, o.rtol, o.max_it, 1);
-  CK(cudaMemcpyAsync(kr.p, kr.z, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  // first direction p = z: beta = 0 against a zero previous direction
+  CK(cudaMemsetAsync(kr.p, 0, sizeof(double) * n, s));
+  CK(cudaMemsetAsync(kr.scal + S_BETA, 0, sizeof(double), s));
   CK_LAUNCH("pcg init");
 
-  // one iteration, captured once
-  auto iteration = [&](cudaStream_t st) {
-    spmv_any(h, kr.p, kr.q, kr.part, kr.flag, true, st);
-    k_fin_alpha<<<1, NT, 0, st>>>(kr.part, NBLK, kr.scal, kr.flag);
-    k_pcg_update<<<vg, NT, 0, st>>>(n, x, kr.r, kr.p, kr.q, kr.scal, kr.part, kr.flag);
-    k_fin_res<<<1, NT, 0, st>>>(kr.part, NBLK, kr.scal, kr.flag, nullptr, 0);
-    apply_preconditioner(h, kr.r, kr.z, st, kr.flag);
-    k_dot<<<vg, NT, 0, st>>>(n, kr.r, kr.z, kr.part, kr.flag);
-    k_fin_beta<<<1, NT, 0, st>>>(kr.part, NBLK, kr.scal, kr.flag);
-    k_update_p<<<vg, NT, 0, st>>>(n, kr.p, kr.z, kr.scal, kr.flag);
+  const double avg = n ? (double)h.nnz / n : 1;
+  const int vw = avg <= 6 ? 4 : avg <= 12 ? 8 : avg <= 24 ? 16 : 32;
+  const unsigned sg = (unsigned)std::min<int64_t>(ceil_div(n, NT / vw), RBLK);
+  const unsigned xg = (unsigned)std::min<int64_t>(ceil_div(n, NT), RBLK);
+  const GridSum g_pq{kr.gpart, kr.ticket}, g_rr{kr.gpart + RBLK, kr.ticket + 1};
+  ApplyDot rzdot;
+  rzdot.r = kr.r;
+  rzdot.gs = GridSum{kr.gpart + 2 * RBLK, kr.ticket + 2};
+  rzdot.rz = kr.scal + S_RZ;
+  rzdot.beta = kr.scal + S_BETA;
+  // one iteration, the direction update first (beta of the previous one)
+  auto iteration = [&](cudaStream_t st, int) {
+    k_pcg_p<<<xg, NT, 0, st>>>(n, kr.p, kr.z, kr.scal, kr.flag);
+    switch (vw) {
+      case 4: k_pcg_spmv<4><<<sg, NT, 0, st>>>(n, h.row_ptr, h.col_idx, h.val, kr.p, kr.q, kr.scal, kr.flag, g_pq); break;
+      case 8: k_pcg_spmv<8><<<sg, NT, 0, st>>>(n, h.row_ptr, h.col_idx, h.val, kr.p, kr.q, kr.scal, kr.flag, g_pq); break;
+      case 16: k_pcg_spmv<16><<<sg, NT, 0, st>>>(n, h.row_ptr, h.col_idx, h.val, kr.p, kr.q, kr.scal, kr.flag, g_pq); break;
+      default: k_pcg_spmv<32><<<sg, NT, 0, st>>>(n, h.row_ptr, h.col_idx, h.val, kr.p, kr.q, kr.scal, kr.flag, g_pq); break;
+    }
+    k_pcg_xr<<<xg, NT, 0, st>>>(n, x, kr.r, kr.p, kr.q, kr.scal, kr.flag, g_rr);
+    apply_preconditioner(h, kr.r, kr.z, st, kr.flag, &rzdot);
   };
   cudaStream_t cs;
   CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
@@ -259,7 +282,7 @@ void solve_pcg(Handle& h, const double* b, double* x, const asm_solve_opts& o, a
   cudaGraphExec_t exec;
   const int chunk = std::max(1, o.check_every > 0 ? o.check_every : 8);
   CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-  for (int k = 0; k < chunk; ++k) iteration(cs);
+  for (int k = 0; k < chunk; ++k) iteration(cs, k);
   CK(cudaStreamEndCapture(cs, &graph));
   CK(cudaGraphInstantiate(&exec, graph, 0));
   int32_t* hflag = reinterpret_cast<int32_t*>(kr.hpin);
@@ -413,7 +436,7 @@ __global__ void k_backsolve(const double* H, int ldh, int khost, const int32_t* 
 
 void solve_fgmres(Handle& h, const double* b, double* x, const asm_solve_opts& o, asm_solve_info& info,
                   cudaStream_t s) {
-  ensure_krylov(h);
+  ensure_krylov(h, s);
   Krylov& kr = h.kr;
   const int n = h.n;
   const int m = std::max(1, std::min(o.restart, MAXV - 1));

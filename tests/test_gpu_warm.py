@@ -155,6 +155,10 @@ def test_training_reduces_loss_and_warm_start_gains():
             kw = dict(warm_start=warm, warm_net=net.ptr if warm else None)
             S = setup(prob, "fp32", **kw)
             sweeps[warm].append(P.asm_get_eigen_stats(S.h)[1])
+            x, info = S.solve(torch.as_tensor(prob.b, device="cuda"))
+            A = prob.csr()
+            rel = np.linalg.norm(prob.b - A @ x.cpu().numpy()) / np.linalg.norm(prob.b)
+            assert info.converged and rel <= 1.5e-8
             S.close()
             S = setup(prob, "fp32", max_sweeps=3, **kw)
             r, _ = P.asm_get_eigen_stats(S.h)
