@@ -124,6 +124,8 @@ typedef struct {
   int64_t coarse_front_entries; /* FP64 entries stored in the dense fronts      */
   int32_t coarse_max_front; /* order of the largest front                       */
   int32_t tile_ctas;        /* resident tile-pass blocks per SM the apply uses  */
+  int32_t local_sym;        /* subdomains whose local solve is the explicit
+                               inverse (one pass); the rest use W^T W        */
 } asm_setup_info;
 
 /* Fill *o with defaults: spd 1, FP64, oversample 8, max_sweeps 0 (= 40 in
@@ -168,10 +170,9 @@ asm_status asm_get_info(const asm_handle* h, asm_setup_info* info);
  * loaded (graph replays included), read from per-unit device counters;
  * synchronises the device.
  * asm_time_apply: runs the apply `iters` times on `stream` with CUDA events
- * around its parts and writes mean milliseconds to ms[6]: [0] one pass over
- * the local tiles (SPD: mean of the row pass t = W x and the column pass
- * y = W^T t), [1] the whole local part (gather and passes), [2] coarse
- * restriction + coarse
+ * around its parts and writes mean milliseconds to ms[6]: [0] the pass over
+ * all local tiles (row pass), [1] the whole local part (gather, row pass,
+ * the second stage), [2] coarse restriction + coarse
  * solve, [3] pull-sum, [4] the parts run one after the other, [5] the apply
  * as asm_apply runs it (coarse part overlapped on a side stream).
  * r, z: device. */

@@ -58,7 +58,7 @@ class asm_setup_info(C.Structure):
                 ("sum_ni", C.c_int64), ("max_ni", C.c_int32), ("sweeps_max", C.c_int32),
                 ("eig_resid_max", C.c_double), ("stage_ms", C.c_double * 12), ("coarse_levels", C.c_int32),
                 ("coarse_fronts", C.c_int32), ("coarse_front_entries", C.c_int64), ("coarse_max_front", C.c_int32),
-                ("tile_ctas", C.c_int32)]
+                ("tile_ctas", C.c_int32), ("local_sym", C.c_int32)]
 
 
 _lib = None

@@ -232,6 +232,7 @@ asm_status asm_setup(const asm_csr* A, const int32_t* part, int32_t N, int32_t o
     inf.coarse_front_entries = h.nd.n_mat;
     inf.coarse_max_front = h.nd.max_m;
     inf.tile_ctas = h.tile_ctas;
+    for (int8_t v : h.dn.h_sym) inf.local_sym += v ? 1 : 0;
   });
   if (st != ASM_OK) {
     free_handle_memory(H->h);

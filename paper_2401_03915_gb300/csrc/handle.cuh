@@ -56,8 +56,12 @@ struct Dense {
   void* xpad = nullptr;               // apply: gathered, scaled r in the padded space (local precision)
   void* tpad = nullptr;               // apply: t = W x (SPD first pass), padded space
   int2* row_items = nullptr;          // (subdomain, row block), most tiles first
-  int2* col_items = nullptr;          // (subdomain, column block), most tiles first (SPD)
-  int n_row_items = 0, n_col_items = 0;
+  int2* col_items = nullptr;          // (subdomain, column block) of two-pass subdomains, most tiles first
+  int2* sym_items = nullptr;          // (subdomain, block) of explicit-inverse subdomains
+  int n_row_items = 0, n_col_items = 0, n_sym_items = 0;
+  int8_t* sym = nullptr;              // per subdomain: 1 = tiles hold S = W^T W (SPD, single precision)
+  std::vector<int8_t> h_sym;
+  void* slots = nullptr;              // explicit-inverse column contributions, TILE per stored tile
   double* ypos = nullptr;             // per omega position: local solution before the pull
   int64_t n_tiles = 0, n_work = 0, n_xs = 0, n_s = 0, n_pad = 0;
   int32_t* err = nullptr;             // device error word

@@ -253,13 +253,16 @@ template <typename T>
 __global__ void __launch_bounds__(NT) k_chol_trtri(T* __restrict__ work, const int64_t* __restrict__ work_off,
                                                    const int32_t* __restrict__ np_arr,
                                                    const int32_t* __restrict__ n_arr, T* __restrict__ dinv_all,
-                                                   const int64_t* __restrict__ dinv_off, int32_t* err) {
+                                                   const int64_t* __restrict__ dinv_off, int32_t* err,
+                                                   T* __restrict__ tiles, const int64_t* __restrict__ tile_off,
+                                                   int8_t* __restrict__ sym, double sym_max_ratio) {
   COUNT_LAUNCH();
   extern __shared__ unsigned char smraw[];
   T (*Dm)[TILE + 1] = reinterpret_cast<T (*)[TILE + 1]>(smraw);
   T (*Xm)[TILE + 1] = Dm + TILE;
   T (*Ym)[TILE + 1] = Xm + TILE;
   __shared__ int bad;
+  __shared__ double piv_min, piv_max;
   const int i = blockIdx.x;
   const int n = n_arr[i], ld = np_arr[i];
   T* M = work + work_off[i];
@@ -275,7 +278,7 @@ __global__ void __launch_bounds__(NT) k_chol_trtri(T* __restrict__ work, const i
       S[r][c] = (r < rw && c < cw) ? B[(int64_t)r * ld + c] : T(0);
     }
   };
-  if (tid == 0) bad = 0;
+  if (tid == 0) { bad = 0; piv_min = 3.0e300; piv_max = 0; }
   // ---------------- phase 1: Cholesky
   for (int kb = 0; kb < nt; ++kb) {
     const int kw = min(TILE, n - kb * TILE);
@@ -293,6 +296,7 @@ __global__ void __launch_bounds__(NT) k_chol_trtri(T* __restrict__ work, const i
       if (tid == 0) {
         T d = Dm[j][j];
         if (!(d > T(0)) || !isfinite((double)d)) { bad = 1; d = T(1); }
+        if (j < kw) { piv_min = fmin(piv_min, (double)d); piv_max = fmax(piv_max, (double)d); }
         Dm[j][j] = sqrt(d);
       }
       __syncthreads();
@@ -413,6 +417,41 @@ __global__ void __launch_bounds__(NT) k_chol_trtri(T* __restrict__ work, const i
         }
     }
   }
+  // ---------------- phase 3 (well-conditioned subdomains, single precision):
+  // the explicit inverse S = W^T W as its lower tiles, S_IJ = sum_{K>=I} W_KI^T W_KJ.
+  // The pivot ratio max/min of the Cholesky bounds cond(A^_ii) from below; past
+  // sym_max_ratio the subdomain keeps the two-pass W^T W form, which stays SPD
+  // whatever the rounding (an explicit FP32 inverse would not).
+  const bool use_sym = sym_max_ratio > 0 && piv_max <= sym_max_ratio * piv_min;
+  if (tid == 0) sym[i] = use_sym ? 1 : 0;
+  if (!use_sym) return;
+  T* out = tiles + tile_off[i] * (TILE * TILE);
+  for (int I = 0; I < nt; ++I)
+    for (int J = 0; J <= I; ++J) {
+      T acc[4][4] = {};
+      for (int K = I; K < nt; ++K) {
+        __syncthreads();
+        {
+          // Ym = W_KI^T, Xm = W_KJ
+          const T* BI = blk(K, I);
+          const T* BJ = blk(K, J);
+          const int kw2 = min(TILE, n - K * TILE);
+          for (int idx = tid; idx < TILE * TILE; idx += NT) {
+            int q = idx / TILE, r = idx % TILE;
+            const bool in = q < kw2;
+            Ym[r][q] = (in && I * TILE + r < n) ? BI[(int64_t)q * ld + r] : T(0);
+            Xm[q][r] = (in && J * TILE + r < n) ? BJ[(int64_t)q * ld + r] : T(0);
+          }
+        }
+        __syncthreads();
+        block_mma<T>(acc, Ym, Xm, false, tx, ty);
+      }
+      T* o = out + ((int64_t)I * (I + 1) / 2 + J) * (TILE * TILE);
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) o[(ty + 16 * a) * TILE + tx + 16 * b] = acc[a][b];
+    }
 }
 
 // Copy A_ii^{-1} into TILE x TILE tiles: SPD keeps the lower tiles (I >= J),
@@ -420,11 +459,13 @@ __global__ void __launch_bounds__(NT) k_chol_trtri(T* __restrict__ work, const i
 template <typename T>
 __global__ void __launch_bounds__(NT) k_pack(const T* __restrict__ work, const int64_t* __restrict__ work_off,
                                              const int32_t* __restrict__ np, const int32_t* __restrict__ n_arr,
-                                             const int4* __restrict__ desc, int64_t ntiles, T* __restrict__ tiles) {
+                                             const int4* __restrict__ desc, int64_t ntiles,
+                                             const int8_t* __restrict__ sym, T* __restrict__ tiles) {
   COUNT_LAUNCH();
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     int4 d = desc[t];
     int i = d.x, I = d.y, J = d.z;
+    if (sym != nullptr && sym[i]) continue;  // tiles of S already written
     int n = n_arr[i], ld = np[i];
     const T* M = work + work_off[i];
     T* out = tiles + t * (TILE * TILE);
@@ -474,24 +515,6 @@ void run_local(Handle& h, cudaStream_t s) {
   dn.h_tile_off[N] = tl;
   h_pad_off[N] = pt;
   dn.n_work = w; dn.n_xs = xs; dn.n_s = ss; dn.n_tiles = tl; dn.n_pad = pt;
-  // apply work items, longest first: row blocks (SPD: row I has I+1 tiles;
-  // general: nt) and column blocks (SPD: column J has nt-J tiles)
-  std::vector<std::pair<int, int2>> ri, ci;
-  for (int i = 0; i < N; ++i) {
-    const int nt = dn.h_nt[i];
-    for (int b = 0; b < nt; ++b) {
-      ri.push_back({spd ? b + 1 : nt, make_int2(i, b)});
-      if (spd) ci.push_back({nt - b, make_int2(i, b)});
-    }
-  }
-  auto longest_first = [](const std::pair<int, int2>& a, const std::pair<int, int2>& b) { return a.first > b.first; };
-  std::stable_sort(ri.begin(), ri.end(), longest_first);
-  std::stable_sort(ci.begin(), ci.end(), longest_first);
-  std::vector<int2> rv, cv;
-  for (auto& e : ri) rv.push_back(e.second);
-  for (auto& e : ci) cv.push_back(e.second);
-  dn.n_row_items = (int)rv.size();
-  dn.n_col_items = (int)cv.size();
   dn.np = mem.alloc<int32_t>(N);
   dn.nt = mem.alloc<int32_t>(N);
   dn.work_off = mem.alloc<int64_t>(N);
@@ -499,8 +522,8 @@ void run_local(Handle& h, cudaStream_t s) {
   dn.s_off = mem.alloc<int64_t>(N);
   dn.tile_off = mem.alloc<int64_t>(N + 1);
   dn.pad_off = mem.alloc<int64_t>(N + 1);
-  dn.row_items = mem.alloc<int2>(std::max(dn.n_row_items, 1));
-  dn.col_items = mem.alloc<int2>(std::max(dn.n_col_items, 1));
+  dn.sym = mem.alloc<int8_t>(N);
+  CK(cudaMemsetAsync(dn.sym, 0, N, s));
   dn.tile_desc = mem.alloc<int4>(tl);
   int32_t* d_n = mem.alloc<int32_t>(N);
   int32_t* d_m = mem.alloc<int32_t>(N);
@@ -512,8 +535,7 @@ void run_local(Handle& h, cudaStream_t s) {
   CK(cudaMemcpyAsync(dn.s_off, dn.h_s_off.data(), 8 * N, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(dn.tile_off, dn.h_tile_off.data(), 8 * (N + 1), cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(dn.pad_off, h_pad_off.data(), 8 * (N + 1), cudaMemcpyHostToDevice, s));
-  CK(cudaMemcpyAsync(dn.row_items, rv.data(), sizeof(int2) * rv.size(), cudaMemcpyHostToDevice, s));
-  if (!cv.empty()) CK(cudaMemcpyAsync(dn.col_items, cv.data(), sizeof(int2) * cv.size(), cudaMemcpyHostToDevice, s));
+
   CK(cudaMemcpyAsync(dn.tile_desc, desc.data(), sizeof(int4) * tl, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(d_n, h.h_n.data(), 4 * N, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(d_m, h.h_m.data(), 4 * N, cudaMemcpyHostToDevice, s));
@@ -541,7 +563,11 @@ void run_local(Handle& h, cudaStream_t s) {
   if (spd) {
     const size_t sm3 = sizeof(T) * 3 * TILE * (TILE + 1);
     CK(cudaFuncSetAttribute(k_chol_trtri<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3));
-    k_chol_trtri<T><<<N, NT, sm3, s>>>(work, dn.work_off, dn.np, d_n, (T*)dn.dinv, dn.dinv_off, dn.err);
+    // single precision: subdomains whose Cholesky pivots span at most three
+    // decades get the explicit inverse (one pass in the apply)
+    const double ratio = sizeof(T) == 4 ? 1e3 : 0.0;
+    k_chol_trtri<T><<<N, NT, sm3, s>>>(work, dn.work_off, dn.np, d_n, (T*)dn.dinv, dn.dinv_off, dn.err,
+                                       (T*)dn.tiles, dn.tile_off, dn.sym, ratio);
   } else {
     k_sweep<T, false><<<N, NT, 0, s>>>(work, dn.work_off, dn.np, d_n, d_m, d_p, (T*)dn.XpT, dn.xs_off,
                                        (T*)dn.S, dn.s_off, dn.err);
@@ -550,9 +576,45 @@ void run_local(Handle& h, cudaStream_t s) {
   if (h.events) CK(cudaEventRecord(h.ev[4], s));
   // -- pack the apply tiles
   unsigned gp = (unsigned)std::min<int64_t>(std::max<int64_t>(tl, 1), 152 * 8);
-  k_pack<T><<<gp, NT, 0, s>>>(work, dn.work_off, dn.np, d_n, dn.tile_desc, tl, (T*)dn.tiles);
+  k_pack<T><<<gp, NT, 0, s>>>(work, dn.work_off, dn.np, d_n, dn.tile_desc, tl, spd ? dn.sym : nullptr,
+                              (T*)dn.tiles);
   CK_LAUNCH("pack tiles");
   if (h.events) CK(cudaEventRecord(h.ev[5], s));
+  // apply work items, longest first.  Row pass: every row block (SPD: row I
+  // has I+1 tiles; general: nt).  Column pass: the column blocks (nt-J
+  // tiles) of the subdomains kept in the two-pass form; the explicit-inverse
+  // subdomains instead add their column contributions per row block.
+  dn.h_sym.assign(N, 0);
+  if (spd) {
+    CK(cudaMemcpyAsync(dn.h_sym.data(), dn.sym, N, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  std::vector<std::pair<int, int2>> ri, ci;
+  std::vector<int2> si;
+  for (int i = 0; i < N; ++i) {
+    const int nt = dn.h_nt[i];
+    for (int b = 0; b < nt; ++b) {
+      ri.push_back({spd ? b + 1 : nt, make_int2(i, b)});
+      if (spd && !dn.h_sym[i]) ci.push_back({nt - b, make_int2(i, b)});
+      if (spd && dn.h_sym[i]) si.push_back(make_int2(i, b));
+    }
+  }
+  auto longest_first = [](const std::pair<int, int2>& a, const std::pair<int, int2>& b) { return a.first > b.first; };
+  std::stable_sort(ri.begin(), ri.end(), longest_first);
+  std::stable_sort(ci.begin(), ci.end(), longest_first);
+  std::vector<int2> rv, cv;
+  for (auto& e : ri) rv.push_back(e.second);
+  for (auto& e : ci) cv.push_back(e.second);
+  dn.n_row_items = (int)rv.size();
+  dn.n_col_items = (int)cv.size();
+  dn.n_sym_items = (int)si.size();
+  dn.row_items = mem.alloc<int2>(std::max(dn.n_row_items, 1));
+  dn.col_items = mem.alloc<int2>(std::max(dn.n_col_items, 1));
+  dn.sym_items = mem.alloc<int2>(std::max(dn.n_sym_items, 1));
+  CK(cudaMemcpyAsync(dn.row_items, rv.data(), sizeof(int2) * rv.size(), cudaMemcpyHostToDevice, s));
+  if (!cv.empty()) CK(cudaMemcpyAsync(dn.col_items, cv.data(), sizeof(int2) * cv.size(), cudaMemcpyHostToDevice, s));
+  if (!si.empty()) CK(cudaMemcpyAsync(dn.sym_items, si.data(), sizeof(int2) * si.size(), cudaMemcpyHostToDevice, s));
+  if (spd && !si.empty()) dn.slots = mem.alloc<T>(tl * TILE);
 }
 
 }  // namespace

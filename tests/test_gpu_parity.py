@@ -131,6 +131,27 @@ def test_fp64_apply_matches_oracle(P):
     pre.close(); pre1.close()
 
 
+@pytest.mark.parametrize("case", ["poisson", "contrast3d"])
+def test_fp32_local_solves_match_oracle(P, case):
+    """One-level FP32 apply (explicit inverse S = W^T W in one pass for the
+    well-conditioned subdomains, two passes W^T (W x) for the rest) against
+    the FP64 oracle's sum_i R_i^T A_ii^{-1} R_i r."""
+    if case == "poisson":
+        prob = poisson2d(64, 64, 4, 4, nev=4)
+    else:
+        prob = diffusion3d(16, (2, 2, 2), contrast=1e4, nev=6)
+    A = prob.csr()
+    st = O.setup(A, prob.part, prob.N, 1, prob.nev)
+    pre = make(P, A, prob.part, prob.N, 1, 0, precision="fp32", coarse=0)
+    assert pre.info.local_sym > 0
+    r = SplitMix64(31).normal(prob.n)
+    z = pre.apply(torch.as_tensor(r, device="cuda")).cpu().numpy()
+    zr = st.apply_one_level(r)
+    rel = np.linalg.norm(z - zr) / np.linalg.norm(zr)
+    assert rel < (1e-5 if case == "poisson" else 1e-3), rel
+    pre.close()
+
+
 def test_apply_is_deterministic(P):
     prob = poisson2d(64, 64, 4, 4, nev=4)
     for prec in ("fp64", "fp32"):
