@@ -29,8 +29,12 @@ namespace asmgpu {
 namespace {
 
 constexpr int NT = 256;
-constexpr int FB = 64;  // block size of the fronts
-// Blocks per 64-row task of the forward/backward solve: one row per warp.
+// Block size of the fronts.  Each elimination step inverts one FB x FB pivot
+// block in a single CTA, FB^3 FP64 FMAs at GB300's 2 per cycle per SM, on
+// the critical path of its level: 32 costs an eighth of 64 per step.
+constexpr int FB = 32;
+constexpr int RB = FB / 16;  // rows (and columns) per thread in a 16 x 16 thread grid
+// Blocks per FB-row task of the forward/backward solve: one row per warp.
 // The solve is bound by GB300's FP64 FMA rate (2 per cycle per SM), so every
 // level is spread over as many SMs as it has rows to give.
 constexpr int SPLIT = FB / (NT / 32);
@@ -40,7 +44,7 @@ constexpr int SPLIT = FB / (NT / 32);
 // ---------------------------------------------------------------------------
 // F = E restricted to (V u B) x (V u B) with at least one index in V, identity
 // on padded pivots, plus the children's update matrices.  One task = one
-// 64-row slab of one front.
+// FB-row slab of one front.
 __global__ void __launch_bounds__(NT) k_front_assemble(const FrontDev* __restrict__ fr, const int2* __restrict__ tasks,
                                                        const double* __restrict__ E, int ldE,
                                                        const int32_t* __restrict__ dofs,
@@ -141,7 +145,7 @@ __global__ void __launch_bounds__(NT) k_front_rowpanel(const FrontDev* __restric
   }
 }
 
-// Rank-64 update: M[R][C] -= M[R][K] M[K][C] for R, C != K (row panel already new).
+// Rank-FB update: M[R][C] -= M[R][K] M[K][C] for R, C != K (row panel already new).
 __global__ void __launch_bounds__(NT) k_front_update(const FrontDev* __restrict__ fr, const int4* __restrict__ tasks,
                                                      int k, double* __restrict__ M) {
   COUNT_LAUNCH();
@@ -158,22 +162,22 @@ __global__ void __launch_bounds__(NT) k_front_update(const FrontDev* __restrict_
   }
   __syncthreads();
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  double acc[4][4] = {};
+  double acc[RB][RB] = {};
   for (int q = 0; q < FB; ++q) {
-    double av[4], bv[4];
+    double av[RB], bv[RB];
 #pragma unroll
-    for (int a = 0; a < 4; ++a) av[a] = A[ty + 16 * a][q];
+    for (int a = 0; a < RB; ++a) av[a] = A[ty + 16 * a][q];
 #pragma unroll
-    for (int b = 0; b < 4; ++b) bv[b] = B[q][tx + 16 * b];
+    for (int b = 0; b < RB; ++b) bv[b] = B[q][tx + 16 * b];
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < RB; ++a)
 #pragma unroll
-      for (int b = 0; b < 4; ++b) acc[a][b] += av[a] * bv[b];
+      for (int b = 0; b < RB; ++b) acc[a][b] += av[a] * bv[b];
   }
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int a = 0; a < RB; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) F[(int64_t)(r0 + ty + 16 * a) * f.m + c0 + tx + 16 * b] -= acc[a][b];
+    for (int b = 0; b < RB; ++b) F[(int64_t)(r0 + ty + 16 * a) * f.m + c0 + tx + 16 * b] -= acc[a][b];
 }
 
 // Column panel: M[R][K] <- -M[R][K] P for R != K; the task with R == K
