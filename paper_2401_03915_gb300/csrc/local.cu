@@ -232,12 +232,47 @@ __global__ void __launch_bounds__(NT) k_sweep(T* __restrict__ work, const int64_
 // accurate to about cond(A^_ii) * eps (an explicitly inverted A^_ii^{-1} would
 // only be accurate to cond^2 * eps).  Dinv receives the inverses of the
 // diagonal blocks of L (which are the diagonal blocks of W).
+// 64 x 64 x 64 block products acc (+)= Am * (btrans ? Bm^T : Bm) from shared
+// memory ([64][65] layout), behind one interface for both precisions.
+//  FP64: CUDA-core FMAs, thread (tx, ty) owns rows ty + 16a, columns tx + 16b.
+//  FP32: tensor cores, mma.sync m16n8k8 TF32 with the 3xTF32 split
+//        (a = a_hi + a_lo, products a_hi b_hi + a_hi b_lo + a_lo b_hi, FP32
+//        accumulation), which keeps single-precision accuracy; warp w owns
+//        rows 16 (w % 4) .. +15 and columns 32 (w / 4) .. +31.
 template <typename T>
-__device__ __forceinline__ void block_mma(T (&acc)[4][4], const T (*Am)[TILE + 1], const T (*Bm)[TILE + 1],
-                                          bool btrans, int tx, int ty) {
-  // acc += Am * (btrans ? Bm^T : Bm) on 64 x 64 blocks; thread owns rows ty+16a, cols tx+16b
+struct BlockAcc {
+  T v[4][4];
+};
+
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
+  hi = to_tf32(x);
+  lo = to_tf32(x - __uint_as_float(hi));
+}
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+template <typename T>
+__device__ __forceinline__ void acc_zero(BlockAcc<T>& acc) {
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc.v[a][b] = T(0);
+}
+
+__device__ __forceinline__ void acc_mma(BlockAcc<double>& acc, const double (*Am)[TILE + 1],
+                                        const double (*Bm)[TILE + 1], bool btrans) {
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   for (int q = 0; q < TILE; ++q) {
-    T av[4], bv[4];
+    double av[4], bv[4];
 #pragma unroll
     for (int a = 0; a < 4; ++a) av[a] = Am[ty + 16 * a][q];
 #pragma unroll
@@ -245,8 +280,55 @@ __device__ __forceinline__ void block_mma(T (&acc)[4][4], const T (*Am)[TILE + 1
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-      for (int b = 0; b < 4; ++b) acc[a][b] += av[a] * bv[b];
+      for (int b = 0; b < 4; ++b) acc.v[a][b] += av[a] * bv[b];
   }
+}
+
+__device__ __forceinline__ void acc_mma(BlockAcc<float>& acc, const float (*Am)[TILE + 1],
+                                        const float (*Bm)[TILE + 1], bool btrans) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  const int r0 = 16 * (w & 3), c0 = 32 * (w >> 2);
+#pragma unroll 2
+  for (int k0 = 0; k0 < TILE; k0 += 8) {
+    uint32_t ah[4], al[4];
+    split_tf32(Am[r0 + g][k0 + t], ah[0], al[0]);
+    split_tf32(Am[r0 + g + 8][k0 + t], ah[1], al[1]);
+    split_tf32(Am[r0 + g][k0 + t + 4], ah[2], al[2]);
+    split_tf32(Am[r0 + g + 8][k0 + t + 4], ah[3], al[3]);
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt) {
+      const int n = c0 + 8 * nt + g;
+      const float x0 = btrans ? Bm[n][k0 + t] : Bm[k0 + t][n];
+      const float x1 = btrans ? Bm[n][k0 + t + 4] : Bm[k0 + t + 4][n];
+      uint32_t bh0, bl0, bh1, bl1;
+      split_tf32(x0, bh0, bl0);
+      split_tf32(x1, bh1, bl1);
+      mma_tf32(acc.v[nt], al, bh0, bh1);
+      mma_tf32(acc.v[nt], ah, bl0, bl1);
+      mma_tf32(acc.v[nt], ah, bh0, bh1);
+    }
+  }
+}
+
+// f(row, col, value) for every element of the thread's share of the block
+template <typename F>
+__device__ __forceinline__ void acc_for_each(const BlockAcc<double>& acc, F&& f) {
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) f(ty + 16 * a, tx + 16 * b, acc.v[a][b]);
+}
+template <typename F>
+__device__ __forceinline__ void acc_for_each(const BlockAcc<float>& acc, F&& f) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  const int r0 = 16 * (w & 3), c0 = 32 * (w >> 2);
+#pragma unroll
+  for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) f(r0 + g + (q >= 2 ? 8 : 0), c0 + 8 * nt + 2 * t + (q & 1), acc.v[nt][q]);
 }
 
 template <typename T>
@@ -338,17 +420,14 @@ __global__ void __launch_bounds__(NT) k_chol_trtri(T* __restrict__ work, const i
       __syncthreads();
       load(Ym, rb, kb);
       __syncthreads();
-      T acc[4][4] = {};
-      block_mma<T>(acc, Ym, Xm, true, tx, ty);
+      BlockAcc<T> acc;
+      acc_zero(acc);
+      acc_mma(acc, Ym, Xm, true);
       const int rw = min(TILE, n - rb * TILE);
       T* B = blk(rb, kb);
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-          int r = ty + 16 * a, c = tx + 16 * b;
-          if (r < rw && c < kw) B[(int64_t)r * ld + c] = acc[a][b];
-        }
+      acc_for_each(acc, [&](int r, int c, T v) {
+        if (r < rw && c < kw) B[(int64_t)r * ld + c] = v;
+      });
     }
     // trailing update: A_rc -= L_rk L_ck^T, c <= r
     for (int rb = kb + 1; rb < nt; ++rb) {
@@ -358,17 +437,14 @@ __global__ void __launch_bounds__(NT) k_chol_trtri(T* __restrict__ work, const i
         __syncthreads();
         load(Dm, cb, kb);
         __syncthreads();
-        T acc[4][4] = {};
-        block_mma<T>(acc, Ym, Dm, true, tx, ty);
+        BlockAcc<T> acc;
+        acc_zero(acc);
+        acc_mma(acc, Ym, Dm, true);
         const int rw = min(TILE, n - rb * TILE), cw = min(TILE, n - cb * TILE);
         T* B = blk(rb, cb);
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-          for (int b = 0; b < 4; ++b) {
-            int r = ty + 16 * a, c = tx + 16 * b;
-            if (r < rw && c < cw && (cb < rb || c <= r)) B[(int64_t)r * ld + c] -= acc[a][b];
-          }
+        acc_for_each(acc, [&](int r, int c, T v) {
+          if (r < rw && c < cw && (cb < rb || c <= r)) B[(int64_t)r * ld + c] -= v;
+        });
       }
     }
   }
@@ -385,36 +461,31 @@ __global__ void __launch_bounds__(NT) k_chol_trtri(T* __restrict__ work, const i
       }
     }
     for (int ib = jb + 1; ib < nt; ++ib) {
-      T acc[4][4] = {};
+      BlockAcc<T> acc;
+      acc_zero(acc);
       for (int kb = jb; kb < ib; ++kb) {
         __syncthreads();
         load(Ym, ib, kb);   // L_ik (kb >= jb: not yet overwritten)
         load(Xm, kb, jb);   // W_kj (kb < ib: already computed)
         __syncthreads();
-        block_mma<T>(acc, Ym, Xm, false, tx, ty);
+        acc_mma(acc, Ym, Xm, false);
       }
       __syncthreads();
       // W_ij = -Dinv_i acc
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) Xm[ty + 16 * a][tx + 16 * b] = acc[a][b];
+      acc_for_each(acc, [&](int r, int c, T v) { Xm[r][c] = v; });
       {
         const T* Dv = Dinv + (int64_t)ib * TILE * TILE;
         for (int idx = tid; idx < TILE * TILE; idx += NT) Ym[idx / TILE][idx % TILE] = Dv[idx];
       }
       __syncthreads();
-      T w[4][4] = {};
-      block_mma<T>(w, Ym, Xm, false, tx, ty);
+      BlockAcc<T> w;
+      acc_zero(w);
+      acc_mma(w, Ym, Xm, false);
       const int rw = min(TILE, n - ib * TILE);
       T* B = blk(ib, jb);
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-          int r = ty + 16 * a, c = tx + 16 * b;
-          if (r < rw && c < jw) B[(int64_t)r * ld + c] = -w[a][b];
-        }
+      acc_for_each(w, [&](int r, int c, T v) {
+        if (r < rw && c < jw) B[(int64_t)r * ld + c] = -v;
+      });
     }
   }
   // ---------------- phase 3 (well-conditioned subdomains, single precision):
@@ -428,7 +499,8 @@ __global__ void __launch_bounds__(NT) k_chol_trtri(T* __restrict__ work, const i
   T* out = tiles + tile_off[i] * (TILE * TILE);
   for (int I = 0; I < nt; ++I)
     for (int J = 0; J <= I; ++J) {
-      T acc[4][4] = {};
+      BlockAcc<T> acc;
+      acc_zero(acc);
       for (int K = I; K < nt; ++K) {
         __syncthreads();
         {
@@ -444,13 +516,10 @@ __global__ void __launch_bounds__(NT) k_chol_trtri(T* __restrict__ work, const i
           }
         }
         __syncthreads();
-        block_mma<T>(acc, Ym, Xm, false, tx, ty);
+        acc_mma(acc, Ym, Xm, false);
       }
       T* o = out + ((int64_t)I * (I + 1) / 2 + J) * (TILE * TILE);
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) o[(ty + 16 * a) * TILE + tx + 16 * b] = acc[a][b];
+      acc_for_each(acc, [&](int r, int c, T v) { o[r * TILE + c] = v; });
     }
 }
 
