@@ -43,6 +43,34 @@ constexpr int GM = 128;  // rows per CTA-GEMM tile
 constexpr int GK = 32;   // K chunk
 constexpr int GN = 32;   // columns per pass
 
+// Shared memory of one CTA GEMM: A tile GM x (GK + pad), B tile GK x (GN + pad).
+// The single-precision path feeds tensor cores and pads for conflict-free
+// fragment loads (A row stride 36, B row stride 40); FP64 keeps 33 / 32.
+template <typename T>
+__host__ __device__ constexpr int gemm_lda() { return sizeof(T) == 4 ? GK + 4 : GK + 1; }
+template <typename T>
+__host__ __device__ constexpr int gemm_ldb() { return sizeof(T) == 4 ? GN + 8 : GN; }
+template <typename T>
+__host__ __device__ constexpr size_t gemm_smem_bytes() {
+  return ((sizeof(T) * (GM * gemm_lda<T>() + GK * gemm_ldb<T>()) + 7) / 8) * 8;
+}
+
+__device__ __forceinline__ uint32_t f2tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ void split3(float x, uint32_t& hi, uint32_t& lo) {
+  hi = f2tf32(x);
+  lo = f2tf32(x - __uint_as_float(hi));
+}
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
 // Optional diagonal scalings (general path): factor for index q.
 struct Scale {
   const double* ds = nullptr;
@@ -57,13 +85,16 @@ struct Scale {
 template <typename T, bool ACOL, bool SUB = false>
 __device__ void cta_gemm(int M, int N, int K, const T* __restrict__ A, int lda, const T* __restrict__ B, int ldb,
                          T* __restrict__ C, int ldc, T* sm, Scale rs = Scale(), Scale ks = Scale(), bool kinv = false) {
-  T* As = sm;                  // GM x (GK + 1)
-  T* Bs = sm + GM * (GK + 1);  // GK x GN
-  // thread owns rows tr + 32 a (a = 0..3) and columns 4 tc .. 4 tc + 3 of a GM x GN tile
-  const int t = threadIdx.x, tr = t & 31, tc = t >> 5;
+  constexpr int LA = gemm_lda<T>(), LB = gemm_ldb<T>();
+  T* As = sm;             // GM x LA
+  T* Bs = sm + GM * LA;   // GK x LB
+  const int t = threadIdx.x;
   for (int n0 = 0; n0 < N; n0 += GN) {
     const int nw = min(GN, N - n0);
     for (int m0 = 0; m0 < M; m0 += GM) {
+      // FP32: tensor cores, warp w owns rows 16w .. 16w+15 of the GM x GN tile,
+      // 3xTF32 (hi/lo split) keeps single-precision accuracy.
+      // FP64: thread owns rows tr + 32 a (a = 0..3) and columns 4 tc .. 4 tc + 3.
       T acc[4][4];
 #pragma unroll
       for (int a = 0; a < 4; ++a)
@@ -76,48 +107,80 @@ __device__ void cta_gemm(int M, int N, int K, const T* __restrict__ A, int lda, 
             int r = idx / GK, kk = idx % GK;
             T v = (m0 + r < M && k0 + kk < K) ? A[(int64_t)(m0 + r) * lda + k0 + kk] : T(0);
             if (ks.on() && k0 + kk < K) v = (T)(kinv ? (double)v / ks(k0 + kk) : (double)v * ks(k0 + kk));
-            As[r * (GK + 1) + kk] = v;
+            As[r * LA + kk] = v;
           }
         } else {
           for (int idx = t; idx < GM * GK; idx += NT) {
             int kk = idx / GM, r = idx % GM;
             T v = (m0 + r < M && k0 + kk < K) ? A[(int64_t)(k0 + kk) * lda + m0 + r] : T(0);
             if (ks.on() && k0 + kk < K) v = (T)(kinv ? (double)v / ks(k0 + kk) : (double)v * ks(k0 + kk));
-            As[r * (GK + 1) + kk] = v;
+            As[r * LA + kk] = v;
           }
         }
         for (int idx = t; idx < GK * GN; idx += NT) {
           int kk = idx / GN, c = idx % GN;
-          Bs[idx] = (k0 + kk < K && c < nw) ? B[(int64_t)(k0 + kk) * ldb + n0 + c] : T(0);
+          Bs[kk * LB + c] = (k0 + kk < K && c < nw) ? B[(int64_t)(k0 + kk) * ldb + n0 + c] : T(0);
         }
         __syncthreads();
+        if constexpr (sizeof(T) == 4) {
+          const int lane = t & 31, w = t >> 5, g = lane >> 2, tq = lane & 3;
+          const float* Ar = reinterpret_cast<const float*>(As) + (16 * w) * LA;
+          const float* Bf = reinterpret_cast<const float*>(Bs);
+#pragma unroll
+          for (int kk = 0; kk < GK; kk += 8) {
+            uint32_t ah[4], al[4];
+            split3(Ar[g * LA + kk + tq], ah[0], al[0]);
+            split3(Ar[(g + 8) * LA + kk + tq], ah[1], al[1]);
+            split3(Ar[g * LA + kk + tq + 4], ah[2], al[2]);
+            split3(Ar[(g + 8) * LA + kk + tq + 4], ah[3], al[3]);
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt) {
+              uint32_t bh0, bl0, bh1, bl1;
+              split3(Bf[(kk + tq) * LB + 8 * nt + g], bh0, bl0);
+              split3(Bf[(kk + tq + 4) * LB + 8 * nt + g], bh1, bl1);
+              float* d = reinterpret_cast<float*>(acc[nt]);
+              float (&dd)[4] = *reinterpret_cast<float(*)[4]>(d);
+              mma_tf32(dd, al, bh0, bh1);
+              mma_tf32(dd, ah, bl0, bl1);
+              mma_tf32(dd, ah, bh0, bh1);
+            }
+          }
+        } else {
+          const int tr = t & 31, tc = t >> 5;
 #pragma unroll 4
-        for (int kk = 0; kk < GK; ++kk) {
-          T av[4], bv[4];
+          for (int kk = 0; kk < GK; ++kk) {
+            T av[4], bv[4];
 #pragma unroll
-          for (int a = 0; a < 4; ++a) av[a] = As[(tr + 32 * a) * (GK + 1) + kk];
+            for (int a = 0; a < 4; ++a) av[a] = As[(tr + 32 * a) * LA + kk];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) bv[q] = Bs[kk * GN + 4 * tc + q];
+            for (int q = 0; q < 4; ++q) bv[q] = Bs[kk * LB + 4 * tc + q];
 #pragma unroll
-          for (int a = 0; a < 4; ++a)
+            for (int a = 0; a < 4; ++a)
 #pragma unroll
-            for (int q = 0; q < 4; ++q) acc[a][q] += av[a] * bv[q];
-        }
-      }
-#pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        const int row = m0 + tr + 32 * a;
-        if (row >= M) continue;
-        const T f = rs.on() ? (T)rs(row) : T(1);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          int c = 4 * tc + q;
-          if (c < nw) {
-            T* cp = C + (int64_t)row * ldc + n0 + c;
-            if (SUB) *cp -= acc[a][q] * f; else *cp = acc[a][q] * f;
+              for (int q = 0; q < 4; ++q) acc[a][q] += av[a] * bv[q];
           }
         }
       }
+      // epilogue: element (row, col) of the tile for each accumulator entry
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          int row, c;
+          if constexpr (sizeof(T) == 4) {
+            const int lane = t & 31, w = t >> 5;
+            row = 16 * w + (lane >> 2) + (q >= 2 ? 8 : 0);
+            c = 8 * a + 2 * (lane & 3) + (q & 1);
+          } else {
+            row = (t & 31) + 32 * a;
+            c = 4 * (t >> 5) + q;
+          }
+          row += m0;
+          if (row >= M || c >= nw) continue;
+          const T f = rs.on() ? (T)rs(row) : T(1);
+          T* cp = C + (int64_t)row * ldc + n0 + c;
+          if (SUB) *cp -= acc[a][q] * f; else *cp = acc[a][q] * f;
+        }
     }
   }
   __syncthreads();
@@ -321,7 +384,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 4 : 1) k_subspace(
   T* AV = base + 6 * blk; // p x s  (general: g x s)
   // shared memory: GEMM tiles, then the small dense matrices
   T* gsm = reinterpret_cast<T*>(shd);
-  double* G = shd + (sizeof(T) * (GM * (GK + 1) + GK * GN) + 7) / 8;
+  double* G = shd + gemm_smem_bytes<T>() / 8;
   double* Minv = G + s * s;
   T* H = reinterpret_cast<T*>(Minv + s * s);
   T* Q = H + s * s;
@@ -765,7 +828,7 @@ void run_eigen(Handle& h, cudaStream_t s) {
   co.sweeps = mem.alloc<int32_t>(N);
   CK(cudaMemcpyAsync(co.scr_off, scr.data(), 8 * N, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(co.z_off, zo.data(), 8 * (N + 1), cudaMemcpyHostToDevice, s));
-  size_t gemm_bytes = ((sizeof(T) * (GM * (GK + 1) + GK * GN) + 7) / 8) * 8;
+  size_t gemm_bytes = gemm_smem_bytes<T>();
   size_t smem = gemm_bytes + (size_t)2 * smax * smax * sizeof(double) +
                 (size_t)(4 * smax * smax + 2 * smax) * sizeof(T) + 64;
   const double tol = h.opt.eig_tol > 0 ? h.opt.eig_tol : (h.fp32 ? 1e-3 : 1e-8);
