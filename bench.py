@@ -61,8 +61,10 @@ def parse():
     ap.add_argument("--no-forms", action="store_true", help="skip the FP64 / FP32 comparison forms")
     ap.add_argument("--warm-instances", type=int, default=12)
     ap.add_argument("--warm-steps", type=int, default=2000)
-    ap.add_argument("--mode", default="step", choices=["step", "apply"],
-                    help="apply: one setup, then --apply-iters applies (for profiler captures)")
+    ap.add_argument("--mode", default="step", choices=["step", "apply", "stream"],
+                    help="apply: one setup, then --apply-iters applies (for profiler captures); "
+                         "stream: the batched stream of generated 3D diffusion instances, learned vs randomized start")
+    ap.add_argument("--instances", type=int, default=200, help="stream mode: instances in the stream")
     return ap.parse_args()
 
 
@@ -258,6 +260,53 @@ def train_warm_net(P, torch, n_instances: int, steps: int):
                  "loss_after": round(loss1, 4)}
 
 
+def run_stream(args, P, torch, dev, stream):
+    """The stream workload: `--instances` seeded 3D diffusion instances (cube
+    sides 24..48, contrast 10^2..10^6, boxes of 6-8 per side), each set up
+    and solved to 1e-8 with FP32 local work, once with the randomized start and
+    once with the learned warm start (network trained first on instances with
+    other seeds).  Inputs are resident on the device; CUDA events around each
+    pass over the whole stream."""
+    from asm_inputs import stream_instance
+    net, warm_info = train_warm_net(P, torch, args.warm_instances, args.warm_steps)
+    insts = []
+    for k in range(args.instances):
+        p = stream_instance(k, base_seed=0)
+        insts.append((p, torch.as_tensor(p.indptr, device=dev), torch.as_tensor(p.indices, device=dev),
+                      torch.as_tensor(p.data, device=dev), torch.as_tensor(p.part, device=dev),
+                      torch.as_tensor(p.b, device=dev)))
+    sopt = P.default_solve_opts(rtol=1e-8, max_it=5000)
+    out = {}
+    for name, warm in (("random", False), ("learned", True)):
+        opt = P.default_options(local_precision=P.PREC_FP32, warm_start=1 if warm else 0,
+                                warm_net=net.ptr if warm else None)
+        for p, rp, ci, va, pa, b in insts[:3]:  # warm-up (tuner caches, pools)
+            x = torch.zeros_like(b)
+            h = P.asm_setup(rp, ci, va, pa, p.N, p.delta, p.nev, opt, stream, True)
+            P.asm_solve(h, b, x, sopt, stream)
+            P.asm_destroy(h)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        its, sweeps, subs, rows = [], [], 0, 0
+        e0.record(stream)
+        for p, rp, ci, va, pa, b in insts:
+            x = torch.zeros_like(b)
+            h = P.asm_setup(rp, ci, va, pa, p.N, p.delta, p.nev, opt, stream, True)
+            its.append(P.asm_solve(h, b, x, sopt, stream).iterations)
+            sweeps.append(float(np.mean(P.asm_get_eigen_stats(h)[1])))
+            subs += p.N
+            rows += p.n
+            P.asm_destroy(h)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out[name] = {"s_total": e0.elapsed_time(e1) / 1e3, "iterations_total": int(np.sum(its)),
+                     "mean_sweeps": float(np.mean(sweeps)), "subdomains": subs, "unknowns": rows}
+    print(json.dumps({"mode": "stream", "instances": args.instances, "warm_start": warm_info, **out,
+                      "learned_vs_random": out["random"]["s_total"] / out["learned"]["s_total"]}), flush=True)
+    net.close()
+
+
 def run_ours(args):
     import torch
     rank = int(os.environ.get("RANK", "0"))
@@ -289,6 +338,10 @@ def run_ours(args):
     opt = P.default_options(local_precision=prec, warm_start=1 if net else 0, warm_net=net.ptr if net else None)
     sopt = P.default_solve_opts(rtol=1e-8, max_it=5000)
     stream = torch.cuda.current_stream()
+
+    if args.mode == "stream":
+        run_stream(args, P, torch, dev, stream)
+        return
 
     if args.mode == "apply":
         h = P.asm_setup(rp, ci, va, pa, prob.N, prob.delta, prob.nev, opt, stream, True)
