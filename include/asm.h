@@ -83,7 +83,8 @@ typedef struct {
                                block are predicted by warm_net from per-node
                                features; the rest stay random                 */
   int32_t filter_degree;    /* Chebyshev filter degree between Rayleigh-Ritz
-                               steps of the subspace iteration (0: 4)          */
+                               steps of the subspace iteration (0: 4 in FP64,
+                               3 in FP32)                                      */
   int32_t record_warm;      /* 1 (SPD only): keep the network inputs and the
                                converged start blocks for asm_get_warm_data   */
   int32_t reserved[3];
@@ -130,7 +131,8 @@ typedef struct {
 
 /* Fill *o with defaults: spd 1, FP64, oversample 8, max_sweeps 0 (= 40 in
  * FP64, 12 in FP32), eig_tol 0 (= 1e-8 in FP64, 1e-3 in FP32), nu off, coarse
- * on, seed 0, filter degree 0 (= 4), no warm start, nothing recorded. */
+ * on, seed 0, filter degree 0 (= 4 in FP64, 3 in FP32), no warm start, nothing
+ * recorded. */
 void asm_default_options(asm_options* o);
 void asm_default_solve_opts(asm_solve_opts* o);
 
