@@ -336,7 +336,6 @@ __global__ void __launch_bounds__(NT) k_chol_trtri(T* __restrict__ work, const i
                                                    const int32_t* __restrict__ np_arr,
                                                    const int32_t* __restrict__ n_arr, T* __restrict__ dinv_all,
                                                    const int64_t* __restrict__ dinv_off, int32_t* err,
-                                                   T* __restrict__ tiles, const int64_t* __restrict__ tile_off,
                                                    int8_t* __restrict__ sym, double sym_max_ratio) {
   COUNT_LAUNCH();
   extern __shared__ unsigned char smraw[];
@@ -488,39 +487,51 @@ __global__ void __launch_bounds__(NT) k_chol_trtri(T* __restrict__ work, const i
       });
     }
   }
-  // ---------------- phase 3 (well-conditioned subdomains, single precision):
-  // the explicit inverse S = W^T W as its lower tiles, S_IJ = sum_{K>=I} W_KI^T W_KJ.
-  // The pivot ratio max/min of the Cholesky bounds cond(A^_ii) from below; past
-  // sym_max_ratio the subdomain keeps the two-pass W^T W form, which stays SPD
+  // The pivot ratio max/min of the Cholesky bounds cond(A^_ii) from below;
+  // within sym_max_ratio the subdomain gets the explicit inverse S = W^T W
+  // (k_lauum); past it, it keeps the two-pass W^T W form, which stays SPD
   // whatever the rounding (an explicit FP32 inverse would not).
-  const bool use_sym = sym_max_ratio > 0 && piv_max <= sym_max_ratio * piv_min;
-  if (tid == 0) sym[i] = use_sym ? 1 : 0;
-  if (!use_sym) return;
-  T* out = tiles + tile_off[i] * (TILE * TILE);
-  for (int I = 0; I < nt; ++I)
-    for (int J = 0; J <= I; ++J) {
-      BlockAcc<T> acc;
-      acc_zero(acc);
-      for (int K = I; K < nt; ++K) {
-        __syncthreads();
-        {
-          // Ym = W_KI^T, Xm = W_KJ
-          const T* BI = blk(K, I);
-          const T* BJ = blk(K, J);
-          const int kw2 = min(TILE, n - K * TILE);
-          for (int idx = tid; idx < TILE * TILE; idx += NT) {
-            int q = idx / TILE, r = idx % TILE;
-            const bool in = q < kw2;
-            Ym[r][q] = (in && I * TILE + r < n) ? BI[(int64_t)q * ld + r] : T(0);
-            Xm[q][r] = (in && J * TILE + r < n) ? BJ[(int64_t)q * ld + r] : T(0);
-          }
-        }
-        __syncthreads();
-        acc_mma(acc, Ym, Xm, false);
+  if (tid == 0) sym[i] = (sym_max_ratio > 0 && piv_max <= sym_max_ratio * piv_min) ? 1 : 0;
+}
+
+// S = W^T W for the subdomains flagged in sym, one block per lower tile:
+// S_IJ = sum_{K >= I} W_KI^T W_KJ from the W left in the working matrix,
+// written to the apply tile of (I, J).  Many small independent blocks hide
+// the tile loads that bound a one-block-per-subdomain loop.
+template <typename T>
+__global__ void __launch_bounds__(NT) k_lauum(const T* __restrict__ work, const int64_t* __restrict__ work_off,
+                                              const int32_t* __restrict__ np_arr, const int32_t* __restrict__ n_arr,
+                                              const int4* __restrict__ desc, int64_t ntiles,
+                                              const int8_t* __restrict__ sym, T* __restrict__ tiles) {
+  COUNT_LAUNCH();
+  __shared__ T Xm[TILE][TILE + 1];
+  __shared__ T Ym[TILE][TILE + 1];
+  const int tid = threadIdx.x;
+  for (int64_t tt = blockIdx.x; tt < ntiles; tt += gridDim.x) {
+    const int4 d = desc[tt];
+    const int i = d.x, I = d.y, J = d.z;
+    if (!sym[i]) continue;
+    const int n = n_arr[i], ld = np_arr[i], nt = (n + TILE - 1) / TILE;
+    const T* M = work + work_off[i];
+    BlockAcc<T> acc;
+    acc_zero(acc);
+    for (int K = I; K < nt; ++K) {
+      __syncthreads();
+      const T* BI = M + (int64_t)K * TILE * ld + I * TILE;
+      const T* BJ = M + (int64_t)K * TILE * ld + J * TILE;
+      const int kw = min(TILE, n - K * TILE);
+      for (int idx = tid; idx < TILE * TILE; idx += NT) {
+        const int q = idx / TILE, r = idx % TILE;
+        const bool in = q < kw;
+        Ym[r][q] = (in && I * TILE + r < n) ? BI[(int64_t)q * ld + r] : T(0);  // W_KI^T
+        Xm[q][r] = (in && J * TILE + r < n) ? BJ[(int64_t)q * ld + r] : T(0);  // W_KJ
       }
-      T* o = out + ((int64_t)I * (I + 1) / 2 + J) * (TILE * TILE);
-      acc_for_each(acc, [&](int r, int c, T v) { o[r * TILE + c] = v; });
+      __syncthreads();
+      acc_mma(acc, Ym, Xm, false);
     }
+    T* o = tiles + tt * (TILE * TILE);
+    acc_for_each(acc, [&](int r, int c, T v) { o[r * TILE + c] = v; });
+  }
 }
 
 // Copy A_ii^{-1} into TILE x TILE tiles: SPD keeps the lower tiles (I >= J),
@@ -635,8 +646,12 @@ void run_local(Handle& h, cudaStream_t s) {
     // single precision: subdomains whose Cholesky pivots span at most three
     // decades get the explicit inverse (one pass in the apply)
     const double ratio = sizeof(T) == 4 ? 1e3 : 0.0;
-    k_chol_trtri<T><<<N, NT, sm3, s>>>(work, dn.work_off, dn.np, d_n, (T*)dn.dinv, dn.dinv_off, dn.err,
-                                       (T*)dn.tiles, dn.tile_off, dn.sym, ratio);
+    k_chol_trtri<T><<<N, NT, sm3, s>>>(work, dn.work_off, dn.np, d_n, (T*)dn.dinv, dn.dinv_off, dn.err, dn.sym,
+                                       ratio);
+    if constexpr (sizeof(T) == 4) {
+      const unsigned gl = (unsigned)std::min<int64_t>(std::max<int64_t>(tl, 1), 152 * 64);
+      k_lauum<T><<<gl, NT, 0, s>>>(work, dn.work_off, dn.np, d_n, dn.tile_desc, tl, dn.sym, (T*)dn.tiles);
+    }
   } else {
     k_sweep<T, false><<<N, NT, 0, s>>>(work, dn.work_off, dn.np, d_n, d_m, d_p, (T*)dn.XpT, dn.xs_off,
                                        (T*)dn.S, dn.s_off, dn.err);
