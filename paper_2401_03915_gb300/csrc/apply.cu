@@ -286,7 +286,10 @@ __global__ void __launch_bounds__(NT) k_sym_reduce(const int2* __restrict__ item
 // c[col_off[i] + j] = sum_{a < p_i} Z_i[a][j] r[omega_i[a]]  (Z^T r).
 // Thread (g, c) of the block sums rows a = g, g + 16, ... of column j0 + c;
 // the 16 row groups are added in a fixed order.
-__global__ void __launch_bounds__(NT) k_coarse_restrict(const double* __restrict__ Z, const int64_t* __restrict__ z_off,
+// ZT = float: the single-precision copy of Z (the FP64 master is rounded to
+// it, so E = Z^T A Z describes exactly this basis) with FP32 products and sums.
+template <typename ZT>
+__global__ void __launch_bounds__(NT) k_coarse_restrict(const ZT* __restrict__ Z, const int64_t* __restrict__ z_off,
                                                         const int32_t* __restrict__ count,
                                                         const int32_t* __restrict__ col_off,
                                                         const int32_t* __restrict__ sub_off,
@@ -296,20 +299,20 @@ __global__ void __launch_bounds__(NT) k_coarse_restrict(const double* __restrict
                                                         const int32_t* __restrict__ done) {
   COUNT_LAUNCH();
   if (done != nullptr && *done) return;
-  __shared__ double red[16][17];
+  __shared__ ZT red[16][17];
   const int i = blockIdx.x;
   const int k = count[i], p = p_arr[i], b0 = sub_off[i];
-  const double* Zi = Z + z_off[i];
+  const ZT* Zi = Z + z_off[i];
   const int g = threadIdx.x >> 4, cc = threadIdx.x & 15;
   for (int j0 = 0; j0 < k; j0 += 16) {
-    double acc = 0;
+    ZT acc = 0;
     if (j0 + cc < k)
-      for (int a = g; a < p; a += 16) acc += Zi[(int64_t)a * nev + j0 + cc] * r[omega[b0 + a]];
+      for (int a = g; a < p; a += 16) acc += Zi[(int64_t)a * nev + j0 + cc] * (ZT)r[omega[b0 + a]];
     red[g][cc] = acc;
     __syncthreads();
     if (threadIdx.x < 16 && j0 + threadIdx.x < k) {
       double s = 0;
-      for (int q = 0; q < 16; ++q) s += red[q][threadIdx.x];
+      for (int q = 0; q < 16; ++q) s += (double)red[q][threadIdx.x];
       c[col_off[i] + j0 + threadIdx.x] = s;
     }
     __syncthreads();
@@ -318,11 +321,12 @@ __global__ void __launch_bounds__(NT) k_coarse_restrict(const double* __restrict
 
 // z[v] = s_v * sum over the occurrences (i, a) of v of y_pos[(i, a)]
 //        + Z_{part v}[own position] . y_coarse   (fixed order, no atomics)
+template <typename ZT>
 __global__ void __launch_bounds__(NT) k_apply_pull(int n, const int32_t* __restrict__ occ_ptr,
                                                    const int32_t* __restrict__ occ_pos,
                                                    const double* __restrict__ ypos, const int32_t* __restrict__ part,
                                                    const int32_t* __restrict__ own_pos,
-                                                   const int32_t* __restrict__ sub_off, const double* __restrict__ Z,
+                                                   const int32_t* __restrict__ sub_off, const ZT* __restrict__ Z,
                                                    const int64_t* __restrict__ z_off, const int32_t* __restrict__ count,
                                                    const int32_t* __restrict__ col_off, int nev,
                                                    const double* __restrict__ yc, const double* __restrict__ ds,
@@ -339,18 +343,11 @@ __global__ void __launch_bounds__(NT) k_apply_pull(int n, const int32_t* __restr
       int i = part[v];
       int k = count[i];
       if (k > 0) {
-        const double* zr = Z + z_off[i] + (int64_t)(own_pos[v] - sub_off[i]) * nev;
+        const ZT* zr = Z + z_off[i] + (int64_t)(own_pos[v] - sub_off[i]) * nev;
         const double* y = yc + col_off[i];
-        double s = 0;
-        int j = 0;
-        if ((nev & 1) == 0) {
-          for (; j + 1 < k; j += 2) {
-            double2 zz = *reinterpret_cast<const double2*>(zr + j);
-            s += zz.x * y[j] + zz.y * y[j + 1];
-          }
-        }
-        for (; j < k; ++j) s += zr[j] * y[j];
-        acc += s;
+        ZT s = 0;
+        for (int j = 0; j < k; ++j) s += zr[j] * (ZT)y[j];
+        acc += (double)s;
       }
     }
     z[v] = acc;
@@ -440,8 +437,12 @@ const double* apply_coarse(Handle& h, const double* r, cudaStream_t s, const int
   if (co.n_C == 0) return nullptr;
   double* c = co.cvec;
   double* y = co.cvec + round_up(co.n_C, 64);
-  k_coarse_restrict<<<h.N, NT, 0, s>>>(co.Z, co.z_off, co.count, co.col_off, h.ov.sub_off, h.dev_p, h.ov.omega,
-                                       h.nev, r, c, done);
+  if (co.Zf)
+    k_coarse_restrict<float><<<h.N, NT, 0, s>>>(co.Zf, co.z_off, co.count, co.col_off, h.ov.sub_off, h.dev_p,
+                                                h.ov.omega, h.nev, r, c, done);
+  else
+    k_coarse_restrict<double><<<h.N, NT, 0, s>>>(co.Z, co.z_off, co.count, co.col_off, h.ov.sub_off, h.dev_p,
+                                                 h.ov.omega, h.nev, r, c, done);
   coarse_solve(h, c, y, s, done);
   return y;
 }
@@ -452,9 +453,14 @@ void apply_pull(Handle& h, const double* yc, double* z, cudaStream_t s, const in
   Dense& dn = h.dn;
   Coarse& co = h.co;
   unsigned gp = (unsigned)std::min<int64_t>(ceil_div(h.n, NT), 152 * 16);
-  k_apply_pull<<<gp, NT, 0, s>>>(h.n, h.ov.occ_ptr, h.ov.occ_pos, dn.ypos, h.part, h.ov.own_pos, h.ov.sub_off,
-                                 co.Z, co.z_off, co.count, co.col_off, h.nev, yc, h.dscale, z, done,
-                                 dot ? *dot : ApplyDot());
+  if (co.Zf)
+    k_apply_pull<float><<<gp, NT, 0, s>>>(h.n, h.ov.occ_ptr, h.ov.occ_pos, dn.ypos, h.part, h.ov.own_pos,
+                                          h.ov.sub_off, co.Zf, co.z_off, co.count, co.col_off, h.nev, yc, h.dscale,
+                                          z, done, dot ? *dot : ApplyDot());
+  else
+    k_apply_pull<double><<<gp, NT, 0, s>>>(h.n, h.ov.occ_ptr, h.ov.occ_pos, dn.ypos, h.part, h.ov.own_pos,
+                                           h.ov.sub_off, co.Z, co.z_off, co.count, co.col_off, h.nev, yc, h.dscale,
+                                           z, done, dot ? *dot : ApplyDot());
 }
 
 // The coarse part (Z^T r, the level-by-level coarse solve) is independent of

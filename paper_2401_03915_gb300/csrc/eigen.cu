@@ -795,6 +795,15 @@ __global__ void __launch_bounds__(NT) k_warm_features(
   }
 }
 
+__global__ void k_round_z(double* __restrict__ Z, float* __restrict__ Zf, int64_t n) {
+  COUNT_LAUNCH();
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    const float f = (float)Z[k];
+    Zf[k] = f;
+    Z[k] = (double)f;
+  }
+}
+
 template <typename T>
 void run_eigen(Handle& h, cudaStream_t s) {
   const int N = h.N, nev = h.nev;
@@ -888,6 +897,14 @@ void run_eigen(Handle& h, cudaStream_t s) {
   if (spd) launch(k_subspace<T, true>);
   else launch(k_subspace<T, false>);
   CK_LAUNCH("subspace iteration");
+  if (h.fp32) {
+    // the apply restricts and prolongs with an FP32 copy of Z; rounding the
+    // FP64 master to the same values keeps E = Z^T A Z exact for that basis
+    co.Zf = mem.alloc<float>(std::max<int64_t>(zt, 1));
+    const unsigned gz = (unsigned)std::min<int64_t>(std::max<int64_t>(ceil_div(zt, NT), 1), 152 * 16);
+    k_round_z<<<gz, NT, 0, s>>>(co.Z, co.Zf, zt);
+    CK_LAUNCH("round Z");
+  }
 }
 
 }  // namespace

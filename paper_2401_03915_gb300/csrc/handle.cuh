@@ -75,6 +75,8 @@ struct Coarse {
   int32_t* col_off = nullptr;         // N+1 first coarse column
   int64_t* z_off = nullptr;           // offset of Z_i (p_i x nev, row-major FP64)
   double* Z = nullptr;
+  float* Zf = nullptr;                // single-precision local work: Z rounded to FP32 for the
+                                      // restriction and prolongation (Z itself holds the same values)
   double* values = nullptr;           // N * nev
   double* resid = nullptr;            // N * nev eigen-residuals
   int32_t* sweeps = nullptr;          // N
