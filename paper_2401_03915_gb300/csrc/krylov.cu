@@ -21,18 +21,14 @@ constexpr int RBLK = 152 * 16;  // most blocks of a fused-reduction launch
 enum Scal { S_RZ = 0, S_PQ, S_ALPHA, S_BETA, S_RR, S_BNORM, S_RTOL, S_RELRES, S_TMP, S_NSCAL = 16 };
 enum Flag { F_DONE = 0, F_IT, F_MAXIT, F_NFLAG = 4 };
 
-// vector-per-row CSR SpMV with VW lanes per row; optional dot(x, y) partials.
-template <int VW, bool DOT>
+// vector-per-row CSR SpMV with VW lanes per row.
+template <int VW>
 __global__ void __launch_bounds__(NT) k_spmv(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                                              const double* __restrict__ val, const double* __restrict__ x,
-                                             double* __restrict__ y, double* __restrict__ part,
-                                             const int32_t* __restrict__ done) {
+                                             double* __restrict__ y) {
   COUNT_LAUNCH();
-  if (done != nullptr && done[F_DONE]) return;
-  __shared__ double red[NT / 32];
   const int lane = threadIdx.x % VW;
   const int rows_per_block = NT / VW;
-  double dsum = 0;
   for (int base = blockIdx.x * rows_per_block; base < n; base += gridDim.x * rows_per_block) {
     int r = base + threadIdx.x / VW;
     double acc = 0;
@@ -42,14 +38,7 @@ __global__ void __launch_bounds__(NT) k_spmv(int n, const int32_t* __restrict__ 
     }
 #pragma unroll
     for (int o = VW / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (r < n && lane == 0) {
-      y[r] = acc;
-      if (DOT) dsum += acc * x[r];
-    }
-  }
-  if (DOT) {
-    dsum = block_sum(dsum, red);
-    if (threadIdx.x == 0) part[blockIdx.x] = dsum;
+    if (r < n && lane == 0) y[r] = acc;
   }
 }
 
@@ -174,23 +163,18 @@ __global__ void k_init_scalars(double* scal, int32_t* flag, const double* part, 
 inline unsigned vgrid(int n) { return (unsigned)std::min<int64_t>(ceil_div(n, NT), NBLK); }
 
 template <int VW>
-void spmv_launch(Handle& h, const double* x, double* y, double* part, const int32_t* done, bool dot, cudaStream_t s) {
+void spmv_launch(Handle& h, const double* x, double* y, cudaStream_t s) {
   const int rows = NT / VW;
-  unsigned g = (unsigned)std::min<int64_t>(ceil_div(h.n, rows), NBLK);
-  if (dot) {
-    // the dot partials need exactly NBLK slots for a fixed reduction
-    k_spmv<VW, true><<<NBLK, NT, 0, s>>>(h.n, h.row_ptr, h.col_idx, h.val, x, y, part, done);
-  } else {
-    k_spmv<VW, false><<<g, NT, 0, s>>>(h.n, h.row_ptr, h.col_idx, h.val, x, y, part, done);
-  }
+  const unsigned g = (unsigned)std::min<int64_t>(ceil_div(h.n, rows), RBLK);
+  k_spmv<VW><<<g, NT, 0, s>>>(h.n, h.row_ptr, h.col_idx, h.val, x, y);
 }
 
-void spmv_any(Handle& h, const double* x, double* y, double* part, const int32_t* done, bool dot, cudaStream_t s) {
+void spmv_any(Handle& h, const double* x, double* y, cudaStream_t s) {
   double avg = h.n ? (double)h.nnz / h.n : 1;
-  if (avg <= 6) spmv_launch<4>(h, x, y, part, done, dot, s);
-  else if (avg <= 12) spmv_launch<8>(h, x, y, part, done, dot, s);
-  else if (avg <= 24) spmv_launch<16>(h, x, y, part, done, dot, s);
-  else spmv_launch<32>(h, x, y, part, done, dot, s);
+  if (avg <= 6) spmv_launch<4>(h, x, y, s);
+  else if (avg <= 12) spmv_launch<8>(h, x, y, s);
+  else if (avg <= 24) spmv_launch<16>(h, x, y, s);
+  else spmv_launch<32>(h, x, y, s);
 }
 
 void ensure_krylov(Handle& h, cudaStream_t s) {
@@ -216,7 +200,7 @@ void ensure_krylov(Handle& h, cudaStream_t s) {
 }  // namespace
 
 void spmv(Handle& h, const double* x, double* y, cudaStream_t s) {
-  spmv_any(h, x, y, nullptr, nullptr, false, s);
+  spmv_any(h, x, y, s);
   CK_LAUNCH("spmv");
 }
 
@@ -234,7 +218,7 @@ void solve_pcg(Handle& h, const double* b, double* x, const asm_solve_opts& o, a
   k_dot<<<vg, NT, 0, s>>>(n, b, b, kr.part, nullptr);
   k_init_scalars<<<1, NT, 0, s>>>(kr.scal, kr.flag, kr.part, NBLK, o.rtol, o.max_it, 0);
   if (o.use_x0) {
-    spmv_any(h, x, kr.q, nullptr, nullptr, false, s);
+    spmv_any(h, x, kr.q, s);
     k_axpby<<<vgrid(n), NT, 0, s>>>(n, kr.r, b, kr.q, -1.0);
   } else {
     CK(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
@@ -300,7 +284,7 @@ void solve_pcg(Handle& h, const double* b, double* x, const asm_solve_opts& o, a
   CK(cudaEventDestroy(ej));
   CK(cudaEventRecord(e1, s));
   // true residual
-  spmv_any(h, x, kr.q, nullptr, nullptr, false, s);
+  spmv_any(h, x, kr.q, s);
   k_axpby<<<vgrid(n), NT, 0, s>>>(n, kr.w, b, kr.q, -1.0);
   k_dot<<<vg, NT, 0, s>>>(n, kr.w, kr.w, kr.part, nullptr);
   double sc[S_NSCAL];
@@ -469,7 +453,7 @@ void solve_fgmres(Handle& h, const double* b, double* x, const asm_solve_opts& o
   bool done = false;
   while (!done) {
     // restart: r = b - A x, beta, v_0, g = beta e_1
-    spmv_any(h, x, kr.q, nullptr, nullptr, false, s);
+    spmv_any(h, x, kr.q, s);
     k_axpby<<<vgrid(n), NT, 0, s>>>(n, kr.r, b, kr.q, -1.0);
     k_dot<<<vg, NT, 0, s>>>(n, kr.r, kr.r, kr.part, nullptr);
     CK(cudaMemsetAsync(g, 0, sizeof(double) * ldh, s));
@@ -480,7 +464,7 @@ void solve_fgmres(Handle& h, const double* b, double* x, const asm_solve_opts& o
       double* zj = kr.ZB + (int64_t)j * n;
       double* col = H + (int64_t)j * ldh;
       apply_preconditioner(h, vj, zj, s, nullptr);
-      spmv_any(h, zj, tmp, nullptr, nullptr, false, s);
+      spmv_any(h, zj, tmp, s);
       // classical Gram-Schmidt, twice
       k_multidot<<<vg, NT, 0, s>>>(n, kr.V, j + 1, tmp, kr.mpart);
       k_multidot_fin<<<1, NT, 0, s>>>(kr.mpart, NBLK, j + 1, col);
@@ -511,7 +495,7 @@ void solve_fgmres(Handle& h, const double* b, double* x, const asm_solve_opts& o
   }
   CK(cudaEventRecord(e1, s));
   // true residual
-  spmv_any(h, x, kr.q, nullptr, nullptr, false, s);
+  spmv_any(h, x, kr.q, s);
   k_axpby<<<vgrid(n), NT, 0, s>>>(n, kr.w, b, kr.q, -1.0);
   k_dot<<<vg, NT, 0, s>>>(n, kr.w, kr.w, kr.part, nullptr);
   double sc[S_NSCAL];
