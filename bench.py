@@ -228,6 +228,17 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
+def max_over_ranks(v: float, dist, device) -> float:
+    """Largest value of v over the ranks of the process group (v itself
+    without one): replicas are timed by the slowest."""
+    if dist is None:
+        return v
+    import torch
+    t = torch.tensor([v], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def train_warm_net(P, torch, n_instances: int, steps: int):
     """Train the warm-start network on subdomains of generated 3D diffusion
     instances (cube sides 24..48, contrast 1e2..1e6; generator seeds
@@ -389,10 +400,7 @@ def run_ours(args):
     clocks = sampler.stop()
     # launches of the timed steps only (the last handle's destroy launches nothing)
     launches = int(l1 - l0)
-    if dist:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, dev)
     setup_info = P.asm_get_info(h_last)
     stages = {n: round(setup_info.stage_ms[i], 3) for i, n in enumerate(P.stage_names()) if n}
 
@@ -460,10 +468,7 @@ def run_ours(args):
         te = (time.perf_counter() - t0) / n_e2e
         h2d = 4 * (prob.n + 1) + 12 * prob.nnz + 4 * prob.n + 8 * prob.n
         e2e = {"value": te, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(8 * prob.n)}
-        if dist:
-            t = torch.tensor([te], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e["value"] = float(t.item())
+        e2e["value"] = max_over_ranks(te, dist, dev)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
