@@ -187,6 +187,46 @@ def test_one_subdomain_gives_exact_inverse(P):
     pre.close()
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_tiny_ragged_problem(P, prec):
+    """7 x 5 grid in 3 x 2 uneven boxes (n = 35, subdomains of 4..9 nodes,
+    one tile each, nev larger than some interfaces): same overlap, local
+    values and iteration count as the oracle, solution to 1e-8."""
+    prob = poisson2d(7, 5, 3, 2, nev=3)
+    A = prob.csr()
+    st = O.setup(A, prob.part, prob.N, 1, prob.nev)
+    pre = make(P, A, prob.part, prob.N, 1, prob.nev, precision=prec,
+               **({"eig_tol": 1e-11, "max_sweeps": 200} if prec == "fp64" else {}))
+    check_overlap(P, pre.h, O.overlap(A, prob.part, prob.N, 1))
+    vals, cnt = P.asm_get_local_values(pre.h)
+    for i, loc in enumerate(st.locals):
+        k = len(loc.values)
+        assert cnt[i] == k
+        np.testing.assert_allclose(vals[i, :k], loc.values, rtol=1e-9 if prec == "fp64" else 1e-4)
+    ref = O.solve(st, prob.b)
+    x, info = pre.solve(torch.as_tensor(prob.b, device="cuda"))
+    rel = np.linalg.norm(prob.b - A @ x.cpu().numpy()) / np.linalg.norm(prob.b)
+    assert info.converged and rel <= 1.5e-8
+    assert abs(info.iterations - ref.iterations) <= 1
+    pre.close()
+
+
+def test_solve_is_bitwise_reproducible(P):
+    """Every reduction of the setup and the solve runs in a fixed order: two
+    setups and solves of the same system give identical bits."""
+    prob = diffusion3d(24, (3, 3, 3), contrast=1e6, nev=8)
+    A = prob.csr()
+    out = []
+    for _ in range(2):
+        pre = make(P, A, prob.part, prob.N, 1, 8, precision="fp32")
+        x, info = pre.solve(torch.as_tensor(prob.b, device="cuda"))
+        out.append((x.cpu().numpy(), info.iterations, P.asm_get_local_values(pre.h)[0]))
+        pre.close()
+    assert out[0][1] == out[1][1]
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][2], out[1][2])
+
+
 # ---------------------------------------------------------------------------
 # FP32 path
 # ---------------------------------------------------------------------------
