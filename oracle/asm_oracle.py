@@ -16,6 +16,9 @@ two-level Schwarz preconditioner for sparse matrices") in its own notation:
   (eq. gevpsvd) and the coarse space of eq. coarse_space_2.
 * Section 4.1: coarse operator A_00 = R_0 A R_0^T (the coarse matrix E).
 * Remark in Section 4.3: M_2^{-1} = sum_{i=0}^N R_i^T A_ii^{-1} R_i.
+* Section 2.3 / Section 6: restricted ASM (eq. onelevelras) and the deflated
+  coarse correction that the experiments combine it with (a reading: the
+  formula is in the paper's PCHPDDM reference, not in the paper).
 * Section 6: the nonsymmetric variant keeps left singular vectors of
   D_i Pi_i (Euclidean) and drops eq. uppergevp.
 * Theorems 4.5 / 5.3 (labels th:upper_bound_1, th:upper_bound_2): the
@@ -265,6 +268,29 @@ class OracleSetup:
         """M_2^{-1} r = sum_{i=0}^N R_i^T A_ii^{-1} R_i r (Remark, Section 4.3)."""
         return self.apply_one_level(r) + self.apply_coarse(r)
 
+    def apply_one_level_ras(self, r: np.ndarray) -> np.ndarray:
+        """sum_i R_i^T D_i A_ii^{-1} R_i r (eq. onelevelras, Boolean D_i)."""
+        z = np.zeros_like(r)
+        for loc, f in zip(self.locals, self.factors):
+            y = _local_solve(f, r[loc.ov.omega], self.spd)
+            np.add.at(z, loc.ov.omega, pou(loc.ov) * y)
+        return z
+
+    def apply_variant(self, r: np.ndarray, one_level: str = "asm", coarse: str = "additive") -> np.ndarray:
+        """The apply with either one-level part and either coarse correction.
+
+        one_level: "asm" (eq. onelevelasm) or "ras" (eq. onelevelras).
+        coarse: "additive" (the Remark of Section 4.3: M_1^{-1} r + Q r) or
+        "deflated", the combination the experiments of Section 6 use.  The
+        paper takes the deflated form from its PCHPDDM reference without
+        printing it; reading: M^{-1} r = Q r + M_1^{-1} (r - A Q r) with
+        Q = Z E^{-1} Z^T, so that M^{-1} A Z = Z."""
+        one = self.apply_one_level_ras if one_level == "ras" else self.apply_one_level
+        if coarse == "deflated":
+            q = self.apply_coarse(r)
+            return q + one(r - self.A @ q)
+        return one(r) + self.apply_coarse(r)
+
 
 def _local_solve(f, x, spd):
     return sla.cho_solve(f, x) if spd else sla.lu_solve(f, x)
@@ -452,10 +478,13 @@ def fgmres(A, b, apply, restart: int = 30, rtol: float = 1e-8, maxit: int = 1000
 
 
 def solve(st: OracleSetup, b: np.ndarray, rtol: float = 1e-8, maxit: int = 1000,
-          restart: int = 30) -> SolveResult:
-    if st.spd:
+          restart: int = 30, one_level: str = "asm", coarse: str = "additive") -> SolveResult:
+    """PCG for SPD A with the additive ASM preconditioner (symmetric);
+    right-preconditioned FGMRES otherwise, as with RAS or the deflated
+    correction, which are not symmetric (Section 6)."""
+    if st.spd and one_level == "asm" and coarse == "additive":
         return pcg(st.A, b, st.apply, rtol, maxit)
-    return fgmres(st.A, b, st.apply, restart, rtol, maxit)
+    return fgmres(st.A, b, lambda r: st.apply_variant(r, one_level, coarse), restart, rtol, maxit)
 
 
 # ---------------------------------------------------------------------------
