@@ -428,9 +428,9 @@ def run_ours(args):
     # ---- the other forms on the same GPU: plain FP64, FP32 with the randomized start
     forms = None
     if not args.no_forms:
-        def time_form(o, n_steps=2):
+        def time_form(o, n_steps=2, so=sopt):
             hh = P.asm_setup(rp, ci, va, pa, prob.N, prob.delta, prob.nev, o, stream, True)
-            P.asm_solve(hh, b, x, sopt, stream)
+            P.asm_solve(hh, b, x, so, stream)
             P.asm_destroy(hh)
             torch.cuda.synchronize()
             f0 = torch.cuda.Event(enable_timing=True)
@@ -439,13 +439,19 @@ def run_ours(args):
             its = 0
             for _ in range(n_steps):
                 hh = P.asm_setup(rp, ci, va, pa, prob.N, prob.delta, prob.nev, o, stream, True)
-                its = P.asm_solve(hh, b, x, sopt, stream).iterations
+                its = P.asm_solve(hh, b, x, so, stream).iterations
                 P.asm_destroy(hh)
             f1.record(stream)
             torch.cuda.synchronize()
             return {"s_per_step": f0.elapsed_time(f1) / n_steps / 1e3, "iterations": its}
         forms = {"fp64_random": time_form(P.default_options(local_precision=P.PREC_FP64)),
                  "fp32_random": time_form(P.default_options(local_precision=P.PREC_FP32))}
+        # the combination of the paper's experiments: restricted one-level part,
+        # deflated coarse correction, right-preconditioned GMRES without restart
+        # (FGMRES with a 512-vector basis)
+        so_ras = P.default_solve_opts(rtol=1e-8, max_it=5000, restart=512)
+        forms["fp32_ras_deflated_gmres"] = time_form(
+            P.default_options(local_precision=P.PREC_FP32, one_level=1, coarse_mode=1), so=so_ras)
         if net:
             forms["fp32_learned"] = {"s_per_step": ms / 1e3, "iterations": infos[-1].iterations}
         forms["this_line"] = ("fp32" if args.precision == "fp32" else "fp64") + ("_learned" if net else "_random")

@@ -87,14 +87,23 @@ typedef struct {
                                3 in FP32)                                      */
   int32_t record_warm;      /* 1 (SPD only): keep the network inputs and the
                                converged start blocks for asm_get_warm_data   */
-  int32_t reserved[3];
+  int32_t one_level;        /* 0: additive ASM (eq. onelevelasm); 1: restricted
+                               ASM (eq. onelevelras, Boolean D_i: each node takes
+                               the local solution of its owner)              */
+  int32_t coarse_mode;      /* 0: additive coarse correction (Remark, Section
+                               4.3); 1: deflated, M^{-1} r = Q r + M_1^{-1}
+                               (r - A Q r), Q = Z E^{-1} Z^T, the combination of
+                               the Section 6 experiments (with one_level = 1)  */
+  int32_t reserved[1];
   asm_mlp* warm_net;        /* network for warm_start (borrowed: must stay
                                alive and unused elsewhere during asm_setup)    */
 } asm_options;
 
 typedef struct {
-  int32_t method;           /* 0: PCG if spd else FGMRES; 1: PCG; 2: FGMRES    */
-  int32_t restart;          /* FGMRES restart length (default 30)              */
+  int32_t method;           /* 0: PCG for SPD A with the symmetric apply
+                               (one_level 0, coarse_mode 0), else FGMRES;
+                               1: PCG; 2: FGMRES                               */
+  int32_t restart;          /* FGMRES restart length (default 30, at most 512)  */
   double rtol;              /* stop at ||b - A x||_2 / ||b||_2 <= rtol         */
   int32_t max_it;           /* iteration cap                                   */
   int32_t use_x0;           /* 1: x holds the initial guess; 0: x0 = 0         */

@@ -39,7 +39,8 @@ class asm_options(C.Structure):
                 ("max_sweeps", C.c_int32), ("eig_tol", C.c_double), ("nu", C.c_double),
                 ("nev_lift", C.c_int32), ("coarse", C.c_int32), ("seed", C.c_uint64),
                 ("warm_start", C.c_int32), ("filter_degree", C.c_int32), ("record_warm", C.c_int32),
-                ("reserved", C.c_int32 * 3), ("warm_net", C.c_void_p)]
+                ("one_level", C.c_int32), ("coarse_mode", C.c_int32),
+                ("reserved", C.c_int32 * 1), ("warm_net", C.c_void_p)]
 
 
 class asm_solve_opts(C.Structure):

@@ -321,8 +321,13 @@ __global__ void __launch_bounds__(NT) k_coarse_restrict(const ZT* __restrict__ Z
 
 // z[v] = s_v * sum over the occurrences (i, a) of v of y_pos[(i, a)]
 //        + Z_{part v}[own position] . y_coarse   (fixed order, no atomics)
+// Restricted one-level part (ras): only the occurrence of v in its owner's
+// I block, i.e. R_i^T D_i with the Boolean D_i.  Deflated form: qadd (= Q r)
+// is added in place of the coarse term; with ypos == nullptr the kernel
+// computes the prolongation Z y_coarse alone.
 template <typename ZT>
-__global__ void __launch_bounds__(NT) k_apply_pull(int n, const int32_t* __restrict__ occ_ptr,
+__global__ void __launch_bounds__(NT) k_apply_pull(int n, int ras, const double* __restrict__ qadd,
+                                                   const int32_t* __restrict__ occ_ptr,
                                                    const int32_t* __restrict__ occ_pos,
                                                    const double* __restrict__ ypos, const int32_t* __restrict__ part,
                                                    const int32_t* __restrict__ own_pos,
@@ -337,8 +342,13 @@ __global__ void __launch_bounds__(NT) k_apply_pull(int n, const int32_t* __restr
   double rz = 0;
   for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
     double acc = 0;
-    for (int t = occ_ptr[v]; t < occ_ptr[v + 1]; ++t) acc += ypos[occ_pos[t]];
-    acc *= ds[v];
+    if (ypos != nullptr) {
+      if (ras) acc = ypos[own_pos[v]];
+      else
+        for (int t = occ_ptr[v]; t < occ_ptr[v + 1]; ++t) acc += ypos[occ_pos[t]];
+      acc *= ds[v];
+    }
+    if (qadd != nullptr) acc += qadd[v];
     if (yc != nullptr) {
       int i = part[v];
       int k = count[i];
@@ -447,18 +457,22 @@ const double* apply_coarse(Handle& h, const double* r, cudaStream_t s, const int
   return y;
 }
 
+// z from the local solutions (local = false: none) plus the coarse term Z yc
+// (yc != nullptr) or a vector qadd (the deflated form's Q r)
 template <typename T>
 void apply_pull(Handle& h, const double* yc, double* z, cudaStream_t s, const int32_t* done,
-                const ApplyDot* dot = nullptr) {
+                const ApplyDot* dot = nullptr, bool local = true, const double* qadd = nullptr) {
   Dense& dn = h.dn;
   Coarse& co = h.co;
+  const int ras = h.opt.one_level == 1;
+  const double* yp = local ? dn.ypos : nullptr;
   unsigned gp = (unsigned)std::min<int64_t>(ceil_div(h.n, NT), 152 * 16);
   if (co.Zf)
-    k_apply_pull<float><<<gp, NT, 0, s>>>(h.n, h.ov.occ_ptr, h.ov.occ_pos, dn.ypos, h.part, h.ov.own_pos,
+    k_apply_pull<float><<<gp, NT, 0, s>>>(h.n, ras, qadd, h.ov.occ_ptr, h.ov.occ_pos, yp, h.part, h.ov.own_pos,
                                           h.ov.sub_off, co.Zf, co.z_off, co.count, co.col_off, h.nev, yc, h.dscale,
                                           z, done, dot ? *dot : ApplyDot());
   else
-    k_apply_pull<double><<<gp, NT, 0, s>>>(h.n, h.ov.occ_ptr, h.ov.occ_pos, dn.ypos, h.part, h.ov.own_pos,
+    k_apply_pull<double><<<gp, NT, 0, s>>>(h.n, ras, qadd, h.ov.occ_ptr, h.ov.occ_pos, yp, h.part, h.ov.own_pos,
                                            h.ov.sub_off, co.Z, co.z_off, co.count, co.col_off, h.nev, yc, h.dscale,
                                            z, done, dot ? *dot : ApplyDot());
 }
@@ -469,6 +483,16 @@ void apply_pull(Handle& h, const double* yc, double* z, cudaStream_t s, const in
 template <typename T>
 void apply_impl(Handle& h, const double* r, double* z, cudaStream_t s, const int32_t* done,
                 const ApplyDot* dot = nullptr) {
+  if (h.opt.coarse_mode == 1 && h.co.n_C > 0) {
+    // deflated: q = Q r, w = r - A q, z = q + M_1^{-1} w (one stream: each
+    // step needs the previous one)
+    const double* yq = apply_coarse(h, r, s, done);
+    apply_pull<T>(h, yq, h.defl_q, s, done, nullptr, false);
+    residual(h, r, h.defl_q, h.defl_w, s, done);
+    apply_local<T>(h, h.defl_w, s, done);
+    apply_pull<T>(h, nullptr, z, s, done, dot, true, h.defl_q);
+    return;
+  }
   const double* yc = nullptr;
   const bool fork = h.co.n_C > 0 && h.side != nullptr;
   if (fork) {

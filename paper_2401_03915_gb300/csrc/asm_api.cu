@@ -146,6 +146,8 @@ asm_status asm_setup(const asm_csr* A, const int32_t* part, int32_t N, int32_t o
   if (o.oversample < 0 || o.oversample > 64) return set_error(ASM_ERR_INVALID_ARG, "oversample must be in 0..64");
   if (o.warm_start && (!o.warm_net || !o.spd))
     return set_error(ASM_ERR_INVALID_ARG, "warm_start needs warm_net and the SPD method");
+  if (o.one_level != 0 && o.one_level != 1) return set_error(ASM_ERR_INVALID_ARG, "one_level must be 0 or 1");
+  if (o.coarse_mode != 0 && o.coarse_mode != 1) return set_error(ASM_ERR_INVALID_ARG, "coarse_mode must be 0 or 1");
   asm_handle* H = new (std::nothrow) asm_handle();
   if (!H) return set_error(ASM_ERR_OOM, "host allocation failed");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -197,6 +199,10 @@ asm_status asm_setup(const asm_csr* A, const int32_t* part, int32_t N, int32_t o
     CK(cudaEventRecord(h.ev[7], s));
     build_coarse(h, s);
     CK(cudaEventRecord(h.ev[8], s));
+    if (h.opt.coarse_mode == 1 && h.co.n_C > 0) {
+      h.defl_q = h.mem.alloc<double>(h.n);
+      h.defl_w = h.mem.alloc<double>(h.n);
+    }
     tune_apply(h, s);
     CK(cudaStreamSynchronize(s));
     // info
@@ -281,7 +287,10 @@ asm_status asm_solve(asm_handle* H, const double* b, double* x, const asm_solve_
       CK(cudaMemcpyAsync(h.kr.bx, b, sizeof(double) * h.n, cudaMemcpyHostToDevice, s));
       if (so.use_x0) CK(cudaMemcpyAsync(dx, x, sizeof(double) * h.n, cudaMemcpyHostToDevice, s));
     }
-    int method = so.method ? so.method : (h.opt.spd ? 1 : 2);
+    // PCG needs a symmetric preconditioner: the additive ASM with the additive
+    // coarse correction; the restricted or deflated forms go to FGMRES
+    const bool symmetric = h.opt.spd && h.opt.one_level == 0 && (h.opt.coarse_mode == 0 || h.co.n_C == 0);
+    int method = so.method ? so.method : (symmetric ? 1 : 2);
     if (method == 1) solve_pcg(h, db, dx, so, *info, s);
     else solve_fgmres(h, db, dx, so, *info, s);
     check_device_error(h, s, "solve");

@@ -116,6 +116,7 @@ struct Handle {
   double* val = nullptr;
   int32_t *dev_n = nullptr, *dev_m = nullptr, *dev_p = nullptr;  // |Omega_i|, |Omega_{1:d-1}|, |I_i|
   double* dscale = nullptr;         // 1/sqrt(|A_vv|): symmetric diagonal scaling of every A_ii
+  double *defl_q = nullptr, *defl_w = nullptr;  // deflated apply: Q r and r - A Q r (n each)
   // learned warm start (SPD path): one row per Gamma_delta node, subdomain i
   // owning rows h_wseg[i] .. h_wseg[i+1]-1
   int64_t warm_rows = 0;
@@ -156,6 +157,8 @@ void apply_preconditioner(Handle& h, const double* r, double* z, cudaStream_t s,
 void time_apply(Handle& h, const double* r, double* z, int iters, cudaStream_t s, double* ms);
 void tune_apply(Handle& h, cudaStream_t s);                                       // apply.cu
 void spmv(Handle& h, const double* x, double* y, cudaStream_t s);                 // krylov.cu
+// y = b - A x (krylov.cu); nothing when *done is set
+void residual(Handle& h, const double* b, const double* x, double* y, cudaStream_t s, const int32_t* done);
 void coarse_solve(Handle& h, const double* c, double* y, cudaStream_t s,
                   const int32_t* done = nullptr);                                 // coarse.cu
 void solve_pcg(Handle& h, const double* b, double* x, const asm_solve_opts& o, asm_solve_info& info,

@@ -22,11 +22,14 @@ enum Scal { S_RZ = 0, S_PQ, S_ALPHA, S_BETA, S_RR, S_BNORM, S_RTOL, S_RELRES, S_
 enum Flag { F_DONE = 0, F_IT, F_MAXIT, F_NFLAG = 4 };
 
 // vector-per-row CSR SpMV with VW lanes per row.
+// y = A x, or y = b - A x when b is given
 template <int VW>
 __global__ void __launch_bounds__(NT) k_spmv(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                                              const double* __restrict__ val, const double* __restrict__ x,
-                                             double* __restrict__ y) {
+                                             double* __restrict__ y, const double* __restrict__ b,
+                                             const int32_t* __restrict__ done) {
   COUNT_LAUNCH();
+  if (done != nullptr && *done) return;
   const int lane = threadIdx.x % VW;
   const int rows_per_block = NT / VW;
   for (int base = blockIdx.x * rows_per_block; base < n; base += gridDim.x * rows_per_block) {
@@ -38,7 +41,7 @@ __global__ void __launch_bounds__(NT) k_spmv(int n, const int32_t* __restrict__ 
     }
 #pragma unroll
     for (int o = VW / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (r < n && lane == 0) y[r] = acc;
+    if (r < n && lane == 0) y[r] = b != nullptr ? b[r] - acc : acc;
   }
 }
 
@@ -163,18 +166,19 @@ __global__ void k_init_scalars(double* scal, int32_t* flag, const double* part, 
 inline unsigned vgrid(int n) { return (unsigned)std::min<int64_t>(ceil_div(n, NT), NBLK); }
 
 template <int VW>
-void spmv_launch(Handle& h, const double* x, double* y, cudaStream_t s) {
+void spmv_launch(Handle& h, const double* x, double* y, cudaStream_t s, const double* b, const int32_t* done) {
   const int rows = NT / VW;
   const unsigned g = (unsigned)std::min<int64_t>(ceil_div(h.n, rows), RBLK);
-  k_spmv<VW><<<g, NT, 0, s>>>(h.n, h.row_ptr, h.col_idx, h.val, x, y);
+  k_spmv<VW><<<g, NT, 0, s>>>(h.n, h.row_ptr, h.col_idx, h.val, x, y, b, done);
 }
 
-void spmv_any(Handle& h, const double* x, double* y, cudaStream_t s) {
+void spmv_any(Handle& h, const double* x, double* y, cudaStream_t s, const double* b = nullptr,
+              const int32_t* done = nullptr) {
   double avg = h.n ? (double)h.nnz / h.n : 1;
-  if (avg <= 6) spmv_launch<4>(h, x, y, s);
-  else if (avg <= 12) spmv_launch<8>(h, x, y, s);
-  else if (avg <= 24) spmv_launch<16>(h, x, y, s);
-  else spmv_launch<32>(h, x, y, s);
+  if (avg <= 6) spmv_launch<4>(h, x, y, s, b, done);
+  else if (avg <= 12) spmv_launch<8>(h, x, y, s, b, done);
+  else if (avg <= 24) spmv_launch<16>(h, x, y, s, b, done);
+  else spmv_launch<32>(h, x, y, s, b, done);
 }
 
 void ensure_krylov(Handle& h, cudaStream_t s) {
@@ -202,6 +206,10 @@ void ensure_krylov(Handle& h, cudaStream_t s) {
 void spmv(Handle& h, const double* x, double* y, cudaStream_t s) {
   spmv_any(h, x, y, s);
   CK_LAUNCH("spmv");
+}
+
+void residual(Handle& h, const double* b, const double* x, double* y, cudaStream_t s, const int32_t* done) {
+  spmv_any(h, x, y, s, b, done);
 }
 
 void solve_pcg(Handle& h, const double* b, double* x, const asm_solve_opts& o, asm_solve_info& info,
@@ -309,34 +317,44 @@ void solve_pcg(Handle& h, const double* b, double* x, const asm_solve_opts& o, a
 
 namespace {
 
-constexpr int MAXV = 65;  // restart length + 1
+constexpr int MAXV = 513;  // restart length + 1 (512: GMRES without restart for up to 512 iterations)
 
-// part[b * MAXV + k] = partial sums of V_k . w over the block's rows, k < nvec
-__global__ void __launch_bounds__(NT) k_multidot(int n, const double* __restrict__ V, int nvec,
+// V^T w for the n x nvec basis V (vectors n apart) as a tall-skinny product:
+// block b owns rows [b*rows, (b+1)*rows), warp k%8 of it the vectors
+// k = wid, wid+8, ...; part[b * MAXV + k] = that chunk of V_k . w.  No block
+// reduction per vector: every vector's chunk is one warp's lane-strided sum.
+constexpr int MD_MAXB = 2048;  // blocks (row chunks) of the multi-dot at most
+__global__ void __launch_bounds__(NT) k_multidot(int n, int rows, const double* __restrict__ V, int nvec,
                                                  const double* __restrict__ w, double* __restrict__ part) {
   COUNT_LAUNCH();
-  __shared__ double red[NT / 32];
-  for (int k = 0; k < nvec; ++k) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int r0 = blockIdx.x * rows;
+  const int r1 = min(n, r0 + rows);
+  for (int k = wid; k < nvec; k += NT / 32) {
     const double* v = V + (int64_t)k * n;
     double s = 0;
-    for (int i = blockIdx.x * NT + threadIdx.x; i < n; i += gridDim.x * NT) s += v[i] * w[i];
-    s = block_sum(s, red);
-    if (threadIdx.x == 0) part[blockIdx.x * MAXV + k] = s;
+    for (int i = r0 + lane; i < r1; i += 32) s += v[i] * w[i];
+    s = warp_sum(s);
+    if (lane == 0) part[blockIdx.x * MAXV + k] = s;
   }
 }
 
-// out[k] = sum_b part[b * MAXV + k] (fixed order)
+// out[k] = sum_b part[b * MAXV + k], one warp per k (fixed order)
 __global__ void __launch_bounds__(NT) k_multidot_fin(const double* __restrict__ part, int nb, int nvec,
                                                      double* __restrict__ out) {
   COUNT_LAUNCH();
-  __shared__ double red[NT / 32];
-  for (int k = 0; k < nvec; ++k) {
-    double s = 0;
-    for (int b = threadIdx.x; b < nb; b += NT) s += part[b * MAXV + k];
-    s = block_sum(s, red);
-    if (threadIdx.x == 0) out[k] = s;
-  }
+  const int lane = threadIdx.x & 31;
+  const int k = blockIdx.x * (NT / 32) + (threadIdx.x >> 5);
+  if (k >= nvec) return;
+  double s = 0;
+  for (int b = lane; b < nb; b += 32) s += part[b * MAXV + k];
+  s = warp_sum(s);
+  if (lane == 0) out[k] = s;
 }
+
+// row chunks of the multi-dot: about 512 rows each, at most MD_MAXB chunks
+inline int md_rows(int n) { return (int)std::max<int64_t>(512, ceil_div(n, MD_MAXB)); }
+inline int md_blocks(int n) { return (int)std::max<int64_t>(1, ceil_div(n, md_rows(n))); }
 
 // w -= sum_k V_k c_k
 __global__ void __launch_bounds__(NT) k_sub_vc(int n, const double* __restrict__ V, int nvec,
@@ -430,7 +448,7 @@ void solve_fgmres(Handle& h, const double* b, double* x, const asm_solve_opts& o
     kr.V = mem.alloc<double>((int64_t)(m + 1) * n);
     kr.ZB = mem.alloc<double>((int64_t)m * n);
     kr.H = mem.alloc<double>((int64_t)ldh * m + 4 * ldh + 16);
-    kr.mpart = mem.alloc<double>((int64_t)NBLK * MAXV);
+    kr.mpart = mem.alloc<double>((int64_t)MD_MAXB * MAXV);
     kr.restart = m;
   }
   double* H = kr.H;
@@ -440,6 +458,8 @@ void solve_fgmres(Handle& h, const double* b, double* x, const asm_solve_opts& o
   double* y = g + ldh;
   double* tmp = kr.w;  // n
   const unsigned vg = NBLK;
+  const int mdr = md_rows(n);
+  const unsigned mdb = (unsigned)md_blocks(n);
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
@@ -466,11 +486,12 @@ void solve_fgmres(Handle& h, const double* b, double* x, const asm_solve_opts& o
       apply_preconditioner(h, vj, zj, s, nullptr);
       spmv_any(h, zj, tmp, s);
       // classical Gram-Schmidt, twice
-      k_multidot<<<vg, NT, 0, s>>>(n, kr.V, j + 1, tmp, kr.mpart);
-      k_multidot_fin<<<1, NT, 0, s>>>(kr.mpart, NBLK, j + 1, col);
+      const unsigned fb = (unsigned)ceil_div(j + 1, NT / 32);
+      k_multidot<<<mdb, NT, 0, s>>>(n, mdr, kr.V, j + 1, tmp, kr.mpart);
+      k_multidot_fin<<<fb, NT, 0, s>>>(kr.mpart, mdb, j + 1, col);
       k_sub_vc<<<vgrid(n), NT, 0, s>>>(n, kr.V, j + 1, col, tmp);
-      k_multidot<<<vg, NT, 0, s>>>(n, kr.V, j + 1, tmp, kr.mpart);
-      k_multidot_fin<<<1, NT, 0, s>>>(kr.mpart, NBLK, j + 1, y);
+      k_multidot<<<mdb, NT, 0, s>>>(n, mdr, kr.V, j + 1, tmp, kr.mpart);
+      k_multidot_fin<<<fb, NT, 0, s>>>(kr.mpart, mdb, j + 1, y);
       k_sub_vc<<<vgrid(n), NT, 0, s>>>(n, kr.V, j + 1, y, tmp);
       k_axpby<<<1, NT, 0, s>>>(j + 1, col, col, y, 1.0);
       k_dot<<<vg, NT, 0, s>>>(n, tmp, tmp, kr.part, nullptr);
