@@ -296,26 +296,35 @@ def _local_solve(f, x, spd):
     return sla.cho_solve(f, x) if spd else sla.lu_solve(f, x)
 
 
-def select_count(values: np.ndarray, nev: int) -> int:
-    """Reading of the selection rule: the paper keeps eigenvalues above tau^2
-    (or singular values above tau); a fixed count nev is used instead, capped
-    at the number of numerically nonzero values."""
+def select_count(values: np.ndarray, nev: int, threshold: float | None = None) -> int:
+    """How many of the descending ``values`` enter the coarse space.
+
+    The paper keeps the eigenvalues of eq. gevpsvd above tau^2 (Prop. 5.1),
+    or the singular values of D_i Pi_i above tau (Section 5.2).  With
+    ``threshold`` (tau^2, or tau) given that rule is applied; ``nev`` caps the
+    count either way (reading: a fixed count when no threshold is given), and
+    numerically zero values are never kept."""
     if values.size == 0 or nev <= 0:
         return 0
     vmax = max(float(values[0]), 0.0)
     nz = int(np.count_nonzero(values > RANK_TOL * vmax)) if vmax > 0 else 0
-    return min(nev, nz)
+    k = min(nev, nz)
+    if threshold is not None:
+        k = min(k, int(np.count_nonzero(values > threshold)))
+    return k
 
 
 def setup(A: sp.spmatrix, part: np.ndarray, N: int, delta: int, nev: int, spd: bool = True,
           nu: float | None = None, nev_lift: int | None = None,
-          subdomains: list | None = None) -> OracleSetup:
+          subdomains: list | None = None, tau: float | None = None) -> OracleSetup:
     """Build the two-level preconditioner.
 
     SPD: per subdomain the top ``nev`` eigenvectors of eq. gevpsvd, mapped by
     D_i Pi_i, and, if ``nu`` is given, the eigenvectors of eq. uppergevp with
     lambda > nu (at most ``nev_lift``), mapped by D_i.  General A: the top
-    ``nev`` left singular vectors of D_i Pi_i (Section 6).  The coarse operator
+    ``nev`` left singular vectors of D_i Pi_i (Section 6).  With ``tau``, only
+    eigenvalues above tau^2 (singular values above tau) are kept, at most
+    ``nev`` of them (Prop. 5.1, Section 5.2).  The coarse operator
     is E = Z^T A Z, Cholesky-factored (SPD) or LU-factored (general)."""
     A = sp.csr_matrix(A)
     n = A.shape[0]
@@ -334,7 +343,7 @@ def setup(A: sp.spmatrix, part: np.ndarray, N: int, delta: int, nev: int, spd: b
             except np.linalg.LinAlgError as e:
                 raise OracleError(f"A_ii of subdomain {i} is not SPD") from e
             mu, W, Pi = gevp_svd(Aii, ov)
-            k = select_count(mu, nev)
+            k = select_count(mu, nev, None if tau is None else tau * tau)
             blocks = [(d[:, None] * (Pi @ W[:, :k]))]
             lift = np.zeros(0)
             if nu is not None:
@@ -349,7 +358,7 @@ def setup(A: sp.spmatrix, part: np.ndarray, N: int, delta: int, nev: int, spd: b
         else:
             factors.append(sla.lu_factor(Aii))
             s, U, Pi = svd_dpi(Aii, ov)
-            k = select_count(s, nev)
+            k = select_count(s, nev, tau)
             Bi = d[:, None] * U[:, :k]
             mu, lift, vals_i = s, np.zeros(0), s[:k]
         basis = Bi[:ov.p]

@@ -82,3 +82,45 @@ def test_ras_deflated_fgmres_matches_direct(spd):
     # two-level beats one-level RAS on the same Krylov method
     one = O.fgmres(A, p.b, st.apply_one_level_ras)
     assert res.iterations < one.iterations
+
+
+# ---------------------------------------------------------------------------
+# selection by the threshold tau (Prop. 5.1: eigenvalues above tau^2;
+# Section 5.2: singular values above tau)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("tau", [0.3, 0.6])
+def test_threshold_selection_satisfies_theorem2(tau):
+    # nev large enough that the threshold alone decides: Theorem 5.3 then
+    # holds with the prescribed tau (not an effective one)
+    p = poisson2d(16, 16, 2, 2)
+    A = p.csr()
+    st = O.setup(A, p.part, p.N, 1, 64, tau=tau)
+    for loc in st.locals:
+        k = len(loc.values)
+        assert np.all(loc.all_values[:k] > tau * tau)
+        assert k == len(loc.all_values) or loc.all_values[k] <= tau * tau
+    ovs = [l.ov for l in st.locals]
+    kc = O.color_count(ovs)
+    lam_s = O.lambda_star(A, ovs)
+    nu_eff = max(O.lifting_gevp(O.local_matrix(A, ov), ov)[0][0] for ov in ovs)
+    assert 1.0 <= O.condition_number(st) <= O.bound_thm2(kc, nu_eff, lam_s, tau)
+
+
+def test_threshold_selection_general_path():
+    p = convdiff2d(32, (2, 2), peclet=1e2, delta=2, nev=64)
+    A = p.csr()
+    tau = 0.5
+    st = O.setup(A, p.part, p.N, 2, 64, spd=False, tau=tau)
+    for loc in st.locals:
+        k = len(loc.values)
+        assert np.all(loc.all_values[:k] > tau)
+        assert k == len(loc.all_values) or loc.all_values[k] <= tau
+
+
+def test_more_overlap_contributes_fewer_vectors_at_fixed_tau():
+    # Section 6 (discussion of Fig. 1): for a fixed tau, more overlap layers
+    # decrease the number of vectors each subdomain contributes
+    p = poisson2d(48, 48, 3, 3)
+    A = p.csr()
+    sizes = [O.setup(A, p.part, p.N, d, 200, tau=0.25).n_C for d in (1, 2, 3)]
+    assert sizes[0] > sizes[1] > sizes[2] > 0, sizes
