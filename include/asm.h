@@ -95,6 +95,10 @@ typedef struct {
                                (r - A Q r), Q = Z E^{-1} Z^T, the combination of
                                the Section 6 experiments (with one_level = 1)  */
   int32_t reserved[1];
+  double tau;               /* > 0: keep only the eigenvalues of eq. gevpsvd
+                               above tau^2 (Prop. 5.1), or the singular values
+                               of D_i Pi_i above tau (general method), at most
+                               nev per subdomain; 0: the top nev             */
   asm_mlp* warm_net;        /* network for warm_start (borrowed: must stay
                                alive and unused elsewhere during asm_setup)    */
 } asm_options;

@@ -40,7 +40,7 @@ class asm_options(C.Structure):
                 ("nev_lift", C.c_int32), ("coarse", C.c_int32), ("seed", C.c_uint64),
                 ("warm_start", C.c_int32), ("filter_degree", C.c_int32), ("record_warm", C.c_int32),
                 ("one_level", C.c_int32), ("coarse_mode", C.c_int32),
-                ("reserved", C.c_int32 * 1), ("warm_net", C.c_void_p)]
+                ("reserved", C.c_int32 * 1), ("tau", C.c_double), ("warm_net", C.c_void_p)]
 
 
 class asm_solve_opts(C.Structure):
