@@ -61,9 +61,10 @@ def parse():
     ap.add_argument("--no-forms", action="store_true", help="skip the FP64 / FP32 comparison forms")
     ap.add_argument("--warm-instances", type=int, default=12)
     ap.add_argument("--warm-steps", type=int, default=2000)
-    ap.add_argument("--mode", default="step", choices=["step", "apply", "stream"],
+    ap.add_argument("--mode", default="step", choices=["step", "apply", "stream", "sweep"],
                     help="apply: one setup, then --apply-iters applies (for profiler captures); "
-                         "stream: the batched stream of generated 3D diffusion instances, learned vs randomized start")
+                         "stream: the batched stream of generated 3D diffusion instances, learned vs randomized start; "
+                         "sweep: local eigenvalue decay and coarse dimension at a fixed tau for overlap 1, 3, 5")
     ap.add_argument("--instances", type=int, default=200, help="stream mode: instances in the stream")
     return ap.parse_args()
 
@@ -318,6 +319,51 @@ def run_stream(args, P, torch, dev, stream):
     net.close()
 
 
+def run_sweep(args, P, torch, dev, stream):
+    """Section 6 / Fig. 1 on a stand-in input: the 3D high-contrast diffusion
+    recipe on a 24^3 grid with 64 subdomains of 6^3.  For overlap 1, 3 and 5:
+    the first 64 eigenvalues of eq. gevpsvd on four subdomains (the decay
+    shape), and, with the coarse vectors selected by a fixed tau, the coarse
+    dimension, grid complexity and the PCG iterations and times."""
+    from asm_inputs import diffusion3d
+    tau, nev = 0.3, 64
+    sopt = P.default_solve_opts(rtol=1e-8, max_it=5000)
+    out = {"workload": "3D 7-point high-contrast diffusion 24^3, 64 subdomains 6^3, contrast 1e6 at 10%",
+           "tau": tau, "nev_cap": nev, "local_precision": "fp32", "subdomains_shown": [0, 21, 42, 63], "overlaps": {}}
+    for delta in (1, 3, 5):
+        prob = diffusion3d(24, (4, 4, 4), contrast=1e6, frac=0.10, delta=delta, nev=nev)
+        rp = torch.as_tensor(prob.indptr, device=dev); ci = torch.as_tensor(prob.indices, device=dev)
+        va = torch.as_tensor(prob.data, device=dev); pa = torch.as_tensor(prob.part, device=dev)
+        b = torch.as_tensor(prob.b, device=dev)
+        row = {}
+        # the spectra: top nev per subdomain, no threshold
+        h = P.asm_setup(rp, ci, va, pa, prob.N, delta, nev, P.default_options(local_precision=P.PREC_FP32), stream,
+                        True)
+        vals, cnt = P.asm_get_local_values(h)
+        row["eigenvalues"] = {str(i): [float("%.4g" % v) for v in vals[i, :cnt[i]]] for i in out["subdomains_shown"]}
+        P.asm_destroy(h)
+        # selection by tau, setup + solve timed
+        opt = P.default_options(local_precision=P.PREC_FP32, tau=tau)
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e2 = torch.cuda.Event(enable_timing=True)
+        x = torch.zeros_like(b)
+        e0.record(stream)
+        h = P.asm_setup(rp, ci, va, pa, prob.N, delta, nev, opt, stream, True)
+        e1.record(stream)
+        info = P.asm_solve(h, b, x, sopt, stream)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        si = P.asm_get_info(h)
+        _, cnt = P.asm_get_local_values(h)
+        row.update({"n_C": si.n_C, "gc": si.gc, "oc": si.oc, "per_subdomain_min_mean_max":
+                    [int(cnt.min()), float(cnt.mean()), int(cnt.max())], "max_ni": si.max_ni,
+                    "pcg_iterations": info.iterations, "setup_ms": e0.elapsed_time(e1),
+                    "solve_ms": e1.elapsed_time(e2)})
+        P.asm_destroy(h)
+        out["overlaps"][str(delta)] = row
+    print(json.dumps({"mode": "sweep", **out}), flush=True)
+
+
 def run_ours(args):
     import torch
     rank = int(os.environ.get("RANK", "0"))
@@ -352,6 +398,9 @@ def run_ours(args):
 
     if args.mode == "stream":
         run_stream(args, P, torch, dev, stream)
+        return
+    if args.mode == "sweep":
+        run_sweep(args, P, torch, dev, stream)
         return
 
     if args.mode == "apply":

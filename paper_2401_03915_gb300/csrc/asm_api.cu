@@ -147,6 +147,7 @@ asm_status asm_setup(const asm_csr* A, const int32_t* part, int32_t N, int32_t o
   if (o.warm_start && (!o.warm_net || !o.spd))
     return set_error(ASM_ERR_INVALID_ARG, "warm_start needs warm_net and the SPD method");
   if (o.one_level != 0 && o.one_level != 1) return set_error(ASM_ERR_INVALID_ARG, "one_level must be 0 or 1");
+  if (!(o.tau >= 0) || !std::isfinite(o.tau)) return set_error(ASM_ERR_INVALID_ARG, "tau must be finite and >= 0");
   if (o.coarse_mode != 0 && o.coarse_mode != 1) return set_error(ASM_ERR_INVALID_ARG, "coarse_mode must be 0 or 1");
   asm_handle* H = new (std::nothrow) asm_handle();
   if (!H) return set_error(ASM_ERR_OOM, "host allocation failed");

@@ -344,7 +344,8 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 4 : 1) k_subspace(
     const int32_t* __restrict__ lcol, const int32_t* __restrict__ omega, const int32_t* __restrict__ rp,
     const int32_t* __restrict__ ci, const double* __restrict__ val, const double* __restrict__ ds,
     const T* __restrict__ aval, T* scratch,
-    const int64_t* __restrict__ scr_off, int nev, int over, int max_sweeps, int degree, double tol, uint64_t seed,
+    const int64_t* __restrict__ scr_off, int nev, int over, int max_sweeps, int degree, double tol, double thresh,
+    uint64_t seed,
     const float* __restrict__ warm, int wld, int wk, const int64_t* __restrict__ wseg, float* __restrict__ tgt,
     double* __restrict__ values,
     double* __restrict__ resid, int32_t* __restrict__ count, int32_t* __restrict__ sweeps_out,
@@ -641,8 +642,11 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 4 : 1) k_subspace(
   int kept = 0;
   {
     const T mu0 = mu[perm[0]] > T(0) ? mu[perm[0]] : T(0);
+    // numerically nonzero values; with a threshold (tau^2: eigenvalues of
+    // eq. gevpsvd, squared singular values of D_i Pi_i) only those above it
     for (int j = 0; j < k; ++j)
-      if (mu[perm[j]] > T(sizeof(T) == 8 ? 1e-12 : 1e-6) * mu0) kept = j + 1;
+      if (mu[perm[j]] > T(sizeof(T) == 8 ? 1e-12 : 1e-6) * mu0 && (thresh <= 0 || (double)mu[perm[j]] > thresh))
+        kept = j + 1;
   }
   if (threadIdx.x == 0) { count[i] = kept; sweeps_out[i] = sweep; }
   for (int j = threadIdx.x; j < nev; j += NT) {
@@ -843,6 +847,16 @@ void run_eigen(Handle& h, cudaStream_t s) {
   size_t gemm_bytes = gemm_smem_bytes<T>();
   size_t smem = gemm_bytes + (size_t)2 * smax * smax * sizeof(double) +
                 (size_t)(4 * smax * smax + 2 * smax) * sizeof(T) + 64;
+  {
+    // the Rayleigh-Ritz blocks live in shared memory: s = nev + oversample
+    // columns need about 48 s^2 bytes in FP64 and 32 s^2 in FP32
+    int dev = 0, optin = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    if (smem > (size_t)optin)
+      fail(ASM_ERR_UNSUPPORTED, "nev + oversample too large for the subspace iteration's shared memory "
+                                "(at most about 64 columns in FP64, 80 in FP32 on this device)");
+  }
   const double tol = h.opt.eig_tol > 0 ? h.opt.eig_tol : (h.fp32 ? 1e-3 : 1e-8);
   // FP32 cannot resolve Ritz values ~1e5 below the top one to 1e-3: a cap
   // keeps such subdomains from holding the launch
@@ -891,7 +905,8 @@ void run_eigen(Handle& h, cudaStream_t s) {
     kern<<<N, NT, smem, s>>>((const T*)dn.XpT, dn.xs_off, (const T*)dn.S, dn.s_off, (const T*)dn.work, dn.work_off,
                              dn.np, h.dev_n, h.dev_m, h.dev_p, h.ov.sub_off, h.ov.ent_off, h.ov.lcol, h.ov.omega,
                              h.row_ptr, h.col_idx, h.val, h.dscale, aval, (T*)co.scratch, co.scr_off, nev, over, maxsw,
-                             degree, tol, h.opt.seed, warm, wld, wk, h.wseg, h.wtgt, co.values, co.resid, co.count,
+                             degree, tol, h.opt.tau > 0 ? h.opt.tau * h.opt.tau : 0.0, h.opt.seed, warm, wld, wk,
+                             h.wseg, h.wtgt, co.values, co.resid, co.count,
                              co.sweeps, co.Z, co.z_off);
   };
   if (spd) launch(k_subspace<T, true>);
