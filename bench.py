@@ -61,10 +61,11 @@ def parse():
     ap.add_argument("--no-forms", action="store_true", help="skip the FP64 / FP32 comparison forms")
     ap.add_argument("--warm-instances", type=int, default=12)
     ap.add_argument("--warm-steps", type=int, default=2000)
-    ap.add_argument("--mode", default="step", choices=["step", "apply", "stream", "sweep"],
+    ap.add_argument("--mode", default="step", choices=["step", "apply", "stream", "sweep", "weak"],
                     help="apply: one setup, then --apply-iters applies (for profiler captures); "
                          "stream: the batched stream of generated 3D diffusion instances, learned vs randomized start; "
-                         "sweep: local eigenvalue decay and coarse dimension at a fixed tau for overlap 1, 3, 5")
+                         "sweep: local eigenvalue decay and coarse dimension at a fixed tau for overlap 1, 3, 5; "
+                         "weak: one-GPU weak scaling of 3D Poisson at 8^3 unknowns per subdomain")
     ap.add_argument("--instances", type=int, default=200, help="stream mode: instances in the stream")
     return ap.parse_args()
 
@@ -364,6 +365,40 @@ def run_sweep(args, P, torch, dev, stream):
     print(json.dumps({"mode": "sweep", **out}), flush=True)
 
 
+def run_weak(args, P, torch, dev, stream):
+    """One-GPU weak scaling (the paper's Section 6 Poisson sweep, at a fixed
+    8^3 unknowns per subdomain): 3D 7-point Poisson (unit coefficient) on
+    m^3 grids, m = 32 .. 96, boxes of 8^3, overlap 1, nev 16, FP32 local
+    work, PCG to 1e-8.  Iteration counts should stay flat as N grows."""
+    from asm_inputs import diffusion3d
+    sopt = P.default_solve_opts(rtol=1e-8, max_it=5000)
+    opt = P.default_options(local_precision=P.PREC_FP32)
+    rows = []
+    for m in (32, 48, 64, 80, 96):
+        prob = diffusion3d(m, (m // 8,) * 3, contrast=1.0, frac=0.0, delta=1, nev=16)
+        rp = torch.as_tensor(prob.indptr, device=dev); ci = torch.as_tensor(prob.indices, device=dev)
+        va = torch.as_tensor(prob.data, device=dev); pa = torch.as_tensor(prob.part, device=dev)
+        b = torch.as_tensor(prob.b, device=dev)
+        h = P.asm_setup(rp, ci, va, pa, prob.N, 1, 16, opt, stream, True)  # warm-up of this shape
+        P.asm_destroy(h)
+        x = torch.zeros_like(b)
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e2 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        h = P.asm_setup(rp, ci, va, pa, prob.N, 1, 16, opt, stream, True)
+        e1.record(stream)
+        info = P.asm_solve(h, b, x, sopt, stream)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        si = P.asm_get_info(h)
+        rows.append({"m": m, "n": prob.n, "N": prob.N, "n_C": si.n_C, "gc": si.gc, "oc": si.oc,
+                     "pcg_iterations": info.iterations, "true_relres": info.true_relres,
+                     "setup_ms": e0.elapsed_time(e1), "solve_ms": e1.elapsed_time(e2)})
+        P.asm_destroy(h)
+    print(json.dumps({"mode": "weak", "workload": "3D 7-point Poisson, unit coefficient, 8^3 per subdomain, "
+                      "overlap 1, nev 16, FP32 local work, PCG 1e-8", "rows": rows}), flush=True)
+
+
 def run_ours(args):
     import torch
     rank = int(os.environ.get("RANK", "0"))
@@ -401,6 +436,9 @@ def run_ours(args):
         return
     if args.mode == "sweep":
         run_sweep(args, P, torch, dev, stream)
+        return
+    if args.mode == "weak":
+        run_weak(args, P, torch, dev, stream)
         return
 
     if args.mode == "apply":
