@@ -532,7 +532,8 @@ def run_ours(args):
             torch.cuda.synchronize()
             return {"s_per_step": f0.elapsed_time(f1) / n_steps / 1e3, "iterations": its}
         forms = {"fp64_random": time_form(P.default_options(local_precision=P.PREC_FP64)),
-                 "fp32_random": time_form(P.default_options(local_precision=P.PREC_FP32))}
+                 "fp32_random": time_form(P.default_options(local_precision=P.PREC_FP32)),
+                 "fp32_fp16_inverses_random": time_form(P.default_options(local_precision=P.PREC_FP32_H16))}
         # the combination of the paper's experiments: restricted one-level part,
         # deflated coarse correction, right-preconditioned GMRES without restart
         # (FGMRES with a 512-vector basis)

@@ -51,7 +51,12 @@ typedef enum {
   ASM_ERR_UNSUPPORTED = 10      /* size beyond a kernel's stated capacity        */
 } asm_status;
 
-typedef enum { ASM_PREC_FP64 = 0, ASM_PREC_FP32 = 1 } asm_precision;
+/* ASM_PREC_FP32_H16: single-precision local work, and the explicit local
+ * inverses S_i of the SPD method stored in FP16 (products and sums in FP32)
+ * wherever 2^-11 ||S_i||_inf ||A^_ii||_inf + |Omega_i| 2^-25 ||A^_ii||_inf <= 1/4,
+ * which keeps the eigenvalues of the stored inverse times A^_ii within
+ * [3/4, 5/4]; the other subdomains keep FP32 tiles. */
+typedef enum { ASM_PREC_FP64 = 0, ASM_PREC_FP32 = 1, ASM_PREC_FP32_H16 = 2 } asm_precision;
 
 /* Sparse matrix A (eq. Ax=b).  row_ptr has n+1 entries, col_idx and val nnz.
  * on_device != 0: the three arrays (and the partition passed to asm_setup)
@@ -140,6 +145,8 @@ typedef struct {
   int32_t tile_ctas;        /* resident tile-pass blocks per SM the apply uses  */
   int32_t local_sym;        /* subdomains whose local solve is the explicit
                                inverse (one pass); the rest use W^T W        */
+  int32_t local_fp16;       /* of those, the ones stored in FP16
+                               (ASM_PREC_FP32_H16)                           */
 } asm_setup_info;
 
 /* Fill *o with defaults: spd 1, FP64, oversample 8, max_sweeps 0 (= 40 in

@@ -19,7 +19,7 @@ from . import build as _build
 ASM_OK = 0
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "NOT_SPD", 3: "ZERO_PIVOT", 4: "COARSE_SINGULAR",
           5: "NONFINITE", 6: "NO_CONVERGENCE", 7: "TIMEOUT", 8: "CUDA", 9: "OOM", 10: "UNSUPPORTED"}
-PREC_FP64, PREC_FP32 = 0, 1
+PREC_FP64, PREC_FP32, PREC_FP32_H16 = 0, 1, 2
 
 
 class AsmError(RuntimeError):
@@ -59,7 +59,7 @@ class asm_setup_info(C.Structure):
                 ("sum_ni", C.c_int64), ("max_ni", C.c_int32), ("sweeps_max", C.c_int32),
                 ("eig_resid_max", C.c_double), ("stage_ms", C.c_double * 12), ("coarse_levels", C.c_int32),
                 ("coarse_fronts", C.c_int32), ("coarse_front_entries", C.c_int64), ("coarse_max_front", C.c_int32),
-                ("tile_ctas", C.c_int32), ("local_sym", C.c_int32)]
+                ("tile_ctas", C.c_int32), ("local_sym", C.c_int32), ("local_fp16", C.c_int32)]
 
 
 _lib = None
@@ -420,8 +420,8 @@ class TwoLevelSchwarz:
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required")
-        o = default_options(spd=1 if spd else 0,
-                            local_precision=PREC_FP32 if precision == "fp32" else PREC_FP64, **opts)
+        prec = {"fp64": PREC_FP64, "fp32": PREC_FP32, "fp32h": PREC_FP32_H16}[precision]
+        o = default_options(spd=1 if spd else 0, local_precision=prec, **opts)
         self.device = device
         self.n = len(indptr) - 1
         if device:

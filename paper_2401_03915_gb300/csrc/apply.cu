@@ -17,6 +17,8 @@
 #include <mutex>
 #include <tuple>
 
+#include <cuda_fp16.h>
+
 #include "handle.cuh"
 
 namespace asmgpu {
@@ -87,9 +89,11 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   return true;
 }
 
+// T: the type of the stored tiles (FP16 tiles: twice the ring depth, the
+// same 48 KB of shared memory as FP32)
 template <typename T>
 struct Stages {
-  static constexpr int S = sizeof(T) == 4 ? 3 : 2;                  // ring depth
+  static constexpr int S = sizeof(T) == 2 ? 6 : (sizeof(T) == 4 ? 3 : 2);  // ring depth
   static constexpr uint32_t BYTES = TILE * TILE * sizeof(T);        // one tile
   static constexpr size_t SMEM = (size_t)S * BYTES;
 };
@@ -100,8 +104,15 @@ struct Stages {
 // output: the padded vector tout (SPD first pass) or, per Omega position,
 // ypos in FP64 (general).  Column pass (COL = true, SPD), item (i, J):
 // y_J = sum_{I >= J} T_IJ^T t_I, written per Omega position to ypos.
-template <typename T, bool SPD, bool COL>
-__global__ void __launch_bounds__(NT) k_tile_pass(const T* __restrict__ tiles, const int64_t* __restrict__ tile_off,
+__device__ __forceinline__ float tile_val(__half v) { return __half2float(v); }
+__device__ __forceinline__ float tile_val(float v) { return v; }
+__device__ __forceinline__ double tile_val(double v) { return v; }
+
+// T: arithmetic and vectors; TS: the stored tiles (T, or FP16 for the
+// explicit inverses kept in half precision).  Every tile occupies a slot of
+// TILE * TILE elements of T; FP16 tiles fill the first half of theirs.
+template <typename T, typename TS, bool SPD, bool COL>
+__global__ void __launch_bounds__(NT) k_tile_pass(const TS* __restrict__ tiles, const int64_t* __restrict__ tile_off,
                                                   const int2* __restrict__ items, int nitems,
                                                   const int32_t* __restrict__ sub_off, const int32_t* __restrict__ n_arr,
                                                   const int32_t* __restrict__ nt_arr,
@@ -111,10 +122,11 @@ __global__ void __launch_bounds__(NT) k_tile_pass(const T* __restrict__ tiles, c
                                                   int32_t* __restrict__ err, const int32_t* __restrict__ done) {
   COUNT_LAUNCH();
   if (done != nullptr && *done) return;
-  using St = Stages<T>;
+  using St = Stages<TS>;
   constexpr int S = St::S;
+  constexpr int64_t SLOT = (int64_t)TILE * TILE * sizeof(T) / sizeof(TS);  // elements of TS per tile slot
   extern __shared__ __align__(128) unsigned char smraw[];
-  T* stage = reinterpret_cast<T*>(smraw);
+  TS* stage = reinterpret_cast<TS*>(smraw);
   __shared__ __align__(8) uint64_t full[S];
   __shared__ T colpart[NT / 32][TILE];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, cq = tid & 15, rg = tid >> 4;
@@ -124,13 +136,13 @@ __global__ void __launch_bounds__(NT) k_tile_pass(const T* __restrict__ tiles, c
     const int nt = nt_arr[w.x];
     return COL ? nt - w.y : (SPD ? w.y + 1 : nt);
   };
-  auto src = [&](int it, int k) -> const T* {
+  auto src = [&](int it, int k) -> const TS* {
     const int2 w = items[it];
     const int nt = nt_arr[w.x];
     int64_t t;
     if (COL) { const int64_t I = w.y + k; t = I * (I + 1) / 2 + w.y; }
     else t = SPD ? (int64_t)w.y * (w.y + 1) / 2 + k : (int64_t)w.y * nt + k;
-    return tiles + (tile_off[w.x] + t) * (TILE * TILE);
+    return tiles + (tile_off[w.x] + t) * SLOT;
   };
   if (tid == 0) {
     for (int q = 0; q < S; ++q) mbar_init(&full[q], 1);
@@ -178,13 +190,13 @@ __global__ void __launch_bounds__(NT) k_tile_pass(const T* __restrict__ tiles, c
       for (int q = 0; q < 4; ++q) xv[q] = COL ? vb[(B + k) * TILE + rg + 16 * q] : vb[k * TILE + 4 * cq + q];
       const bool got = mbar_wait_bounded(&full[slot], (t / S) & 1);
       if (!__syncthreads_and(got)) { ok = false; break; }
-      const T* tile = stage + (size_t)slot * TILE * TILE;
+      const TS* tile = stage + (size_t)slot * TILE * TILE;
       T v[4][4];
 #pragma unroll
       for (int a = 0; a < 4; ++a) {
-        const T* rp = tile + (rg + 16 * a) * TILE + 4 * cq;
+        const TS* rp = tile + (rg + 16 * a) * TILE + 4 * cq;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) v[a][q] = rp[q];
+        for (int q = 0; q < 4; ++q) v[a][q] = tile_val(rp[q]);
       }
       if (!COL) {
 #pragma unroll
@@ -389,19 +401,29 @@ void gather_x(Handle& h, const double* r, cudaStream_t s, const int32_t* done) {
                                    done);
 }
 
-template <typename T, bool SPD, bool COL>
+template <typename T, bool SPD, bool COL, typename TS = T>
 void launch_pass(Handle& h, int nitems, const int2* items, const T* vin, T* tout, cudaStream_t s,
                  const int32_t* done) {
   Dense& dn = h.dn;
   const unsigned g = tile_grid<T>(h, nitems);
-  k_tile_pass<T, SPD, COL><<<g, NT, Stages<T>::SMEM, s>>>((const T*)dn.tiles, dn.tile_off, items, nitems,
-                                                           h.ov.sub_off, h.dev_n, dn.nt, dn.pad_off, vin, tout,
-                                                           dn.ypos, dn.sym, (T*)dn.slots, dn.err, done);
+  k_tile_pass<T, TS, SPD, COL><<<g, NT, Stages<TS>::SMEM, s>>>((const TS*)dn.tiles, dn.tile_off, items, nitems,
+                                                                h.ov.sub_off, h.dev_n, dn.nt, dn.pad_off, vin, tout,
+                                                                dn.ypos, dn.sym, (T*)dn.slots, dn.err, done);
 }
 
 template <typename T>
 void row_pass(Handle& h, cudaStream_t s, const int32_t* done) {
   Dense& dn = h.dn;
+  if constexpr (sizeof(T) == 4) {
+    if (dn.n_row_items_h > 0) {
+      // explicit inverses stored in FP16, then the rest (FP32 tiles)
+      launch_pass<T, true, false, __half>(h, dn.n_row_items_h, dn.row_items_h, (const T*)dn.xpad, (T*)dn.tpad, s,
+                                          done);
+      if (dn.n_row_items_f > 0)
+        launch_pass<T, true, false>(h, dn.n_row_items_f, dn.row_items_f, (const T*)dn.xpad, (T*)dn.tpad, s, done);
+      return;
+    }
+  }
   if (h.opt.spd)
     launch_pass<T, true, false>(h, dn.n_row_items, dn.row_items, (const T*)dn.xpad, (T*)dn.tpad, s, done);
   else
@@ -428,9 +450,12 @@ void prepare_tile_passes() {
   static bool done = false;
   if (done) return;
   const int sm = (int)Stages<T>::SMEM;
-  CK(cudaFuncSetAttribute(k_tile_pass<T, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-  CK(cudaFuncSetAttribute(k_tile_pass<T, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-  CK(cudaFuncSetAttribute(k_tile_pass<T, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  CK(cudaFuncSetAttribute(k_tile_pass<T, T, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  CK(cudaFuncSetAttribute(k_tile_pass<T, T, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  CK(cudaFuncSetAttribute(k_tile_pass<T, T, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  if constexpr (sizeof(T) == 4)
+    CK(cudaFuncSetAttribute(k_tile_pass<T, __half, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)Stages<__half>::SMEM));
   done = true;
 }
 
@@ -546,7 +571,8 @@ void time_impl(Handle& h, const double* r, double* z, int iters, cudaStream_t s,
 // Autotuner of the apply's launch shape: the whole apply (local tile passes
 // with the coarse part beside them) is timed for each candidate number of
 // resident tile-pass blocks per SM and the fastest is kept.  Results are
-// cached per (device, tiles, subdomains, coarse size, precision), so only the
+// cached per (device, tiles, subdomains, coarse size, precision and tile
+// storage), so only the
 // first setup of a given shape pays for the measurement.
 std::mutex g_tune_mutex;
 std::map<std::tuple<int, int64_t, int, int, int>, int> g_tune_cache;
@@ -555,7 +581,7 @@ template <typename T>
 void tune_impl(Handle& h, cudaStream_t s) {
   int dev = 0;
   CK(cudaGetDevice(&dev));
-  const auto key = std::make_tuple(dev, h.dn.n_tiles, h.N, h.co.n_C, h.fp32 ? 1 : 0);
+  const auto key = std::make_tuple(dev, h.dn.n_tiles, h.N, h.co.n_C, (h.fp32 ? 1 : 0) + (h.dn.n_row_items_h > 0 ? 2 : 0));
   {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     auto it = g_tune_cache.find(key);

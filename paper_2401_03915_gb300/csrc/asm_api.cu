@@ -141,8 +141,9 @@ asm_status asm_setup(const asm_csr* A, const int32_t* part, int32_t N, int32_t o
   if (nev < 0 || nev > 120) return set_error(ASM_ERR_INVALID_ARG, "nev must be in 0..120");
   asm_options o;
   if (opt) o = *opt; else asm_default_options(&o);
-  if (o.local_precision != ASM_PREC_FP64 && o.local_precision != ASM_PREC_FP32)
-    return set_error(ASM_ERR_INVALID_ARG, "local_precision must be ASM_PREC_FP64 or ASM_PREC_FP32");
+  if (o.local_precision != ASM_PREC_FP64 && o.local_precision != ASM_PREC_FP32 &&
+      o.local_precision != ASM_PREC_FP32_H16)
+    return set_error(ASM_ERR_INVALID_ARG, "local_precision must be ASM_PREC_FP64, ASM_PREC_FP32 or ASM_PREC_FP32_H16");
   if (o.oversample < 0 || o.oversample > 64) return set_error(ASM_ERR_INVALID_ARG, "oversample must be in 0..64");
   if (o.warm_start && (!o.warm_net || !o.spd))
     return set_error(ASM_ERR_INVALID_ARG, "warm_start needs warm_net and the SPD method");
@@ -157,7 +158,8 @@ asm_status asm_setup(const asm_csr* A, const int32_t* part, int32_t N, int32_t o
     Handle& h = H->h;
     h.n = A->n; h.nnz = A->nnz; h.N = N; h.delta = overlap; h.nev = nev; h.opt = o;
     h.host_io = A->on_device == 0;
-    h.fp32 = o.local_precision == ASM_PREC_FP32;
+    h.fp32 = o.local_precision != ASM_PREC_FP64;
+    h.s16 = o.local_precision == ASM_PREC_FP32_H16 && o.spd;
     {
       int dev = 0, sms = 0;
       CK(cudaGetDevice(&dev));
@@ -240,6 +242,7 @@ asm_status asm_setup(const asm_csr* A, const int32_t* part, int32_t N, int32_t o
     inf.coarse_max_front = h.nd.max_m;
     inf.tile_ctas = h.tile_ctas;
     for (int8_t v : h.dn.h_sym) inf.local_sym += v ? 1 : 0;
+    for (int8_t v : h.dn.h_s16) inf.local_fp16 += v ? 1 : 0;
   });
   if (st != ASM_OK) {
     free_handle_memory(H->h);

@@ -61,6 +61,13 @@ struct Dense {
   int n_row_items = 0, n_col_items = 0, n_sym_items = 0;
   int8_t* sym = nullptr;              // per subdomain: 1 = tiles hold S = W^T W (SPD, single precision)
   std::vector<int8_t> h_sym;
+  // FP16 storage of the explicit inverses (single precision with half-precision
+  // tiles): per subdomain 1 = its S tiles hold FP16 values; the row items split
+  // into those subdomains' (h) and the rest (f)
+  int8_t* s16 = nullptr;
+  std::vector<int8_t> h_s16;
+  int2 *row_items_h = nullptr, *row_items_f = nullptr;
+  int n_row_items_h = 0, n_row_items_f = 0;
   void* slots = nullptr;              // explicit-inverse column contributions, TILE per stored tile
   double* ypos = nullptr;             // per omega position: local solution before the pull
   int64_t n_tiles = 0, n_work = 0, n_xs = 0, n_s = 0, n_pad = 0;
@@ -111,6 +118,7 @@ struct Handle {
   asm_options opt{};
   bool host_io = false;
   bool fp32 = false;
+  bool s16 = false;                 // explicit local inverses stored in FP16 where the bound allows
   DevMem mem;
   int32_t *row_ptr = nullptr, *col_idx = nullptr, *part = nullptr;
   double* val = nullptr;

@@ -22,6 +22,8 @@
 // copied out; the sweep then continues over Gamma_delta and leaves A_ii^{-1}.
 #include <algorithm>
 
+#include <cuda_fp16.h>
+
 #include "handle.cuh"
 
 namespace asmgpu {
@@ -534,6 +536,142 @@ __global__ void __launch_bounds__(NT) k_lauum(const T* __restrict__ work, const 
   }
 }
 
+// ---------------------------------------------------------------------------
+// FP16 storage of the explicit inverses.  Rounding S_i to FP16 perturbs it
+// by dS with ||dS||_2 <= ||dS||_inf <= 2^-11 ||S_i||_inf + n_i 2^-25 (normal
+// and subnormal range), and lambda_min(S_i) = 1 / lambda_max(A^_ii) >=
+// 1 / ||A^_ii||_inf; so (S_i + dS) A^_ii = I + dS A^_ii has its eigenvalues
+// within 1 -+ ||dS|| ||A^_ii||_inf.  A subdomain is stored in FP16 when that
+// bound is at most 1/4 (then also |S_ij| <= 512 / ||A^_ii||_inf: no overflow).
+// All reductions run in a fixed order (the decision is reproducible).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float warp_max_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// rmax[boff[i] + I] = max over the rows r of row block I of sum_j |S_rj|, from
+// the stored lower tiles: rows of (I, J <= I) and columns of (K > I, I).
+__global__ void __launch_bounds__(NT) k_s_rowsum(const float* __restrict__ tiles, const int64_t* __restrict__ tile_off,
+                                                 const int32_t* __restrict__ nt_arr, const int2* __restrict__ items,
+                                                 int nitems, const int64_t* __restrict__ boff,
+                                                 float* __restrict__ rmax) {
+  COUNT_LAUNCH();
+  __shared__ float racc[TILE];
+  __shared__ float part[NT / TILE][TILE];
+  __shared__ float red[2];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const int2 w = items[it];
+    const int i = w.x, I = w.y, nt = nt_arr[i];
+    const float* base = tiles + tile_off[i] * (int64_t)(TILE * TILE);
+    if (tid < TILE) racc[tid] = 0.f;
+    __syncthreads();
+    for (int J = 0; J <= I; ++J) {
+      const float* T0 = base + ((int64_t)I * (I + 1) / 2 + J) * (TILE * TILE);
+      for (int r = wid; r < TILE; r += NT / 32) {
+        float v = fabsf(T0[r * TILE + lane]) + fabsf(T0[r * TILE + lane + 32]);
+        v = warp_sum(v);
+        if (lane == 0) racc[r] += v;
+      }
+    }
+    __syncthreads();
+    for (int K = I + 1; K < nt; ++K) {
+      const float* T0 = base + ((int64_t)K * (K + 1) / 2 + I) * (TILE * TILE);
+      const int c = tid % TILE, g = tid / TILE;
+      float v = 0.f;
+      for (int k = g * (TILE * TILE / NT); k < (g + 1) * (TILE * TILE / NT); ++k) v += fabsf(T0[k * TILE + c]);
+      part[g][c] = v;
+      __syncthreads();
+      if (tid < TILE) {
+        float sm = racc[tid];
+        for (int q = 0; q < NT / TILE; ++q) sm += part[q][tid];
+        racc[tid] = sm;
+      }
+      __syncthreads();
+    }
+    if (tid < TILE) {
+      const float m = warp_max_f(racc[tid]);
+      if (lane == 0) red[wid] = m;
+    }
+    __syncthreads();
+    if (tid == 0) rmax[boff[i] + I] = fmaxf(red[0], red[1]);
+    __syncthreads();
+  }
+}
+
+// amax[i] = ||A^_ii||_inf for the explicit-inverse subdomains (0 elsewhere)
+__global__ void __launch_bounds__(NT) k_a_rowsum(const int32_t* __restrict__ sub_off, const int32_t* __restrict__ n_arr,
+                                                 const int32_t* __restrict__ omega, const int64_t* __restrict__ ent_off,
+                                                 const int32_t* __restrict__ lcol, const int32_t* __restrict__ rp,
+                                                 const int32_t* __restrict__ ci, const double* __restrict__ val,
+                                                 const double* __restrict__ ds, const int8_t* __restrict__ sym,
+                                                 double* __restrict__ amax) {
+  COUNT_LAUNCH();
+  __shared__ double red[NT / 32];
+  const int i = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  double m = 0;
+  if (sym[i]) {
+    const int n = n_arr[i], b0 = sub_off[i];
+    for (int a = tid; a < n; a += NT) {
+      const int v = omega[b0 + a];
+      const double sv = ds[v];
+      const int64_t e0 = ent_off[b0 + a];
+      const int b = rp[v], e = rp[v + 1];
+      double acc = 0;
+      for (int q = 0; q < e - b; ++q)
+        if (lcol[e0 + q] >= 0) acc += fabs(val[b + q] * sv * ds[ci[b + q]]);
+      m = fmax(m, acc);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (lane == 0) red[wid] = m;
+  __syncthreads();
+  if (tid == 0) {
+    double t = red[0];
+    for (int q = 1; q < NT / 32; ++q) t = fmax(t, red[q]);
+    amax[i] = t;
+  }
+}
+
+__global__ void k_decide_s16(int N, const int8_t* __restrict__ sym, const int32_t* __restrict__ nt_arr,
+                             const int32_t* __restrict__ n_arr, const int64_t* __restrict__ boff,
+                             const float* __restrict__ rmax, const double* __restrict__ amax,
+                             int8_t* __restrict__ s16) {
+  COUNT_LAUNCH();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  int8_t ok = 0;
+  if (sym[i]) {
+    double ms = 0;
+    for (int I = 0; I < nt_arr[i]; ++I) ms = fmax(ms, (double)rmax[boff[i] + I]);
+    const double bound = (ldexp(ms, -11) + n_arr[i] * ldexp(1.0, -25)) * amax[i];
+    ok = isfinite(bound) && bound <= 0.25;
+  }
+  s16[i] = ok;
+}
+
+// in place: the FP32 tile becomes FP16 in the first half of its slot
+__global__ void __launch_bounds__(NT) k_tiles_to_half(float* __restrict__ tiles, const int4* __restrict__ desc,
+                                                      int64_t ntiles, const int8_t* __restrict__ s16) {
+  COUNT_LAUNCH();
+  constexpr int PER = TILE * TILE / NT;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    if (!s16[desc[t].x]) continue;  // the same for the whole block
+    float* src = tiles + t * (TILE * TILE);
+    float v[PER];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) v[k] = src[threadIdx.x + k * NT];
+    __syncthreads();  // the whole tile is read before any of it is overwritten
+    __half* dst = reinterpret_cast<__half*>(src);
+#pragma unroll
+    for (int k = 0; k < PER; ++k) dst[threadIdx.x + k * NT] = __float2half_rn(v[k]);
+    __syncthreads();
+  }
+}
+
 // Copy A_ii^{-1} into TILE x TILE tiles: SPD keeps the lower tiles (I >= J),
 // the general path keeps all of them.  One block per tile.
 template <typename T>
@@ -699,6 +837,42 @@ void run_local(Handle& h, cudaStream_t s) {
   if (!cv.empty()) CK(cudaMemcpyAsync(dn.col_items, cv.data(), sizeof(int2) * cv.size(), cudaMemcpyHostToDevice, s));
   if (!si.empty()) CK(cudaMemcpyAsync(dn.sym_items, si.data(), sizeof(int2) * si.size(), cudaMemcpyHostToDevice, s));
   if (spd && !si.empty()) dn.slots = mem.alloc<T>(tl * TILE);
+  if constexpr (sizeof(T) == 4) {
+    if (h.s16 && spd && !si.empty()) {
+      // which explicit inverses go to FP16, then convert their tiles in place
+      std::vector<int64_t> bo(N);
+      int64_t nb = 0;
+      for (int i = 0; i < N; ++i) { bo[i] = nb; nb += dn.h_nt[i]; }
+      int64_t* boff = mem.alloc<int64_t>(N);
+      float* rmax = mem.alloc<float>(std::max<int64_t>(nb, 1));
+      double* amax = mem.alloc<double>(N);
+      dn.s16 = mem.alloc<int8_t>(N);
+      CK(cudaMemcpyAsync(boff, bo.data(), 8 * N, cudaMemcpyHostToDevice, s));
+      const unsigned gs = (unsigned)std::min<int64_t>((int64_t)si.size(), 152 * 8);
+      k_s_rowsum<<<gs, NT, 0, s>>>((const float*)dn.tiles, dn.tile_off, dn.nt, dn.sym_items, (int)si.size(), boff,
+                                   rmax);
+      k_a_rowsum<<<N, NT, 0, s>>>(ov.sub_off, d_n, ov.omega, ov.ent_off, ov.lcol, h.row_ptr, h.col_idx, h.val,
+                                  h.dscale, dn.sym, amax);
+      k_decide_s16<<<(unsigned)ceil_div(N, NT), NT, 0, s>>>(N, dn.sym, dn.nt, d_n, boff, rmax, amax, dn.s16);
+      k_tiles_to_half<<<gp, NT, 0, s>>>((float*)dn.tiles, dn.tile_desc, tl, dn.s16);
+      CK_LAUNCH("FP16 storage of the explicit inverses");
+      dn.h_s16.assign(N, 0);
+      CK(cudaMemcpyAsync(dn.h_s16.data(), dn.s16, N, cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      std::vector<int2> rh, rf;
+      for (const int2& e : rv) (dn.h_s16[e.x] ? rh : rf).push_back(e);
+      dn.n_row_items_h = (int)rh.size();
+      dn.n_row_items_f = (int)rf.size();
+      if (!rh.empty()) {
+        dn.row_items_h = mem.alloc<int2>(rh.size());
+        dn.row_items_f = mem.alloc<int2>(std::max<size_t>(rf.size(), 1));
+        CK(cudaMemcpyAsync(dn.row_items_h, rh.data(), sizeof(int2) * rh.size(), cudaMemcpyHostToDevice, s));
+        if (!rf.empty())
+          CK(cudaMemcpyAsync(dn.row_items_f, rf.data(), sizeof(int2) * rf.size(), cudaMemcpyHostToDevice, s));
+        CK(cudaStreamSynchronize(s));
+      }
+    }
+  }
 }
 
 }  // namespace
