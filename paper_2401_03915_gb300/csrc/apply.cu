@@ -572,8 +572,7 @@ void time_impl(Handle& h, const double* r, double* z, int iters, cudaStream_t s,
 // with the coarse part beside them) is timed for each candidate number of
 // resident tile-pass blocks per SM and the fastest is kept.  Results are
 // cached per (device, tiles, subdomains, coarse size, precision and tile
-// storage), so only the
-// first setup of a given shape pays for the measurement.
+// storage), so only the first setup of a given shape pays for the measurement.
 std::mutex g_tune_mutex;
 std::map<std::tuple<int, int64_t, int, int, int>, int> g_tune_cache;
 
