@@ -112,7 +112,9 @@ typedef struct {
   int32_t method;           /* 0: PCG for SPD A with the symmetric apply
                                (one_level 0, coarse_mode 0), else FGMRES;
                                1: PCG; 2: FGMRES                               */
-  int32_t restart;          /* FGMRES restart length (default 30, at most 512)  */
+  int32_t restart;          /* FGMRES restart length, at most 512; 0 (default):
+                               512 for the restricted or deflated apply (GMRES
+                               without restart, Section 6), 30 otherwise      */
   double rtol;              /* stop at ||b - A x||_2 / ||b||_2 <= rtol         */
   int32_t max_it;           /* iteration cap                                   */
   int32_t use_x0;           /* 1: x holds the initial guess; 0: x0 = 0         */

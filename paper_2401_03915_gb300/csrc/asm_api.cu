@@ -115,7 +115,7 @@ void asm_default_solve_opts(asm_solve_opts* o) {
   if (!o) return;
   std::memset(o, 0, sizeof(*o));
   o->method = 0;
-  o->restart = 30;
+  o->restart = 0;  // automatic
   o->rtol = 1e-8;
   o->max_it = 1000;
   o->use_x0 = 0;
@@ -277,8 +277,11 @@ asm_status asm_solve(asm_handle* H, const double* b, double* x, const asm_solve_
   asm_solve_opts so;
   if (o) so = *o; else asm_default_solve_opts(&so);
   if (!(so.rtol > 0) || so.max_it < 1) return set_error(ASM_ERR_INVALID_ARG, "rtol must be > 0 and max_it >= 1");
-  if (so.restart <= 0) so.restart = 30;
   Handle& h = H->h;
+  // automatic restart length: GMRES without restart (up to 512 vectors) for
+  // the restricted or deflated apply, as the Section 6 experiments; 30 otherwise
+  if (so.restart <= 0)
+    so.restart = (h.opt.one_level == 1 || (h.opt.coarse_mode == 1 && h.co.n_C > 0)) ? 512 : 30;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   bool conv = false;
   asm_status st = guarded([&] {

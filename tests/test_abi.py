@@ -42,7 +42,9 @@ def test_option_defaults(lib):
     o = P.default_options()
     assert o.spd == 1 and o.oversample == 8 and o.coarse == 1
     s = P.default_solve_opts()
-    assert s.rtol == 1e-8 and s.restart == 30 and s.max_it == 1000
+    # restart 0: chosen at solve time (512 for the restricted or deflated apply, else 30)
+    assert s.rtol == 1e-8 and s.restart == 0 and s.max_it == 1000
+    assert o.one_level == 0 and o.coarse_mode == 0 and o.tau == 0.0
 
 
 def test_invalid_arguments_are_rejected_before_any_device_work(lib):
