@@ -205,6 +205,22 @@ def oracle_sample(prob, n_sub: int, gpu_iterations: int | None):
     return total, threads, sample_desc
 
 
+def cpu_model() -> str:
+    """The host CPU as /proc/cpuinfo names it (x86: model name; Arm: implementer and part)."""
+    import platform
+    try:
+        info = open("/proc/cpuinfo").read().splitlines()
+    except OSError:
+        return platform.machine()
+    for key in ("model name", "Model"):
+        for line in info:
+            if line.startswith(key) and ":" in line:
+                return line.split(":", 1)[1].strip()
+    impl = next((l.split(":", 1)[1].strip() for l in info if l.startswith("CPU implementer")), "")
+    part = next((l.split(":", 1)[1].strip() for l in info if l.startswith("CPU part")), "")
+    return f"{platform.machine()} implementer {impl} part {part}".strip()
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -222,7 +238,8 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "config": args.config},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "cpu": cpu_model(), "kind": "oracle",
+                             "sample": desc},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -567,7 +584,7 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, threads, desc = oracle_sample(prob, n_sub=16, gpu_iterations=None)
-        cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc}
+        cpu = {"value": v, "unit": UNIT, "cores": threads, "cpu": cpu_model(), "kind": "oracle", "sample": desc}
 
     if rank == 0:
         line = {
