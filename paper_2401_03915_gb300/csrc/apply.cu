@@ -19,6 +19,7 @@
 
 #include <cuda_fp16.h>
 
+#include "ffloat.cuh"
 #include "handle.cuh"
 
 namespace asmgpu {
@@ -270,6 +271,246 @@ __global__ void __launch_bounds__(NT) k_tile_pass(const TS* __restrict__ tiles, 
   }
 }
 
+// ---------------------------------------------------------------------------
+// Single-precision storage, FP64-accurate arithmetic.  The tiles hold FP32 (or
+// FP16) values; the vectors are float-float pairs (hi, lo) in the padded
+// space, scaled per subdomain by a power of two so that max |x| is in
+// [1/2, 1); every product is formed exactly and every sum is compensated
+// (ffloat.cuh), so the local solve is the stored operator applied in about
+// 2^-44 relative arithmetic: FP32 rounding of the input, of the sums or of the
+// output each cost the PCG iterations that FP32 storage alone does not.
+//
+// Row pass (COL = false), item (i, B): thread (rg, cq) owns rows rg + 16 a and
+// columns 4 cq .. 4 cq + 3 of every tile, one biased accumulator per row,
+// renormalised after each tile; the 16 column quads of a row are merged at
+// the end of the item.  Explicit-inverse subdomain, tile (B, k), k < B: the
+// column contribution S_Bk^T x_B is a 4-term biased chain per thread and
+// column, merged across the two row groups of a warp and across the 8 warps
+// (through shared memory) into the tile's slot as a float-float pair.
+// Outputs: the row part (SPD) as float-float in tout, or y (general) per
+// Omega position in FP64 times the subdomain's scale.  Column pass (COL =
+// true): y_B = sum_{I >= B} W_IB^T t_I with one biased accumulator per column.
+// ---------------------------------------------------------------------------
+template <typename TS, bool SPD, bool COL>
+__global__ void __launch_bounds__(NT) k_tile_pass_cf(const TS* __restrict__ tiles, const int64_t* __restrict__ tile_off,
+                                                     const int2* __restrict__ items, int nitems,
+                                                     const int32_t* __restrict__ sub_off,
+                                                     const int32_t* __restrict__ n_arr,
+                                                     const int32_t* __restrict__ nt_arr,
+                                                     const int64_t* __restrict__ pad_off,
+                                                     const float2* __restrict__ vin, float2* __restrict__ tout,
+                                                     double* __restrict__ ypos, const double* __restrict__ unscale,
+                                                     const int8_t* __restrict__ sym, float2* __restrict__ slots,
+                                                     int32_t* __restrict__ err, const int32_t* __restrict__ done) {
+  COUNT_LAUNCH();
+  if (done != nullptr && *done) return;
+  using St = Stages<TS>;
+  constexpr int S = St::S;
+  constexpr int64_t SLOT = (int64_t)TILE * TILE * sizeof(float) / sizeof(TS);  // elements of TS per tile slot
+  extern __shared__ __align__(128) unsigned char smraw[];
+  TS* stage = reinterpret_cast<TS*>(smraw);
+  __shared__ __align__(8) uint64_t full[S];
+  __shared__ float2 colpart[NT / 32][TILE];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, cq = tid & 15, rg = tid >> 4;
+  auto count = [&](int it) -> int {
+    const int2 w = items[it];
+    const int nt = nt_arr[w.x];
+    return COL ? nt - w.y : (SPD ? w.y + 1 : nt);
+  };
+  auto src = [&](int it, int k) -> const TS* {
+    const int2 w = items[it];
+    const int nt = nt_arr[w.x];
+    int64_t t;
+    if (COL) { const int64_t I = w.y + k; t = I * (I + 1) / 2 + w.y; }
+    else t = SPD ? (int64_t)w.y * (w.y + 1) / 2 + k : (int64_t)w.y * nt + k;
+    return tiles + (tile_off[w.x] + t) * SLOT;
+  };
+  if (tid == 0) {
+    for (int q = 0; q < S; ++q) mbar_init(&full[q], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  int p_it = blockIdx.x, p_k = 0, p_n = p_it < nitems ? count(p_it) : 0;
+  uint32_t issued = 0;
+  auto issue = [&](int slot) {
+    if (p_it >= nitems) return;
+    mbar_expect_tx(&full[slot], St::BYTES);
+    bulk_g2s(stage + (size_t)slot * TILE * TILE, src(p_it, p_k), St::BYTES, &full[slot]);
+    ++issued;
+    if (++p_k == p_n) {
+      p_it += gridDim.x;
+      p_k = 0;
+      p_n = p_it < nitems ? count(p_it) : 0;
+    }
+  };
+  if (tid == 0)
+    for (int q = 0; q < S; ++q) issue(q);
+  uint32_t t = 0;
+  bool ok = true;
+  for (int it = blockIdx.x; it < nitems && ok; it += gridDim.x) {
+    const int2 w = items[it];
+    const int i = w.x, B = w.y, nt = nt_arr[i];
+    const int cnt = COL ? nt - B : (SPD ? B + 1 : nt);
+    const float2* vb = vin + pad_off[i];
+    const bool symi = !COL && SPD && sym != nullptr && sym[i];
+    float2 xb[4];
+    if (symi) {
+#pragma unroll
+      for (int a = 0; a < 4; ++a) xb[a] = vb[B * TILE + rg + 16 * a];
+    }
+    float2* slot_base = symi ? slots + (tile_off[i] + (int64_t)B * (B + 1) / 2) * TILE : nullptr;
+    BiasAcc acc[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) bias_init(acc[a]);
+    for (int k = 0; k < cnt; ++k, ++t) {
+      const int slot = (int)(t % S);
+      float2 xv[4];
+      if (COL) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) xv[q] = vb[(B + k) * TILE + rg + 16 * q];
+      } else {
+        const float4* xp = reinterpret_cast<const float4*>(vb + k * TILE + 4 * cq);
+        const float4 u0 = xp[0], u1 = xp[1];
+        xv[0] = make_float2(u0.x, u0.y); xv[1] = make_float2(u0.z, u0.w);
+        xv[2] = make_float2(u1.x, u1.y); xv[3] = make_float2(u1.z, u1.w);
+      }
+      const bool got = mbar_wait_bounded(&full[slot], (t / S) & 1);
+      if (!__syncthreads_and(got)) { ok = false; break; }
+      const TS* tile = stage + (size_t)slot * TILE * TILE;
+      float v[4][4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const TS* rp = tile + (rg + 16 * a) * TILE + 4 * cq;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[a][q] = tile_val(rp[q]);
+      }
+      if (!COL) {
+        // rows: acc[a] += sum_q v[a][q] x_q
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          float tb = 0.f;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) tb = __fmaf_ru(fabsf(v[a][q]), fabsf(xv[q].x), tb);
+          bias_reserve(acc[a], tb);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) bias_step(acc[a], v[a][q], xv[q].x, xv[q].y);
+          bias_renorm(acc[a]);
+        }
+      } else {
+        // columns: acc[q] += sum_a v[a][q] t_a
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          float tb = 0.f;
+#pragma unroll
+          for (int a = 0; a < 4; ++a) tb = __fmaf_ru(fabsf(v[a][q]), fabsf(xv[a].x), tb);
+          bias_reserve(acc[q], tb);
+#pragma unroll
+          for (int a = 0; a < 4; ++a) bias_step(acc[q], v[a][q], xv[a].x, xv[a].y);
+          bias_renorm(acc[q]);
+        }
+      }
+      const bool colc = symi && k < B;
+      if (colc) {
+        // column contributions of the explicit inverse: c_q = sum_a v[a][q] xb_a
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          BiasAcc c;
+          bias_init(c);
+          float tb = 0.f;
+#pragma unroll
+          for (int a = 0; a < 4; ++a) tb = __fmaf_ru(fabsf(v[a][q]), fabsf(xb[a].x), tb);
+          bias_reserve(c, tb);
+#pragma unroll
+          for (int a = 0; a < 4; ++a) bias_step(c, v[a][q], xb[a].x, xb[a].y);
+          float h, l;
+          bias_value(c, h, l);
+          ff_add(h, l, __shfl_xor_sync(0xffffffffu, h, 16), __shfl_xor_sync(0xffffffffu, l, 16));
+          if (lane < 16) colpart[wid][4 * cq + q] = make_float2(h, l);
+        }
+      }
+      __syncthreads();  // every thread is done with this slot (and colpart is complete)
+      if (tid == 0) {
+        fence_proxy_async();
+        issue(slot);
+      }
+      if (colc && tid < TILE) {
+        float2 s0 = colpart[0][tid];
+#pragma unroll
+        for (int w2 = 1; w2 < NT / 32; ++w2) ff_add(s0.x, s0.y, colpart[w2][tid].x, colpart[w2][tid].y);
+        slot_base[(int64_t)k * TILE + tid] = s0;
+      }
+    }
+    if (!ok) break;
+    if (!COL && symi) __syncthreads();  // colpart reads of the last tile are done
+    if (!COL) {
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        float h, l;
+        bias_value(acc[a], h, l);
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1)
+          ff_add(h, l, __shfl_xor_sync(0xffffffffu, h, o), __shfl_xor_sync(0xffffffffu, l, o));
+        if (cq == 0) {
+          const int row = B * TILE + rg + 16 * a;
+          if (SPD) tout[pad_off[i] + row] = make_float2(h, l);
+          else if (row < n_arr[i]) ypos[sub_off[i] + row] = ff_to_double(h, l) * unscale[i];
+        }
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        float h, l;
+        bias_value(acc[q], h, l);
+        ff_add(h, l, __shfl_xor_sync(0xffffffffu, h, 16), __shfl_xor_sync(0xffffffffu, l, 16));
+        if (lane < 16) colpart[wid][4 * cq + q] = make_float2(h, l);
+      }
+      __syncthreads();
+      if (tid < TILE) {
+        float2 s0 = colpart[0][tid];
+#pragma unroll
+        for (int w2 = 1; w2 < NT / 32; ++w2) ff_add(s0.x, s0.y, colpart[w2][tid].x, colpart[w2][tid].y);
+        const int col = B * TILE + tid;
+        if (col < n_arr[i]) ypos[sub_off[i] + col] = ff_to_double(s0.x, s0.y) * unscale[i];
+      }
+      __syncthreads();
+    }
+  }
+  if (!ok && tid == 0) {
+    atomicOr(err, (int32_t)DERR_TIMEOUT);
+    for (uint32_t u = t; u < issued; ++u) mbar_wait_bounded(&full[u % S], (u / S) & 1);
+  }
+}
+
+// Explicit-inverse subdomains, float-float: y_J = row part + the slots of the
+// row blocks I > J in order of I, then FP64 times the subdomain's scale.
+__global__ void __launch_bounds__(NT) k_sym_reduce_cf(const int2* __restrict__ items, int nitems,
+                                                      const int64_t* __restrict__ tile_off,
+                                                      const int32_t* __restrict__ sub_off,
+                                                      const int32_t* __restrict__ n_arr,
+                                                      const int32_t* __restrict__ nt_arr,
+                                                      const int64_t* __restrict__ pad_off,
+                                                      const float2* __restrict__ rowpart,
+                                                      const float2* __restrict__ slots,
+                                                      const double* __restrict__ unscale, double* __restrict__ ypos,
+                                                      const int32_t* __restrict__ done) {
+  COUNT_LAUNCH();
+  if (done != nullptr && *done) return;
+  for (int64_t g = blockIdx.x * (int64_t)NT + threadIdx.x; g < (int64_t)nitems * TILE; g += (int64_t)gridDim.x * NT) {
+    const int2 w = items[g / TILE];
+    const int c = (int)(g % TILE);
+    const int i = w.x, J = w.y, nt = nt_arr[i];
+    const int row = J * TILE + c;
+    if (row >= n_arr[i]) continue;
+    float2 y = rowpart[pad_off[i] + row];
+    const int64_t t0 = tile_off[i];
+    for (int I = J + 1; I < nt; ++I) {
+      const float2 sl = slots[(t0 + (int64_t)I * (I + 1) / 2 + J) * TILE + c];
+      ff_add(y.x, y.y, sl.x, sl.y);
+    }
+    ypos[sub_off[i] + row] = ff_to_double(y.x, y.y) * unscale[i];
+  }
+}
+
 // Explicit-inverse subdomains: y_J = (row part from the row pass) + the
 // column contributions S_IJ^T x_I of the row blocks I > J, in order of I.
 // One thread per (item, entry).
@@ -295,13 +536,10 @@ __global__ void __launch_bounds__(NT) k_sym_reduce(const int2* __restrict__ item
   }
 }
 
-// c[col_off[i] + j] = sum_{a < p_i} Z_i[a][j] r[omega_i[a]]  (Z^T r).
+// c[col_off[i] + j] = sum_{a < p_i} Z_i[a][j] r[omega_i[a]]  (Z^T r), FP64.
 // Thread (g, c) of the block sums rows a = g, g + 16, ... of column j0 + c;
 // the 16 row groups are added in a fixed order.
-// ZT = float: the single-precision copy of Z (the FP64 master is rounded to
-// it, so E = Z^T A Z describes exactly this basis) with FP32 products and sums.
-template <typename ZT>
-__global__ void __launch_bounds__(NT) k_coarse_restrict(const ZT* __restrict__ Z, const int64_t* __restrict__ z_off,
+__global__ void __launch_bounds__(NT) k_coarse_restrict(const double* __restrict__ Z, const int64_t* __restrict__ z_off,
                                                         const int32_t* __restrict__ count,
                                                         const int32_t* __restrict__ col_off,
                                                         const int32_t* __restrict__ sub_off,
@@ -311,24 +549,88 @@ __global__ void __launch_bounds__(NT) k_coarse_restrict(const ZT* __restrict__ Z
                                                         const int32_t* __restrict__ done) {
   COUNT_LAUNCH();
   if (done != nullptr && *done) return;
-  __shared__ ZT red[16][17];
+  __shared__ double red[16][17];
   const int i = blockIdx.x;
   const int k = count[i], p = p_arr[i], b0 = sub_off[i];
-  const ZT* Zi = Z + z_off[i];
+  const double* Zi = Z + z_off[i];
   const int g = threadIdx.x >> 4, cc = threadIdx.x & 15;
   for (int j0 = 0; j0 < k; j0 += 16) {
-    ZT acc = 0;
+    double acc = 0;
     if (j0 + cc < k)
-      for (int a = g; a < p; a += 16) acc += Zi[(int64_t)a * nev + j0 + cc] * (ZT)r[omega[b0 + a]];
+      for (int a = g; a < p; a += 16) acc += Zi[(int64_t)a * nev + j0 + cc] * r[omega[b0 + a]];
     red[g][cc] = acc;
     __syncthreads();
     if (threadIdx.x < 16 && j0 + threadIdx.x < k) {
       double s = 0;
-      for (int q = 0; q < 16; ++q) s += (double)red[q][threadIdx.x];
+      for (int q = 0; q < 16; ++q) s += red[q][threadIdx.x];
       c[col_off[i] + j0 + threadIdx.x] = s;
     }
     __syncthreads();
   }
+}
+
+// The same with the single-precision copy of Z (the FP64 master is rounded to
+// it, so E = Z^T A Z describes exactly this basis): r is split into
+// float-float pairs a chunk of rows at a time, products and sums are Dot2
+// (ffloat.cuh), one column group of 16 per pass over the chunk.
+constexpr int CR_GROUPS = 8;  // nev <= 128
+__global__ void __launch_bounds__(NT) k_coarse_restrict_cf(const float* __restrict__ Z,
+                                                           const int64_t* __restrict__ z_off,
+                                                           const int32_t* __restrict__ count,
+                                                           const int32_t* __restrict__ col_off,
+                                                           const int32_t* __restrict__ sub_off,
+                                                           const int32_t* __restrict__ p_arr,
+                                                           const int32_t* __restrict__ omega, int nev,
+                                                           const double* __restrict__ r, double* __restrict__ c,
+                                                           const int32_t* __restrict__ done) {
+  COUNT_LAUNCH();
+  if (done != nullptr && *done) return;
+  __shared__ float2 rs[NT];
+  __shared__ float2 red[16][17];
+  const int i = blockIdx.x;
+  const int k = count[i], p = p_arr[i], b0 = sub_off[i];
+  if (k <= 0) return;
+  const float* Zi = Z + z_off[i];
+  const int g = threadIdx.x >> 4, cc = threadIdx.x & 15;
+  float ah[CR_GROUPS], al[CR_GROUPS];
+#pragma unroll
+  for (int q = 0; q < CR_GROUPS; ++q) { ah[q] = 0.f; al[q] = 0.f; }
+  for (int a0 = 0; a0 < p; a0 += NT) {
+    const int rows = min(NT, p - a0);
+    __syncthreads();
+    if (threadIdx.x < rows) rs[threadIdx.x] = split_ff(r[omega[b0 + a0 + threadIdx.x]]);
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < CR_GROUPS; ++q) {
+      const int j = 16 * q + cc;
+      if (16 * q >= k) break;
+      if (j < k)
+        for (int a = g; a < rows; a += 16) {
+          const float2 x = rs[a];
+          dot2_step(ah[q], al[q], Zi[(int64_t)(a0 + a) * nev + j], x.x, x.y);
+        }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < CR_GROUPS; ++q) {
+    if (16 * q >= k) break;
+    __syncthreads();
+    red[g][cc] = make_float2(ah[q], al[q]);
+    __syncthreads();
+    if (threadIdx.x < 16 && 16 * q + threadIdx.x < k) {
+      float2 t = red[0][threadIdx.x];
+      for (int u = 1; u < 16; ++u) ff_add(t.x, t.y, red[u][threadIdx.x].x, red[u][threadIdx.x].y);
+      c[col_off[i] + 16 * q + threadIdx.x] = ff_to_double(t.x, t.y);
+    }
+  }
+}
+
+// float-float copy of the coarse solution for the single-precision prolongation
+__global__ void k_split_vector(int n, const double* __restrict__ y, float2* __restrict__ yf,
+                               const int32_t* __restrict__ done) {
+  COUNT_LAUNCH();
+  if (done != nullptr && *done) return;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) yf[k] = split_ff(y[k]);
 }
 
 // z[v] = s_v * sum over the occurrences (i, a) of v of y_pos[(i, a)]
@@ -336,7 +638,9 @@ __global__ void __launch_bounds__(NT) k_coarse_restrict(const ZT* __restrict__ Z
 // Restricted one-level part (ras): only the occurrence of v in its owner's
 // I block, i.e. R_i^T D_i with the Boolean D_i.  Deflated form: qadd (= Q r)
 // is added in place of the coarse term; with ypos == nullptr the kernel
-// computes the prolongation Z y_coarse alone.
+// computes the prolongation Z y_coarse alone.  ZT = float: the
+// single-precision copy of Z with the coarse solution as float-float pairs
+// (ycf) and Dot2 products and sums.
 template <typename ZT>
 __global__ void __launch_bounds__(NT) k_apply_pull(int n, int ras, const double* __restrict__ qadd,
                                                    const int32_t* __restrict__ occ_ptr,
@@ -346,9 +650,9 @@ __global__ void __launch_bounds__(NT) k_apply_pull(int n, int ras, const double*
                                                    const int32_t* __restrict__ sub_off, const ZT* __restrict__ Z,
                                                    const int64_t* __restrict__ z_off, const int32_t* __restrict__ count,
                                                    const int32_t* __restrict__ col_off, int nev,
-                                                   const double* __restrict__ yc, const double* __restrict__ ds,
-                                                   double* __restrict__ z, const int32_t* __restrict__ done,
-                                                   ApplyDot dot) {
+                                                   const double* __restrict__ yc, const float2* __restrict__ ycf,
+                                                   const double* __restrict__ ds, double* __restrict__ z,
+                                                   const int32_t* __restrict__ done, ApplyDot dot) {
   COUNT_LAUNCH();
   if (done != nullptr && *done) return;
   double rz = 0;
@@ -366,10 +670,19 @@ __global__ void __launch_bounds__(NT) k_apply_pull(int n, int ras, const double*
       int k = count[i];
       if (k > 0) {
         const ZT* zr = Z + z_off[i] + (int64_t)(own_pos[v] - sub_off[i]) * nev;
-        const double* y = yc + col_off[i];
-        ZT s = 0;
-        for (int j = 0; j < k; ++j) s += zr[j] * (ZT)y[j];
-        acc += (double)s;
+        const int c0 = col_off[i];
+        if constexpr (sizeof(ZT) == 4) {
+          float h = 0.f, l = 0.f;
+          for (int j = 0; j < k; ++j) {
+            const float2 y = ycf[c0 + j];
+            dot2_step(h, l, zr[j], y.x, y.y);
+          }
+          acc += ff_to_double(h, l);
+        } else {
+          double s = 0;
+          for (int j = 0; j < k; ++j) s += zr[j] * yc[c0 + j];
+          acc += s;
+        }
       }
     }
     z[v] = acc;
@@ -384,10 +697,52 @@ __global__ void __launch_bounds__(NT) k_apply_pull(int n, int ras, const double*
   }
 }
 
-// Local part up to the per-position results in dn.ypos.
-// SPD: t = W x (row pass over the lower tiles of W), then y = W^T t (column
-// pass); general: y = A^_ii^{-1} x (row pass over all tiles).
-template <typename T>
+// x for the single-precision local part: per subdomain the scale 2^-e with
+// max |r s| = f 2^e, f in [1/2, 1) (exact), the scaled entries split into
+// float-float pairs (zero beyond n_i), and unscale[i] = 2^e.
+__global__ void __launch_bounds__(NT) k_gather_x_cf(const int32_t* __restrict__ omega,
+                                                    const int32_t* __restrict__ sub_off,
+                                                    const int32_t* __restrict__ n_arr,
+                                                    const int32_t* __restrict__ nt_arr,
+                                                    const int64_t* __restrict__ pad_off, const double* __restrict__ r,
+                                                    const double* __restrict__ ds, float2* __restrict__ xs,
+                                                    double* __restrict__ unscale, const int32_t* __restrict__ done) {
+  COUNT_LAUNCH();
+  if (done != nullptr && *done) return;
+  __shared__ double red[NT / 32];
+  const int i = blockIdx.x;
+  const int n = n_arr[i], np = nt_arr[i] * TILE, b0 = sub_off[i];
+  double m = 0;
+  for (int a = threadIdx.x; a < n; a += NT) {
+    const int g = omega[b0 + a];
+    m = fmax(m, fabs(r[g] * ds[g]));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  double mx = red[0];
+#pragma unroll
+  for (int w = 1; w < NT / 32; ++w) mx = fmax(mx, red[w]);
+  int e = 0;
+  if (mx > 0 && isfinite(mx)) frexp(mx, &e);
+  const double sc = ldexp(1.0, -e);
+  if (threadIdx.x == 0) unscale[i] = ldexp(1.0, e);
+  float2* out = xs + pad_off[i];
+  for (int a = threadIdx.x; a < np; a += NT) {
+    float2 v = make_float2(0.f, 0.f);
+    if (a < n) {
+      const int g = omega[b0 + a];
+      v = split_ff(r[g] * ds[g] * sc);
+    }
+    out[a] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host side.  T = double: the FP64 handle (tiles, vectors and sums in FP64).
+// T = float: single-precision storage with the float-float kernels above.
+// ---------------------------------------------------------------------------
 unsigned tile_grid(const Handle& h, int nitems) {
   // resident blocks per SM chosen by tune_apply: enough to saturate HBM
   // while leaving room for the coarse kernels on the side stream
@@ -397,18 +752,27 @@ unsigned tile_grid(const Handle& h, int nitems) {
 template <typename T>
 void gather_x(Handle& h, const double* r, cudaStream_t s, const int32_t* done) {
   Dense& dn = h.dn;
-  k_gather_x<T><<<h.N, NT, 0, s>>>(h.ov.omega, h.ov.sub_off, h.dev_n, dn.nt, dn.pad_off, r, h.dscale, (T*)dn.xpad,
-                                   done);
+  if constexpr (sizeof(T) == 4)
+    k_gather_x_cf<<<h.N, NT, 0, s>>>(h.ov.omega, h.ov.sub_off, h.dev_n, dn.nt, dn.pad_off, r, h.dscale,
+                                     (float2*)dn.xpad, dn.xunscale, done);
+  else
+    k_gather_x<double><<<h.N, NT, 0, s>>>(h.ov.omega, h.ov.sub_off, h.dev_n, dn.nt, dn.pad_off, r, h.dscale,
+                                          (double*)dn.xpad, done);
 }
 
 template <typename T, bool SPD, bool COL, typename TS = T>
-void launch_pass(Handle& h, int nitems, const int2* items, const T* vin, T* tout, cudaStream_t s,
+void launch_pass(Handle& h, int nitems, const int2* items, const void* vin, void* tout, cudaStream_t s,
                  const int32_t* done) {
   Dense& dn = h.dn;
-  const unsigned g = tile_grid<T>(h, nitems);
-  k_tile_pass<T, TS, SPD, COL><<<g, NT, Stages<TS>::SMEM, s>>>((const TS*)dn.tiles, dn.tile_off, items, nitems,
-                                                                h.ov.sub_off, h.dev_n, dn.nt, dn.pad_off, vin, tout,
-                                                                dn.ypos, dn.sym, (T*)dn.slots, dn.err, done);
+  const unsigned g = tile_grid(h, nitems);
+  if constexpr (sizeof(T) == 4)
+    k_tile_pass_cf<TS, SPD, COL><<<g, NT, Stages<TS>::SMEM, s>>>(
+        (const TS*)dn.tiles, dn.tile_off, items, nitems, h.ov.sub_off, h.dev_n, dn.nt, dn.pad_off,
+        (const float2*)vin, (float2*)tout, dn.ypos, dn.xunscale, dn.sym, (float2*)dn.slots, dn.err, done);
+  else
+    k_tile_pass<double, double, SPD, COL><<<g, NT, Stages<double>::SMEM, s>>>(
+        (const double*)dn.tiles, dn.tile_off, items, nitems, h.ov.sub_off, h.dev_n, dn.nt, dn.pad_off,
+        (const double*)vin, (double*)tout, dn.ypos, dn.sym, (double*)dn.slots, dn.err, done);
 }
 
 template <typename T>
@@ -417,17 +781,13 @@ void row_pass(Handle& h, cudaStream_t s, const int32_t* done) {
   if constexpr (sizeof(T) == 4) {
     if (dn.n_row_items_h > 0) {
       // explicit inverses stored in FP16, then the rest (FP32 tiles)
-      launch_pass<T, true, false, __half>(h, dn.n_row_items_h, dn.row_items_h, (const T*)dn.xpad, (T*)dn.tpad, s,
-                                          done);
-      if (dn.n_row_items_f > 0)
-        launch_pass<T, true, false>(h, dn.n_row_items_f, dn.row_items_f, (const T*)dn.xpad, (T*)dn.tpad, s, done);
+      launch_pass<T, true, false, __half>(h, dn.n_row_items_h, dn.row_items_h, dn.xpad, dn.tpad, s, done);
+      if (dn.n_row_items_f > 0) launch_pass<T, true, false>(h, dn.n_row_items_f, dn.row_items_f, dn.xpad, dn.tpad, s, done);
       return;
     }
   }
-  if (h.opt.spd)
-    launch_pass<T, true, false>(h, dn.n_row_items, dn.row_items, (const T*)dn.xpad, (T*)dn.tpad, s, done);
-  else
-    launch_pass<T, false, false>(h, dn.n_row_items, dn.row_items, (const T*)dn.xpad, (T*)dn.tpad, s, done);
+  if (h.opt.spd) launch_pass<T, true, false>(h, dn.n_row_items, dn.row_items, dn.xpad, dn.tpad, s, done);
+  else launch_pass<T, false, false>(h, dn.n_row_items, dn.row_items, dn.xpad, dn.tpad, s, done);
 }
 
 // second stage of the SPD local part: y = W^T t for the two-pass subdomains,
@@ -435,12 +795,17 @@ void row_pass(Handle& h, cudaStream_t s, const int32_t* done) {
 template <typename T>
 void col_pass(Handle& h, cudaStream_t s, const int32_t* done) {
   Dense& dn = h.dn;
-  if (dn.n_col_items > 0)
-    launch_pass<T, true, true>(h, dn.n_col_items, dn.col_items, (const T*)dn.tpad, nullptr, s, done);
+  if (dn.n_col_items > 0) launch_pass<T, true, true>(h, dn.n_col_items, dn.col_items, dn.tpad, nullptr, s, done);
   if (dn.n_sym_items > 0) {
     const unsigned g = (unsigned)std::min<int64_t>(ceil_div((int64_t)dn.n_sym_items * TILE, NT), (int64_t)h.num_sms * 16);
-    k_sym_reduce<T><<<g, NT, 0, s>>>(dn.sym_items, dn.n_sym_items, dn.tile_off, h.ov.sub_off, h.dev_n, dn.nt,
-                                      dn.pad_off, (const T*)dn.tpad, (const T*)dn.slots, dn.ypos, done);
+    if constexpr (sizeof(T) == 4)
+      k_sym_reduce_cf<<<g, NT, 0, s>>>(dn.sym_items, dn.n_sym_items, dn.tile_off, h.ov.sub_off, h.dev_n, dn.nt,
+                                       dn.pad_off, (const float2*)dn.tpad, (const float2*)dn.slots, dn.xunscale,
+                                       dn.ypos, done);
+    else
+      k_sym_reduce<double><<<g, NT, 0, s>>>(dn.sym_items, dn.n_sym_items, dn.tile_off, h.ov.sub_off, h.dev_n, dn.nt,
+                                            dn.pad_off, (const double*)dn.tpad, (const double*)dn.slots, dn.ypos,
+                                            done);
   }
 }
 
@@ -449,13 +814,19 @@ template <typename T>
 void prepare_tile_passes() {
   static bool done = false;
   if (done) return;
-  const int sm = (int)Stages<T>::SMEM;
-  CK(cudaFuncSetAttribute(k_tile_pass<T, T, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-  CK(cudaFuncSetAttribute(k_tile_pass<T, T, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-  CK(cudaFuncSetAttribute(k_tile_pass<T, T, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-  if constexpr (sizeof(T) == 4)
-    CK(cudaFuncSetAttribute(k_tile_pass<T, __half, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if constexpr (sizeof(T) == 4) {
+    const int sm = (int)Stages<float>::SMEM;
+    CK(cudaFuncSetAttribute(k_tile_pass_cf<float, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    CK(cudaFuncSetAttribute(k_tile_pass_cf<float, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    CK(cudaFuncSetAttribute(k_tile_pass_cf<float, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    CK(cudaFuncSetAttribute(k_tile_pass_cf<__half, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             (int)Stages<__half>::SMEM));
+  } else {
+    const int sm = (int)Stages<double>::SMEM;
+    CK(cudaFuncSetAttribute(k_tile_pass<double, double, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    CK(cudaFuncSetAttribute(k_tile_pass<double, double, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    CK(cudaFuncSetAttribute(k_tile_pass<double, double, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  }
   done = true;
 }
 
@@ -466,19 +837,24 @@ void apply_local(Handle& h, const double* r, cudaStream_t s, const int32_t* done
   if (h.opt.spd) col_pass<T>(h, s, done);
 }
 
-// Z^T r and the coarse solve; returns the coarse solution (or null).
+// Z^T r and the coarse solve; returns the coarse solution (or null).  With
+// the single-precision copy of Z the solution is also split into
+// float-float pairs (co.ycf) for the prolongation.
 const double* apply_coarse(Handle& h, const double* r, cudaStream_t s, const int32_t* done) {
   Coarse& co = h.co;
   if (co.n_C == 0) return nullptr;
   double* c = co.cvec;
   double* y = co.cvec + round_up(co.n_C, 64);
   if (co.Zf)
-    k_coarse_restrict<float><<<h.N, NT, 0, s>>>(co.Zf, co.z_off, co.count, co.col_off, h.ov.sub_off, h.dev_p,
-                                                h.ov.omega, h.nev, r, c, done);
+    k_coarse_restrict_cf<<<h.N, NT, 0, s>>>(co.Zf, co.z_off, co.count, co.col_off, h.ov.sub_off, h.dev_p,
+                                            h.ov.omega, h.nev, r, c, done);
   else
-    k_coarse_restrict<double><<<h.N, NT, 0, s>>>(co.Z, co.z_off, co.count, co.col_off, h.ov.sub_off, h.dev_p,
-                                                 h.ov.omega, h.nev, r, c, done);
+    k_coarse_restrict<<<h.N, NT, 0, s>>>(co.Z, co.z_off, co.count, co.col_off, h.ov.sub_off, h.dev_p, h.ov.omega,
+                                         h.nev, r, c, done);
   coarse_solve(h, c, y, s, done);
+  if (co.Zf)
+    k_split_vector<<<(unsigned)std::min<int64_t>(ceil_div(co.n_C, NT), 152 * 4), NT, 0, s>>>(co.n_C, y, co.ycf,
+                                                                                              done);
   return y;
 }
 
@@ -494,12 +870,12 @@ void apply_pull(Handle& h, const double* yc, double* z, cudaStream_t s, const in
   unsigned gp = (unsigned)std::min<int64_t>(ceil_div(h.n, NT), 152 * 16);
   if (co.Zf)
     k_apply_pull<float><<<gp, NT, 0, s>>>(h.n, ras, qadd, h.ov.occ_ptr, h.ov.occ_pos, yp, h.part, h.ov.own_pos,
-                                          h.ov.sub_off, co.Zf, co.z_off, co.count, co.col_off, h.nev, yc, h.dscale,
-                                          z, done, dot ? *dot : ApplyDot());
+                                          h.ov.sub_off, co.Zf, co.z_off, co.count, co.col_off, h.nev, yc, co.ycf,
+                                          h.dscale, z, done, dot ? *dot : ApplyDot());
   else
     k_apply_pull<double><<<gp, NT, 0, s>>>(h.n, ras, qadd, h.ov.occ_ptr, h.ov.occ_pos, yp, h.part, h.ov.own_pos,
-                                           h.ov.sub_off, co.Z, co.z_off, co.count, co.col_off, h.nev, yc, h.dscale,
-                                           z, done, dot ? *dot : ApplyDot());
+                                           h.ov.sub_off, co.Z, co.z_off, co.count, co.col_off, h.nev, yc, nullptr,
+                                           h.dscale, z, done, dot ? *dot : ApplyDot());
 }
 
 // The coarse part (Z^T r, the level-by-level coarse solve) is independent of

@@ -126,6 +126,7 @@ void build_coarse(Handle& h, cudaStream_t s) {
   co.E = mem.alloc<double>((int64_t)ldE * ldE);
   co.E_copy = mem.alloc<double>((int64_t)ldE * ldE);
   co.cvec = mem.alloc<double>(3LL * ldE);
+  if (co.Zf) co.ycf = mem.alloc<float2>(co.n_C);
   CK(cudaMemsetAsync(co.E, 0, sizeof(double) * ldE * ldE, s));
   std::vector<int64_t> az(N);
   int64_t t = 0;

@@ -53,8 +53,10 @@ struct Dense {
   int64_t* dinv_off = nullptr;
   void* tiles = nullptr;              // apply tiles, TILE*TILE each
   int64_t* pad_off = nullptr;         // start of subdomain i in the padded position space (nt_i * TILE each)
-  void* xpad = nullptr;               // apply: gathered, scaled r in the padded space (local precision)
-  void* tpad = nullptr;               // apply: t = W x (SPD first pass), padded space
+  void* xpad = nullptr;               // apply: gathered, scaled r in the padded space (FP64, or float-float
+                                      // pairs scaled per subdomain by a power of two in single precision)
+  void* tpad = nullptr;               // apply: t = W x (SPD first pass) or the explicit inverses' row part
+  double* xunscale = nullptr;         // single precision: per subdomain, the inverse of the scale of xpad
   int2* row_items = nullptr;          // (subdomain, row block), most tiles first
   int2* col_items = nullptr;          // (subdomain, column block) of two-pass subdomains, most tiles first
   int2* sym_items = nullptr;          // (subdomain, block) of explicit-inverse subdomains
@@ -69,6 +71,7 @@ struct Dense {
   int2 *row_items_h = nullptr, *row_items_f = nullptr;
   int n_row_items_h = 0, n_row_items_f = 0;
   void* slots = nullptr;              // explicit-inverse column contributions, TILE per stored tile
+                                      // (FP64, or float-float pairs in single precision)
   double* ypos = nullptr;             // per omega position: local solution before the pull
   int64_t n_tiles = 0, n_work = 0, n_xs = 0, n_s = 0, n_pad = 0;
   int32_t* err = nullptr;             // device error word
@@ -95,6 +98,7 @@ struct Coarse {
   double* E_copy = nullptr;           // as assembled
   double* Einv_diag = nullptr;        // inverses of the diagonal factor blocks
   double* cvec = nullptr;             // coarse work vectors (2 x n_C)
+  float2* ycf = nullptr;              // single precision: the coarse solution as float-float pairs
 };
 
 struct Krylov {

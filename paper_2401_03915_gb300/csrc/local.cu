@@ -764,8 +764,10 @@ void run_local(Handle& h, cudaStream_t s) {
   dn.dinv = mem.alloc<T>(std::max<int64_t>(ss, 1));
   dn.dinv_off = dn.s_off;
   dn.tiles = mem.alloc<T>(tl * TILE * TILE);
-  dn.xpad = mem.alloc<T>(pt);
-  dn.tpad = mem.alloc<T>(pt);
+  // single precision: the apply's vectors are float-float pairs
+  dn.xpad = mem.alloc<T>(pt * (sizeof(T) == 4 ? 2 : 1));
+  dn.tpad = mem.alloc<T>(pt * (sizeof(T) == 4 ? 2 : 1));
+  if (sizeof(T) == 4) dn.xunscale = mem.alloc<double>(N);
   dn.ypos = mem.alloc<double>(ov.sum_n);
   h.dev_n = d_n; h.dev_m = d_m; h.dev_p = d_p;
   // -- gather A_ii
@@ -836,7 +838,7 @@ void run_local(Handle& h, cudaStream_t s) {
   CK(cudaMemcpyAsync(dn.row_items, rv.data(), sizeof(int2) * rv.size(), cudaMemcpyHostToDevice, s));
   if (!cv.empty()) CK(cudaMemcpyAsync(dn.col_items, cv.data(), sizeof(int2) * cv.size(), cudaMemcpyHostToDevice, s));
   if (!si.empty()) CK(cudaMemcpyAsync(dn.sym_items, si.data(), sizeof(int2) * si.size(), cudaMemcpyHostToDevice, s));
-  if (spd && !si.empty()) dn.slots = mem.alloc<T>(tl * TILE);
+  if (spd && !si.empty()) dn.slots = mem.alloc<T>(tl * TILE * (sizeof(T) == 4 ? 2 : 1));
   if constexpr (sizeof(T) == 4) {
     if (h.s16 && spd && !si.empty()) {
       // which explicit inverses go to FP16, then convert their tiles in place

@@ -411,11 +411,11 @@ def test_c2_full_size_fp32(P):
     rel = np.linalg.norm(prob.b - A @ x.cpu().numpy()) / np.linalg.norm(prob.b)
     assert info.converged and rel <= 1e-8
     it_ref = ref["pcg_iterations_two_level"]
-    # Single-precision local solves cost PCG iterations: in the ~10 subdomains
-    # holding a floating 10^6 inclusion, cond(A^_ii) ~ 10^7 and W = L^{-1} in
-    # FP32 perturbs A_ii^{-1} by up to ~40% in the A_ii-norm.  Measured: 296-297
-    # iterations against 247-267 for the FP64 path (FP64 local solves with the
-    # FP32 coarse space give the FP64 count), i.e. +11..20%; the bound leaves
-    # room for that and fails on anything worse.
-    assert info.iterations <= 1.25 * it_ref, (info.iterations, it_ref)
+    # The local solves keep FP32 storage but evaluate in float-float
+    # arithmetic (inputs split into hi + lo pairs, exact products, compensated
+    # sums), as do the restriction and prolongation with the FP32 copy of Z:
+    # FP32 rounding of the apply's input, sums or output is what costs PCG
+    # iterations, not the stored precision.  Bound: within 10% of the FP64
+    # preconditioner's count.
+    assert info.iterations <= 1.1 * it_ref, (info.iterations, it_ref)
     pre.close()
