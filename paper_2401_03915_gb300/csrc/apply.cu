@@ -108,6 +108,17 @@ struct Stages {
 __device__ __forceinline__ float tile_val(__half v) { return __half2float(v); }
 __device__ __forceinline__ float tile_val(float v) { return v; }
 __device__ __forceinline__ double tile_val(double v) { return v; }
+// four consecutive stored values of a tile row as two pairs
+__device__ __forceinline__ void tile_row4(const float* p, float2& v01, float2& v23) {
+  const float4 u = *reinterpret_cast<const float4*>(p);
+  v01 = make_float2(u.x, u.y);
+  v23 = make_float2(u.z, u.w);
+}
+__device__ __forceinline__ void tile_row4(const __half* p, float2& v01, float2& v23) {
+  const uint2 u = *reinterpret_cast<const uint2*>(p);
+  v01 = __half22float2(*reinterpret_cast<const __half2*>(&u.x));
+  v23 = __half22float2(*reinterpret_cast<const __half2*>(&u.y));
+}
 
 // T: arithmetic and vectors; TS: the stored tiles (T, or FP16 for the
 // explicit inverses kept in half precision).  Every tile occupies a slot of
@@ -283,25 +294,40 @@ __global__ void __launch_bounds__(NT) k_tile_pass(const TS* __restrict__ tiles, 
 // Row pass (COL = false), item (i, B): thread (rg, cq) owns rows rg + 16 a and
 // columns 4 cq .. 4 cq + 3 of every tile, one biased accumulator per row,
 // renormalised after each tile; the 16 column quads of a row are merged at
-// the end of the item.  Explicit-inverse subdomain, tile (B, k), k < B: the
-// column contribution S_Bk^T x_B is a 4-term biased chain per thread and
-// column, merged across the two row groups of a warp and across the 8 warps
-// (through shared memory) into the tile's slot as a float-float pair.
-// Outputs: the row part (SPD) as float-float in tout, or y (general) per
-// Omega position in FP64 times the subdomain's scale.  Column pass (COL =
-// true): y_B = sum_{I >= B} W_IB^T t_I with one biased accumulator per column.
+// the end of the item.  Explicit-inverse subdomains use one bias per row block
+// (sym_bias, a bound on every partial sum of its rows), so the quads' partial
+// sums add exactly; the others keep a running bound per thread.  Tile (B, k),
+// k < B, of an explicit inverse also gives the column contribution
+// S_Bk^T x_B: a 4-term chain per thread and column biased by row block k's
+// bound, added exactly across the warps through shared memory into the
+// tile's slot.  Outputs: the row part (SPD) as float-float in tout, or y
+// (general) per Omega position in FP64 times the subdomain's scale.  Column
+// pass (COL = true): y_B = sum_{I >= B} W_IB^T t_I, one running-bound
+// accumulator per column.
+//
+// Pipeline: thread 0 issues the bulk copies into a ring of S slots, each
+// completing on its own mbarrier.  One block barrier per tile: after the wait
+// for tile t every thread has finished tile t - 1, so thread 0 then refills
+// tile t - 1's slot and the first 64 threads add up tile t - 1's column
+// partials (double-buffered) into its slot.  The producer's position lives in
+// shared memory (only thread 0 touches it).  Every wait is bounded; a wait
+// that gives up sets DERR_TIMEOUT, the block agrees on it at the barrier and
+// leaves after a bounded wait for its copies in flight.
 // ---------------------------------------------------------------------------
+struct TileProducer {
+  const void* base;  // tile 0 of the current item
+  int it, k, n, B;
+  uint32_t issued;
+};
+
 template <typename TS, bool SPD, bool COL>
-__global__ void __launch_bounds__(NT) k_tile_pass_cf(const TS* __restrict__ tiles, const int64_t* __restrict__ tile_off,
-                                                     const int2* __restrict__ items, int nitems,
-                                                     const int32_t* __restrict__ sub_off,
-                                                     const int32_t* __restrict__ n_arr,
-                                                     const int32_t* __restrict__ nt_arr,
-                                                     const int64_t* __restrict__ pad_off,
-                                                     const float2* __restrict__ vin, float2* __restrict__ tout,
-                                                     double* __restrict__ ypos, const double* __restrict__ unscale,
-                                                     const int8_t* __restrict__ sym, float2* __restrict__ slots,
-                                                     int32_t* __restrict__ err, const int32_t* __restrict__ done) {
+__global__ void __launch_bounds__(NT, 4) k_tile_pass_cf(const TS* __restrict__ tiles, const TileItem* __restrict__ desc,
+                                                        int nitems, const float* __restrict__ vin,
+                                                        float* __restrict__ tout, int64_t plane,
+                                                        double* __restrict__ ypos,
+                                                        const double* __restrict__ unscale,
+                                                        float2* __restrict__ slots, const float* __restrict__ sym_bias,
+                                                        int32_t* __restrict__ err, const int32_t* __restrict__ done) {
   COUNT_LAUNCH();
   if (done != nullptr && *done) return;
   using St = Stages<TS>;
@@ -310,138 +336,204 @@ __global__ void __launch_bounds__(NT) k_tile_pass_cf(const TS* __restrict__ tile
   extern __shared__ __align__(128) unsigned char smraw[];
   TS* stage = reinterpret_cast<TS*>(smraw);
   __shared__ __align__(8) uint64_t full[S];
-  __shared__ float2 colpart[NT / 32][TILE];
+  __shared__ float2 colpart[2][NT / 32][TILE];
+  __shared__ TileProducer prod;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, cq = tid & 15, rg = tid >> 4;
-  auto count = [&](int it) -> int {
-    const int2 w = items[it];
-    const int nt = nt_arr[w.x];
-    return COL ? nt - w.y : (SPD ? w.y + 1 : nt);
+  // ---- producer (thread 0): the next tile to copy
+  auto p_load = [&]() {
+    if (prod.it >= nitems) return;
+    const TileItem& d = desc[prod.it];
+    prod.B = d.B;
+    prod.n = d.cnt;
+    prod.base = tiles + d.tile0 * SLOT;
   };
-  auto src = [&](int it, int k) -> const TS* {
-    const int2 w = items[it];
-    const int nt = nt_arr[w.x];
-    int64_t t;
-    if (COL) { const int64_t I = w.y + k; t = I * (I + 1) / 2 + w.y; }
-    else t = SPD ? (int64_t)w.y * (w.y + 1) / 2 + k : (int64_t)w.y * nt + k;
-    return tiles + (tile_off[w.x] + t) * SLOT;
+  auto issue = [&]() {
+    if (prod.it >= nitems) return;
+    const int slot = (int)(prod.issued % S);
+    const TS* base = static_cast<const TS*>(prod.base);
+    const TS* src;
+    if (COL) { const int64_t I = prod.B + prod.k; src = base + (I * (I + 1) / 2 + prod.B) * SLOT; }
+    else src = base + (int64_t)prod.k * SLOT;
+    mbar_expect_tx(&full[slot], St::BYTES);
+    bulk_g2s(stage + (size_t)slot * TILE * TILE, src, St::BYTES, &full[slot]);
+    ++prod.issued;
+    if (++prod.k == prod.n) {
+      prod.it += gridDim.x;
+      prod.k = 0;
+      p_load();
+    }
   };
   if (tid == 0) {
     for (int q = 0; q < S; ++q) mbar_init(&full[q], 1);
     fence_mbar_init();
+    prod.it = blockIdx.x;
+    prod.k = 0;
+    prod.issued = 0;
+    p_load();
+    for (int q = 0; q < S; ++q) issue();
   }
-  __syncthreads();
-  int p_it = blockIdx.x, p_k = 0, p_n = p_it < nitems ? count(p_it) : 0;
-  uint32_t issued = 0;
-  auto issue = [&](int slot) {
-    if (p_it >= nitems) return;
-    mbar_expect_tx(&full[slot], St::BYTES);
-    bulk_g2s(stage + (size_t)slot * TILE * TILE, src(p_it, p_k), St::BYTES, &full[slot]);
-    ++issued;
-    if (++p_k == p_n) {
-      p_it += gridDim.x;
-      p_k = 0;
-      p_n = p_it < nitems ? count(p_it) : 0;
+  __syncthreads();  // the barriers are initialised before any thread waits on them
+  uint32_t t = 0;              // tiles consumed
+  uint32_t nc = 0;             // tiles with column contributions so far (partials buffer)
+  float2* pend = nullptr;      // slot of the previous tile's column contributions, to be added up
+  bool ok = true;
+  // after the barrier of a tile: refill the previous tile's slot, add up its
+  // column partials
+  auto after_barrier = [&]() {
+    if (tid == 0 && t > 0) {
+      fence_proxy_async();  // the block's reads of the slot come before the copy's writes
+      issue();
+    }
+    if (pend != nullptr) {
+      // every warp adds up 8 columns: lane (g, c) the partials 2g, 2g + 1 of
+      // column 8 wid + c, then the 4 groups in a fixed shuffle tree (the P
+      // sums are exact: multiples of ulp(A)/2 below A/4)
+      const float2 (*cp)[TILE] = colpart[(nc - 1) & 1];
+      const int c = 8 * wid + (lane & 7), g = lane >> 3;
+      float P = __fadd_rn(cp[2 * g][c].x, cp[2 * g + 1][c].x);
+      float l = __fadd_rn(cp[2 * g][c].y, cp[2 * g + 1][c].y);
+      P = __fadd_rn(P, __shfl_xor_sync(0xffffffffu, P, 8));
+      l = __fadd_rn(l, __shfl_xor_sync(0xffffffffu, l, 8));
+      P = __fadd_rn(P, __shfl_xor_sync(0xffffffffu, P, 16));
+      l = __fadd_rn(l, __shfl_xor_sync(0xffffffffu, l, 16));
+      if (g == 0) {
+        float h, e;
+        two_sum(P, l, h, e);
+        pend[c] = make_float2(h, e);
+      }
+      pend = nullptr;
     }
   };
-  if (tid == 0)
-    for (int q = 0; q < S; ++q) issue(q);
-  uint32_t t = 0;
-  bool ok = true;
+  // the stage holding tile t, once its copy has landed (false: a wait gave up)
+  auto wait_tile = [&]() -> bool {
+    const int slot = (int)(t % S);
+    const bool got = mbar_try_wait(&full[slot], (t / S) & 1) || mbar_wait_bounded(&full[slot], (t / S) & 1);
+    if (!__syncthreads_and(got)) return false;
+    after_barrier();
+    return true;
+  };
   for (int it = blockIdx.x; it < nitems && ok; it += gridDim.x) {
-    const int2 w = items[it];
-    const int i = w.x, B = w.y, nt = nt_arr[i];
-    const int cnt = COL ? nt - B : (SPD ? B + 1 : nt);
-    const float2* vb = vin + pad_off[i];
-    const bool symi = !COL && SPD && sym != nullptr && sym[i];
-    float2 xb[4];
-    if (symi) {
+    const TileItem& d = desc[it];
+    const int B = d.B, cnt = d.cnt;
+    const float* vh = vin + d.pad;  // hi plane of the item's subdomain
+    const float* vl = vh + plane;   // lo plane
+    if (!COL && SPD && d.symi) {
+      // ---- explicit inverse: one fixed bias for the whole row block (it bounds
+      // every partial sum of its rows) shared by all threads, so that partial
+      // sums add exactly
+      const float* bias_i = sym_bias + d.bias0;
+      float xbh[4], xbl[4];
 #pragma unroll
-      for (int a = 0; a < 4; ++a) xb[a] = vb[B * TILE + rg + 16 * a];
+      for (int a = 0; a < 4; ++a) { xbh[a] = vh[B * TILE + rg + 16 * a]; xbl[a] = vl[B * TILE + rg + 16 * a]; }
+      float2* slot_base = slots + d.slot0 * TILE;
+      const float Ar = bias_i[B];
+      float rh[4], rl[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) { rh[a] = Ar; rl[a] = 0.f; }
+      for (int k = 0; k < cnt; ++k, ++t) {
+        const bool colc = k < B;
+        const float4 h4 = *reinterpret_cast<const float4*>(vh + k * TILE + 4 * cq);
+        const float4 l4 = *reinterpret_cast<const float4*>(vl + k * TILE + 4 * cq);
+        const float Ac = colc ? bias_i[k] : 0.f;
+        if (!wait_tile()) { ok = false; break; }
+        const TS* tile = stage + (size_t)(t % S) * TILE * TILE;
+        const float xh[4] = {h4.x, h4.y, h4.z, h4.w}, xl[4] = {l4.x, l4.y, l4.z, l4.w};
+        float ch[4] = {Ac, Ac, Ac, Ac}, cl[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          float2 v01, v23;
+          tile_row4(tile + (rg + 16 * a) * TILE + 4 * cq, v01, v23);
+          const float v[4] = {v01.x, v01.y, v23.x, v23.y};
+#pragma unroll
+          for (int q = 0; q < 4; ++q) bias_step1(rh[a], rl[a], v[q], xh[q], xl[q]);
+          bias_renorm1(rh[a], rl[a]);
+          if (colc) {
+            // column contributions c_q = sum_a v[a][q] xb_a, biased by the
+            // bound of row block k (the column segment is part of those rows)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) bias_step1(ch[q], cl[q], v[q], xbh[a], xbl[a]);
+          }
+        }
+        if (colc) {
+          // the 16 row groups' partials P = hi - A add exactly; the two row
+          // groups of a warp here, the 8 warps after the next barrier
+          float2 (*cp)[TILE] = colpart[nc & 1];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            float P = __fsub_rn(ch[q], Ac), l = cl[q];
+            P = __fadd_rn(P, __shfl_xor_sync(0xffffffffu, P, 16));
+            l = __fadd_rn(l, __shfl_xor_sync(0xffffffffu, l, 16));
+            if (lane < 16) cp[wid][4 * cq + q] = make_float2(P, l);
+          }
+          pend = slot_base + (int64_t)k * TILE;
+          ++nc;
+        }
+      }
+      if (!ok) break;
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        // the 16 column quads' partial sums add exactly (common bias)
+        float h = __fsub_rn(rh[a], Ar), l = rl[a];
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) {
+          h = __fadd_rn(h, __shfl_xor_sync(0xffffffffu, h, o));
+          l = __fadd_rn(l, __shfl_xor_sync(0xffffffffu, l, o));
+        }
+        float e;
+        two_sum(h, l, h, e);
+        if (cq == 0) {
+          const int row = B * TILE + rg + 16 * a;
+          tout[d.pad + row] = h;
+          tout[plane + d.pad + row] = e;
+        }
+      }
+      continue;
     }
-    float2* slot_base = symi ? slots + (tile_off[i] + (int64_t)B * (B + 1) / 2) * TILE : nullptr;
+    // ---- W = L^{-1} (two-pass subdomains), the general inverse, or the
+    // column pass: a running bound per thread and accumulator
     BiasAcc acc[4];
 #pragma unroll
     for (int a = 0; a < 4; ++a) bias_init(acc[a]);
     for (int k = 0; k < cnt; ++k, ++t) {
-      const int slot = (int)(t % S);
-      float2 xv[4];
+      float xh[4], xl[4];
       if (COL) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) xv[q] = vb[(B + k) * TILE + rg + 16 * q];
+        for (int q = 0; q < 4; ++q) {
+          xh[q] = vh[(B + k) * TILE + rg + 16 * q];
+          xl[q] = vl[(B + k) * TILE + rg + 16 * q];
+        }
       } else {
-        const float4* xp = reinterpret_cast<const float4*>(vb + k * TILE + 4 * cq);
-        const float4 u0 = xp[0], u1 = xp[1];
-        xv[0] = make_float2(u0.x, u0.y); xv[1] = make_float2(u0.z, u0.w);
-        xv[2] = make_float2(u1.x, u1.y); xv[3] = make_float2(u1.z, u1.w);
+        const float4 h4 = *reinterpret_cast<const float4*>(vh + k * TILE + 4 * cq);
+        const float4 l4 = *reinterpret_cast<const float4*>(vl + k * TILE + 4 * cq);
+        xh[0] = h4.x; xh[1] = h4.y; xh[2] = h4.z; xh[3] = h4.w;
+        xl[0] = l4.x; xl[1] = l4.y; xl[2] = l4.z; xl[3] = l4.w;
       }
-      const bool got = mbar_wait_bounded(&full[slot], (t / S) & 1);
-      if (!__syncthreads_and(got)) { ok = false; break; }
-      const TS* tile = stage + (size_t)slot * TILE * TILE;
+      if (!wait_tile()) { ok = false; break; }
+      const TS* tile = stage + (size_t)(t % S) * TILE * TILE;
       float v[4][4];
 #pragma unroll
       for (int a = 0; a < 4; ++a) {
-        const TS* rp = tile + (rg + 16 * a) * TILE + 4 * cq;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) v[a][q] = tile_val(rp[q]);
+        float2 v01, v23;
+        tile_row4(tile + (rg + 16 * a) * TILE + 4 * cq, v01, v23);
+        v[a][0] = v01.x; v[a][1] = v01.y; v[a][2] = v23.x; v[a][3] = v23.y;
       }
-      if (!COL) {
-        // rows: acc[a] += sum_q v[a][q] x_q
+      // rows: acc[a] += sum_q v[a][q] x_q; columns: acc[q] += sum_a v[a][q] t_a
 #pragma unroll
-        for (int a = 0; a < 4; ++a) {
-          float tb = 0.f;
+      for (int a = 0; a < 4; ++a) {
+        float tb = 0.f;
 #pragma unroll
-          for (int q = 0; q < 4; ++q) tb = __fmaf_ru(fabsf(v[a][q]), fabsf(xv[q].x), tb);
-          bias_reserve(acc[a], tb);
-#pragma unroll
-          for (int q = 0; q < 4; ++q) bias_step(acc[a], v[a][q], xv[q].x, xv[q].y);
-          bias_renorm(acc[a]);
-        }
-      } else {
-        // columns: acc[q] += sum_a v[a][q] t_a
+        for (int q = 0; q < 4; ++q)
+          tb = COL ? __fmaf_ru(fabsf(v[q][a]), fabsf(xh[q]), tb) : __fmaf_ru(fabsf(v[a][q]), fabsf(xh[q]), tb);
+        bias_reserve(acc[a], tb);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          float tb = 0.f;
-#pragma unroll
-          for (int a = 0; a < 4; ++a) tb = __fmaf_ru(fabsf(v[a][q]), fabsf(xv[a].x), tb);
-          bias_reserve(acc[q], tb);
-#pragma unroll
-          for (int a = 0; a < 4; ++a) bias_step(acc[q], v[a][q], xv[a].x, xv[a].y);
-          bias_renorm(acc[q]);
+          if (COL) bias_step(acc[a], v[q][a], xh[q], xl[q]);
+          else bias_step(acc[a], v[a][q], xh[q], xl[q]);
         }
-      }
-      const bool colc = symi && k < B;
-      if (colc) {
-        // column contributions of the explicit inverse: c_q = sum_a v[a][q] xb_a
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          BiasAcc c;
-          bias_init(c);
-          float tb = 0.f;
-#pragma unroll
-          for (int a = 0; a < 4; ++a) tb = __fmaf_ru(fabsf(v[a][q]), fabsf(xb[a].x), tb);
-          bias_reserve(c, tb);
-#pragma unroll
-          for (int a = 0; a < 4; ++a) bias_step(c, v[a][q], xb[a].x, xb[a].y);
-          float h, l;
-          bias_value(c, h, l);
-          ff_add(h, l, __shfl_xor_sync(0xffffffffu, h, 16), __shfl_xor_sync(0xffffffffu, l, 16));
-          if (lane < 16) colpart[wid][4 * cq + q] = make_float2(h, l);
-        }
-      }
-      __syncthreads();  // every thread is done with this slot (and colpart is complete)
-      if (tid == 0) {
-        fence_proxy_async();
-        issue(slot);
-      }
-      if (colc && tid < TILE) {
-        float2 s0 = colpart[0][tid];
-#pragma unroll
-        for (int w2 = 1; w2 < NT / 32; ++w2) ff_add(s0.x, s0.y, colpart[w2][tid].x, colpart[w2][tid].y);
-        slot_base[(int64_t)k * TILE + tid] = s0;
+        bias_renorm(acc[a]);
       }
     }
     if (!ok) break;
-    if (!COL && symi) __syncthreads();  // colpart reads of the last tile are done
     if (!COL) {
 #pragma unroll
       for (int a = 0; a < 4; ++a) {
@@ -452,32 +544,44 @@ __global__ void __launch_bounds__(NT) k_tile_pass_cf(const TS* __restrict__ tile
           ff_add(h, l, __shfl_xor_sync(0xffffffffu, h, o), __shfl_xor_sync(0xffffffffu, l, o));
         if (cq == 0) {
           const int row = B * TILE + rg + 16 * a;
-          if (SPD) tout[pad_off[i] + row] = make_float2(h, l);
-          else if (row < n_arr[i]) ypos[sub_off[i] + row] = ff_to_double(h, l) * unscale[i];
+          if (SPD) {
+            tout[d.pad + row] = h;
+            tout[plane + d.pad + row] = l;
+          } else if (row < d.n) {
+            ypos[d.sub_off + row] = ff_to_double(h, l) * unscale[d.i];
+          }
         }
       }
     } else {
+      // column pass: the 16 row groups merged through shared memory (the
+      // buffer not used by a pending partial sum)
+      float2 (*cp)[TILE] = colpart[nc & 1];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         float h, l;
         bias_value(acc[q], h, l);
         ff_add(h, l, __shfl_xor_sync(0xffffffffu, h, 16), __shfl_xor_sync(0xffffffffu, l, 16));
-        if (lane < 16) colpart[wid][4 * cq + q] = make_float2(h, l);
+        if (lane < 16) cp[wid][4 * cq + q] = make_float2(h, l);
       }
       __syncthreads();
       if (tid < TILE) {
-        float2 s0 = colpart[0][tid];
+        float2 s0 = cp[0][tid];
 #pragma unroll
-        for (int w2 = 1; w2 < NT / 32; ++w2) ff_add(s0.x, s0.y, colpart[w2][tid].x, colpart[w2][tid].y);
+        for (int w2 = 1; w2 < NT / 32; ++w2) ff_add(s0.x, s0.y, cp[w2][tid].x, cp[w2][tid].y);
         const int col = B * TILE + tid;
-        if (col < n_arr[i]) ypos[sub_off[i] + col] = ff_to_double(s0.x, s0.y) * unscale[i];
+        if (col < d.n) ypos[d.sub_off + col] = ff_to_double(s0.x, s0.y) * unscale[d.i];
       }
       __syncthreads();
     }
   }
-  if (!ok && tid == 0) {
+  if (ok) {
+    // the last tile's column partials
+    __syncthreads();
+    after_barrier();
+  } else if (tid == 0) {
     atomicOr(err, (int32_t)DERR_TIMEOUT);
-    for (uint32_t u = t; u < issued; ++u) mbar_wait_bounded(&full[u % S], (u / S) & 1);
+    // copies still in flight land before the block's shared memory goes away
+    for (uint32_t u = t; u < prod.issued; ++u) mbar_wait_bounded(&full[u % S], (u / S) & 1);
   }
 }
 
@@ -489,7 +593,7 @@ __global__ void __launch_bounds__(NT) k_sym_reduce_cf(const int2* __restrict__ i
                                                       const int32_t* __restrict__ n_arr,
                                                       const int32_t* __restrict__ nt_arr,
                                                       const int64_t* __restrict__ pad_off,
-                                                      const float2* __restrict__ rowpart,
+                                                      const float* __restrict__ rowpart, int64_t plane,
                                                       const float2* __restrict__ slots,
                                                       const double* __restrict__ unscale, double* __restrict__ ypos,
                                                       const int32_t* __restrict__ done) {
@@ -501,7 +605,7 @@ __global__ void __launch_bounds__(NT) k_sym_reduce_cf(const int2* __restrict__ i
     const int i = w.x, J = w.y, nt = nt_arr[i];
     const int row = J * TILE + c;
     if (row >= n_arr[i]) continue;
-    float2 y = rowpart[pad_off[i] + row];
+    float2 y = make_float2(rowpart[pad_off[i] + row], rowpart[plane + pad_off[i] + row]);
     const int64_t t0 = tile_off[i];
     for (int I = J + 1; I < nt; ++I) {
       const float2 sl = slots[(t0 + (int64_t)I * (I + 1) / 2 + J) * TILE + c];
@@ -699,14 +803,16 @@ __global__ void __launch_bounds__(NT) k_apply_pull(int n, int ras, const double*
 
 // x for the single-precision local part: per subdomain the scale 2^-e with
 // max |r s| = f 2^e, f in [1/2, 1) (exact), the scaled entries split into
-// float-float pairs (zero beyond n_i), and unscale[i] = 2^e.
+// float-float pairs (zero beyond n_i) stored as a hi plane and, `plane`
+// entries further, a lo plane; unscale[i] = 2^e.
 __global__ void __launch_bounds__(NT) k_gather_x_cf(const int32_t* __restrict__ omega,
                                                     const int32_t* __restrict__ sub_off,
                                                     const int32_t* __restrict__ n_arr,
                                                     const int32_t* __restrict__ nt_arr,
                                                     const int64_t* __restrict__ pad_off, const double* __restrict__ r,
-                                                    const double* __restrict__ ds, float2* __restrict__ xs,
-                                                    double* __restrict__ unscale, const int32_t* __restrict__ done) {
+                                                    const double* __restrict__ ds, float* __restrict__ xs,
+                                                    int64_t plane, double* __restrict__ unscale,
+                                                    const int32_t* __restrict__ done) {
   COUNT_LAUNCH();
   if (done != nullptr && *done) return;
   __shared__ double red[NT / 32];
@@ -728,14 +834,15 @@ __global__ void __launch_bounds__(NT) k_gather_x_cf(const int32_t* __restrict__ 
   if (mx > 0 && isfinite(mx)) frexp(mx, &e);
   const double sc = ldexp(1.0, -e);
   if (threadIdx.x == 0) unscale[i] = ldexp(1.0, e);
-  float2* out = xs + pad_off[i];
+  float* out = xs + pad_off[i];
   for (int a = threadIdx.x; a < np; a += NT) {
     float2 v = make_float2(0.f, 0.f);
     if (a < n) {
       const int g = omega[b0 + a];
       v = split_ff(r[g] * ds[g] * sc);
     }
-    out[a] = v;
+    out[a] = v.x;
+    out[plane + a] = v.y;
   }
 }
 
@@ -754,21 +861,21 @@ void gather_x(Handle& h, const double* r, cudaStream_t s, const int32_t* done) {
   Dense& dn = h.dn;
   if constexpr (sizeof(T) == 4)
     k_gather_x_cf<<<h.N, NT, 0, s>>>(h.ov.omega, h.ov.sub_off, h.dev_n, dn.nt, dn.pad_off, r, h.dscale,
-                                     (float2*)dn.xpad, dn.xunscale, done);
+                                     (float*)dn.xpad, dn.n_pad, dn.xunscale, done);
   else
     k_gather_x<double><<<h.N, NT, 0, s>>>(h.ov.omega, h.ov.sub_off, h.dev_n, dn.nt, dn.pad_off, r, h.dscale,
                                           (double*)dn.xpad, done);
 }
 
 template <typename T, bool SPD, bool COL, typename TS = T>
-void launch_pass(Handle& h, int nitems, const int2* items, const void* vin, void* tout, cudaStream_t s,
-                 const int32_t* done) {
+void launch_pass(Handle& h, int nitems, const int2* items, const TileItem* desc, const void* vin, void* tout,
+                 cudaStream_t s, const int32_t* done) {
   Dense& dn = h.dn;
   const unsigned g = tile_grid(h, nitems);
   if constexpr (sizeof(T) == 4)
-    k_tile_pass_cf<TS, SPD, COL><<<g, NT, Stages<TS>::SMEM, s>>>(
-        (const TS*)dn.tiles, dn.tile_off, items, nitems, h.ov.sub_off, h.dev_n, dn.nt, dn.pad_off,
-        (const float2*)vin, (float2*)tout, dn.ypos, dn.xunscale, dn.sym, (float2*)dn.slots, dn.err, done);
+    k_tile_pass_cf<TS, SPD, COL><<<g, NT, Stages<TS>::SMEM, s>>>((const TS*)dn.tiles, desc, nitems, (const float*)vin,
+                                                                 (float*)tout, dn.n_pad, dn.ypos, dn.xunscale,
+                                                                 (float2*)dn.slots, dn.sym_bias, dn.err, done);
   else
     k_tile_pass<double, double, SPD, COL><<<g, NT, Stages<double>::SMEM, s>>>(
         (const double*)dn.tiles, dn.tile_off, items, nitems, h.ov.sub_off, h.dev_n, dn.nt, dn.pad_off,
@@ -781,13 +888,15 @@ void row_pass(Handle& h, cudaStream_t s, const int32_t* done) {
   if constexpr (sizeof(T) == 4) {
     if (dn.n_row_items_h > 0) {
       // explicit inverses stored in FP16, then the rest (FP32 tiles)
-      launch_pass<T, true, false, __half>(h, dn.n_row_items_h, dn.row_items_h, dn.xpad, dn.tpad, s, done);
-      if (dn.n_row_items_f > 0) launch_pass<T, true, false>(h, dn.n_row_items_f, dn.row_items_f, dn.xpad, dn.tpad, s, done);
+      launch_pass<T, true, false, __half>(h, dn.n_row_items_h, dn.row_items_h, dn.row_desc_h, dn.xpad, dn.tpad, s,
+                                          done);
+      if (dn.n_row_items_f > 0)
+        launch_pass<T, true, false>(h, dn.n_row_items_f, dn.row_items_f, dn.row_desc_f, dn.xpad, dn.tpad, s, done);
       return;
     }
   }
-  if (h.opt.spd) launch_pass<T, true, false>(h, dn.n_row_items, dn.row_items, dn.xpad, dn.tpad, s, done);
-  else launch_pass<T, false, false>(h, dn.n_row_items, dn.row_items, dn.xpad, dn.tpad, s, done);
+  if (h.opt.spd) launch_pass<T, true, false>(h, dn.n_row_items, dn.row_items, dn.row_desc, dn.xpad, dn.tpad, s, done);
+  else launch_pass<T, false, false>(h, dn.n_row_items, dn.row_items, dn.row_desc, dn.xpad, dn.tpad, s, done);
 }
 
 // second stage of the SPD local part: y = W^T t for the two-pass subdomains,
@@ -795,13 +904,14 @@ void row_pass(Handle& h, cudaStream_t s, const int32_t* done) {
 template <typename T>
 void col_pass(Handle& h, cudaStream_t s, const int32_t* done) {
   Dense& dn = h.dn;
-  if (dn.n_col_items > 0) launch_pass<T, true, true>(h, dn.n_col_items, dn.col_items, dn.tpad, nullptr, s, done);
+  if (dn.n_col_items > 0)
+    launch_pass<T, true, true>(h, dn.n_col_items, dn.col_items, dn.col_desc, dn.tpad, nullptr, s, done);
   if (dn.n_sym_items > 0) {
     const unsigned g = (unsigned)std::min<int64_t>(ceil_div((int64_t)dn.n_sym_items * TILE, NT), (int64_t)h.num_sms * 16);
     if constexpr (sizeof(T) == 4)
       k_sym_reduce_cf<<<g, NT, 0, s>>>(dn.sym_items, dn.n_sym_items, dn.tile_off, h.ov.sub_off, h.dev_n, dn.nt,
-                                       dn.pad_off, (const float2*)dn.tpad, (const float2*)dn.slots, dn.xunscale,
-                                       dn.ypos, done);
+                                       dn.pad_off, (const float*)dn.tpad, dn.n_pad, (const float2*)dn.slots,
+                                       dn.xunscale, dn.ypos, done);
     else
       k_sym_reduce<double><<<g, NT, 0, s>>>(dn.sym_items, dn.n_sym_items, dn.tile_off, h.ov.sub_off, h.dev_n, dn.nt,
                                             dn.pad_off, (const double*)dn.tpad, (const double*)dn.slots, dn.ypos,

@@ -108,6 +108,23 @@ __device__ __forceinline__ void dot2_step(float& hi, float& lo, float v, float x
   lo = __fmaf_rn(v, xl, lo);
 }
 
+// the biased step and renormalisation on a bare (hi, lo) pair whose bias is
+// kept by the caller
+__device__ __forceinline__ void bias_step1(float& hi, float& lo, float v, float xh, float xl) {
+  const float s = __fmaf_rn(v, xh, hi);
+  const float d = __fsub_rn(hi, s);   // exact
+  const float r = __fmaf_rn(v, xh, d);
+  hi = s;
+  lo = __fadd_rn(lo, r);
+  lo = __fmaf_rn(v, xl, lo);
+}
+__device__ __forceinline__ void bias_renorm1(float& hi, float& lo) {
+  float s, e;
+  fast_two_sum(hi, lo, s, e);
+  hi = s;
+  lo = e;
+}
+
 // split a double into hi + lo (exact up to 2^-48 relative)
 __device__ __forceinline__ float2 split_ff(double x) {
   const float h = (float)x;

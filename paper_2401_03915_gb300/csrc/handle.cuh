@@ -31,6 +31,18 @@ struct Overlap {
   int32_t max_n = 0;
 };
 
+// One work item of the single-precision tile passes, precomputed on the host
+// so that a block reads it in one independent load: subdomain, row (or
+// column) block, tile count, explicit-inverse flag; the padded-vector offset,
+// the first tile (column pass: the subdomain's first tile), the row-block
+// bounds and slots of the explicit inverses; |Omega_i|, its first position,
+// the tiles per side.
+struct __align__(16) TileItem {
+  int32_t i, B, cnt, symi;
+  int64_t pad, tile0, bias0, slot0;
+  int32_t n, sub_off, nt, unused;
+};
+
 struct Dense {
   // per subdomain (host and device copies)
   std::vector<int32_t> h_np;          // padded size round_up(n_i, TILE)
@@ -57,6 +69,9 @@ struct Dense {
                                       // pairs scaled per subdomain by a power of two in single precision)
   void* tpad = nullptr;               // apply: t = W x (SPD first pass) or the explicit inverses' row part
   double* xunscale = nullptr;         // single precision: per subdomain, the inverse of the scale of xpad
+  int64_t* boff = nullptr;            // single precision: first row block of subdomain i in sym_bias
+  float* sym_bias = nullptr;          // single precision, explicit inverses: per row block the power of two
+                                      // that biases the tile pass's accumulators (bounds all its partial sums)
   int2* row_items = nullptr;          // (subdomain, row block), most tiles first
   int2* col_items = nullptr;          // (subdomain, column block) of two-pass subdomains, most tiles first
   int2* sym_items = nullptr;          // (subdomain, block) of explicit-inverse subdomains
@@ -70,6 +85,8 @@ struct Dense {
   std::vector<int8_t> h_s16;
   int2 *row_items_h = nullptr, *row_items_f = nullptr;
   int n_row_items_h = 0, n_row_items_f = 0;
+  // single precision: the descriptors of row_items, row_items_h, row_items_f, col_items
+  TileItem *row_desc = nullptr, *row_desc_h = nullptr, *row_desc_f = nullptr, *col_desc = nullptr;
   void* slots = nullptr;              // explicit-inverse column contributions, TILE per stored tile
                                       // (FP64, or float-float pairs in single precision)
   double* ypos = nullptr;             // per omega position: local solution before the pull

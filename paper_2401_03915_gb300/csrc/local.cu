@@ -653,6 +653,23 @@ __global__ void k_decide_s16(int N, const int8_t* __restrict__ sym, const int32_
   s16[i] = ok;
 }
 
+// Biases of the float-float tile pass (explicit-inverse subdomains): with
+// the apply's input scaled to max |x| < 1, every partial sum over a row, or
+// over a column segment of a tile, of row block I is at most rmax[I]; the
+// bias is the power of two at or above 4 (1.001 rmax + n_i 2^-24), the
+// factors covering the FP32 summation of rmax and FP16 rounding of the tiles.
+__global__ void k_sym_bias(int64_t nitems, const int2* __restrict__ items, const int64_t* __restrict__ boff,
+                           const int32_t* __restrict__ n_arr, const float* __restrict__ rmax,
+                           float* __restrict__ bias) {
+  COUNT_LAUNCH();
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nitems; k += (int64_t)gridDim.x * blockDim.x) {
+    const int2 w = items[k];
+    const int64_t b = boff[w.x] + w.y;
+    const float m = 4.f * (1.001f * rmax[b] + (float)n_arr[w.x] * 0x1.0p-24f);
+    bias[b] = __uint_as_float((__float_as_uint(m) + 0x7fffffu) & 0x7f800000u);
+  }
+}
+
 // in place: the FP32 tile becomes FP16 in the first half of its slot
 __global__ void __launch_bounds__(NT) k_tiles_to_half(float* __restrict__ tiles, const int4* __restrict__ desc,
                                                       int64_t ntiles, const int8_t* __restrict__ s16) {
@@ -840,40 +857,82 @@ void run_local(Handle& h, cudaStream_t s) {
   if (!si.empty()) CK(cudaMemcpyAsync(dn.sym_items, si.data(), sizeof(int2) * si.size(), cudaMemcpyHostToDevice, s));
   if (spd && !si.empty()) dn.slots = mem.alloc<T>(tl * TILE * (sizeof(T) == 4 ? 2 : 1));
   if constexpr (sizeof(T) == 4) {
-    if (h.s16 && spd && !si.empty()) {
-      // which explicit inverses go to FP16, then convert their tiles in place
+    if (spd && !si.empty()) {
+      // row-block bounds of the explicit inverses: the tile pass's biases and
+      // the FP16-storage decision
       std::vector<int64_t> bo(N);
       int64_t nb = 0;
       for (int i = 0; i < N; ++i) { bo[i] = nb; nb += dn.h_nt[i]; }
-      int64_t* boff = mem.alloc<int64_t>(N);
+      dn.boff = mem.alloc<int64_t>(N);
       float* rmax = mem.alloc<float>(std::max<int64_t>(nb, 1));
-      double* amax = mem.alloc<double>(N);
-      dn.s16 = mem.alloc<int8_t>(N);
-      CK(cudaMemcpyAsync(boff, bo.data(), 8 * N, cudaMemcpyHostToDevice, s));
+      dn.sym_bias = mem.alloc<float>(std::max<int64_t>(nb, 1));
+      CK(cudaMemcpyAsync(dn.boff, bo.data(), 8 * N, cudaMemcpyHostToDevice, s));
       const unsigned gs = (unsigned)std::min<int64_t>((int64_t)si.size(), 152 * 8);
-      k_s_rowsum<<<gs, NT, 0, s>>>((const float*)dn.tiles, dn.tile_off, dn.nt, dn.sym_items, (int)si.size(), boff,
+      k_s_rowsum<<<gs, NT, 0, s>>>((const float*)dn.tiles, dn.tile_off, dn.nt, dn.sym_items, (int)si.size(), dn.boff,
                                    rmax);
-      k_a_rowsum<<<N, NT, 0, s>>>(ov.sub_off, d_n, ov.omega, ov.ent_off, ov.lcol, h.row_ptr, h.col_idx, h.val,
-                                  h.dscale, dn.sym, amax);
-      k_decide_s16<<<(unsigned)ceil_div(N, NT), NT, 0, s>>>(N, dn.sym, dn.nt, d_n, boff, rmax, amax, dn.s16);
-      k_tiles_to_half<<<gp, NT, 0, s>>>((float*)dn.tiles, dn.tile_desc, tl, dn.s16);
-      CK_LAUNCH("FP16 storage of the explicit inverses");
-      dn.h_s16.assign(N, 0);
-      CK(cudaMemcpyAsync(dn.h_s16.data(), dn.s16, N, cudaMemcpyDeviceToHost, s));
-      CK(cudaStreamSynchronize(s));
-      std::vector<int2> rh, rf;
-      for (const int2& e : rv) (dn.h_s16[e.x] ? rh : rf).push_back(e);
-      dn.n_row_items_h = (int)rh.size();
-      dn.n_row_items_f = (int)rf.size();
-      if (!rh.empty()) {
-        dn.row_items_h = mem.alloc<int2>(rh.size());
-        dn.row_items_f = mem.alloc<int2>(std::max<size_t>(rf.size(), 1));
-        CK(cudaMemcpyAsync(dn.row_items_h, rh.data(), sizeof(int2) * rh.size(), cudaMemcpyHostToDevice, s));
-        if (!rf.empty())
-          CK(cudaMemcpyAsync(dn.row_items_f, rf.data(), sizeof(int2) * rf.size(), cudaMemcpyHostToDevice, s));
+      k_sym_bias<<<(unsigned)std::min<int64_t>(ceil_div((int64_t)si.size(), NT), 152 * 4), NT, 0, s>>>(
+          (int64_t)si.size(), dn.sym_items, dn.boff, d_n, rmax, dn.sym_bias);
+      CK_LAUNCH("row-block bounds of the explicit inverses");
+      if (h.s16) {
+        const int64_t* boff = dn.boff;
+        double* amax = mem.alloc<double>(N);
+        dn.s16 = mem.alloc<int8_t>(N);
+        k_a_rowsum<<<N, NT, 0, s>>>(ov.sub_off, d_n, ov.omega, ov.ent_off, ov.lcol, h.row_ptr, h.col_idx, h.val,
+                                    h.dscale, dn.sym, amax);
+        k_decide_s16<<<(unsigned)ceil_div(N, NT), NT, 0, s>>>(N, dn.sym, dn.nt, d_n, boff, rmax, amax, dn.s16);
+        k_tiles_to_half<<<gp, NT, 0, s>>>((float*)dn.tiles, dn.tile_desc, tl, dn.s16);
+        CK_LAUNCH("FP16 storage of the explicit inverses");
+        dn.h_s16.assign(N, 0);
+        CK(cudaMemcpyAsync(dn.h_s16.data(), dn.s16, N, cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
+        std::vector<int2> rh, rf;
+        for (const int2& e : rv) (dn.h_s16[e.x] ? rh : rf).push_back(e);
+        dn.n_row_items_h = (int)rh.size();
+        dn.n_row_items_f = (int)rf.size();
+        if (!rh.empty()) {
+          dn.row_items_h = mem.alloc<int2>(rh.size());
+          dn.row_items_f = mem.alloc<int2>(std::max<size_t>(rf.size(), 1));
+          CK(cudaMemcpyAsync(dn.row_items_h, rh.data(), sizeof(int2) * rh.size(), cudaMemcpyHostToDevice, s));
+          if (!rf.empty())
+            CK(cudaMemcpyAsync(dn.row_items_f, rf.data(), sizeof(int2) * rf.size(), cudaMemcpyHostToDevice, s));
+          CK(cudaStreamSynchronize(s));
+        }
       }
     }
+    // descriptors of the single-precision tile passes' work items
+    std::vector<int64_t> bo(N);
+    for (int i = 0, nb = 0; i < N; ++i) { bo[i] = nb; nb += dn.h_nt[i]; }
+    auto make_desc = [&](const int2* dev_items, int count, bool col) -> TileItem* {
+      if (count <= 0) return nullptr;
+      std::vector<int2> it(count);
+      CK(cudaMemcpyAsync(it.data(), dev_items, sizeof(int2) * count, cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      std::vector<TileItem> d(count);
+      for (int k = 0; k < count; ++k) {
+        const int i = it[k].x, B = it[k].y, nt = dn.h_nt[i];
+        TileItem& e = d[k];
+        e.i = i;
+        e.B = B;
+        e.cnt = col ? nt - B : (spd ? B + 1 : nt);
+        e.symi = (!col && spd && dn.h_sym[i]) ? 1 : 0;
+        e.pad = h_pad_off[i];
+        e.tile0 = dn.h_tile_off[i] + (col ? 0 : (spd ? (int64_t)B * (B + 1) / 2 : (int64_t)B * nt));
+        e.bias0 = e.symi ? bo[i] : 0;
+        e.slot0 = dn.h_tile_off[i] + (int64_t)B * (B + 1) / 2;
+        e.n = h.h_n[i];
+        e.sub_off = ov.h_sub_off[i];
+        e.nt = nt;
+        e.unused = 0;
+      }
+      TileItem* out = mem.alloc<TileItem>(count);
+      CK(cudaMemcpyAsync(out, d.data(), sizeof(TileItem) * count, cudaMemcpyHostToDevice, s));
+      CK(cudaStreamSynchronize(s));
+      return out;
+    };
+    dn.row_desc = make_desc(dn.row_items, dn.n_row_items, false);
+    dn.col_desc = make_desc(dn.col_items, dn.n_col_items, true);
+    dn.row_desc_h = make_desc(dn.row_items_h, dn.n_row_items_h, false);
+    dn.row_desc_f = make_desc(dn.row_items_f, dn.n_row_items_f, false);
   }
 }
 
