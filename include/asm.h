@@ -112,9 +112,12 @@ typedef struct {
   int32_t method;           /* 0: PCG for SPD A with the symmetric apply
                                (one_level 0, coarse_mode 0), else FGMRES;
                                1: PCG; 2: FGMRES                               */
-  int32_t restart;          /* FGMRES restart length, at most 512; 0 (default):
-                               512 for the restricted or deflated apply (GMRES
-                               without restart, Section 6), 30 otherwise      */
+  int32_t restart;          /* FGMRES restart length, at most 512 and at most
+                               max_it; 0 (default): 512 for the restricted or
+                               deflated apply (GMRES without restart, Section
+                               6), 30 otherwise, shortened (not below 30) when
+                               the 2m + 1 basis vectors would not fit in 3/4
+                               of the free device memory                      */
   double rtol;              /* stop at ||b - A x||_2 / ||b||_2 <= rtol         */
   int32_t max_it;           /* iteration cap                                   */
   int32_t use_x0;           /* 1: x holds the initial guess; 0: x0 = 0         */
@@ -304,7 +307,8 @@ asm_status asm_get_warm_data(const asm_handle* h, int64_t* row_offsets, float* X
  * unacceptable; applications whose device memory is owned by their own
  * allocator.  This entry point allocates nothing and needs no handle.
  *   n, row_ptr (n+1), col_idx, val: A in CSR, device pointers (as asm_csr).
- *   x (n, device): input.  y (n, device): output A x.  xty (device, one
+ *   x (n, device): input.  y (n, device): output A x; y must not overlap x
+ *   (both are accessed as non-aliased).  xty (device, one
  *   double): output x^T y, summed in a fixed order (deterministic).
  * Scratch: one partial sum per 64 rows in a static device array built into
  * the library (16384 doubles), so n is limited to 1,048,576 rows; larger n is

@@ -261,8 +261,17 @@ def asm_time_apply(h: int, r, z, iters: int = 10, stream=None) -> dict:
 
 
 def asm_spmv_dot_noalloc(row_ptr, col_idx, val, x, y, xty, stream=None) -> None:
-    """y = A x and xty[0] = x^T y without any device allocation (device tensors)."""
-    n = int(x.numel()) if hasattr(x, "numel") else len(x)
+    """y = A x and xty[0] = x^T y without any device allocation (contiguous CUDA
+    tensors: int32 row_ptr (n + 1) and col_idx, float64 val, x, y, xty; y must
+    not overlap x)."""
+    import torch
+    n = int(x.numel())
+    for name, t, dt in (("row_ptr", row_ptr, torch.int32), ("col_idx", col_idx, torch.int32), ("val", val, torch.float64),
+                        ("x", x, torch.float64), ("y", y, torch.float64), ("xty", xty, torch.float64)):
+        if not isinstance(t, torch.Tensor) or t.dtype != dt or not t.is_cuda or not t.is_contiguous():
+            raise TypeError(f"{name} must be a contiguous CUDA tensor of {dt}")
+    if row_ptr.numel() != n + 1 or y.numel() != n or xty.numel() < 1 or col_idx.numel() != val.numel():
+        raise ValueError("sizes: row_ptr n + 1, y n, xty >= 1, col_idx and val alike")
     _check(load().asm_spmv_dot_noalloc(n, _ptr(row_ptr), _ptr(col_idx), _ptr(val), _ptr(x), _ptr(y), _ptr(xty),
                                        _stream(stream)))
 

@@ -280,7 +280,8 @@ asm_status asm_solve(asm_handle* H, const double* b, double* x, const asm_solve_
   Handle& h = H->h;
   // automatic restart length: GMRES without restart (up to 512 vectors) for
   // the restricted or deflated apply, as the Section 6 experiments; 30 otherwise
-  if (so.restart <= 0)
+  const bool auto_restart = so.restart <= 0;
+  if (auto_restart)
     so.restart = (h.opt.one_level == 1 || (h.opt.coarse_mode == 1 && h.co.n_C > 0)) ? 512 : 30;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   bool conv = false;
@@ -299,7 +300,7 @@ asm_status asm_solve(asm_handle* H, const double* b, double* x, const asm_solve_
     const bool symmetric = h.opt.spd && h.opt.one_level == 0 && (h.opt.coarse_mode == 0 || h.co.n_C == 0);
     int method = so.method ? so.method : (symmetric ? 1 : 2);
     if (method == 1) solve_pcg(h, db, dx, so, *info, s);
-    else solve_fgmres(h, db, dx, so, *info, s);
+    else solve_fgmres(h, db, dx, so, *info, s, auto_restart);
     check_device_error(h, s, "solve");
     if (h.host_io) {
       CK(cudaMemcpyAsync(x, dx, sizeof(double) * h.n, cudaMemcpyDeviceToHost, s));

@@ -59,6 +59,16 @@ struct DevMem {
     ptrs.push_back(p);
     return static_cast<T*>(p);
   }
+  // free one allocation made by alloc (nothing for null)
+  void free(void* p) {
+    if (p == nullptr) return;
+    for (size_t k = 0; k < ptrs.size(); ++k)
+      if (ptrs[k] == p) {
+        cudaFreeAsync(p, stream);
+        ptrs.erase(ptrs.begin() + k);
+        return;
+      }
+  }
   void release() {
     for (void* p : ptrs) cudaFreeAsync(p, stream);
     ptrs.clear();

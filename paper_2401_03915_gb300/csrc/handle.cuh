@@ -129,7 +129,7 @@ struct Krylov {
   double* mpart = nullptr;  // multi-dot partial sums
   double* gpart = nullptr;  // PCG: partials of the fused reductions (3 x RBLK)
   unsigned* ticket = nullptr;  // PCG: tickets of the fused reductions (3)
-  int32_t restart = 0;
+  int32_t restart = 0;      // FGMRES basis capacity (restart length) allocated
   double* bx = nullptr;     // device copies of b, x for host-pointer solves
   double* hpin = nullptr;   // pinned host staging
 };
@@ -192,8 +192,10 @@ void coarse_solve(Handle& h, const double* c, double* y, cudaStream_t s,
                   const int32_t* done = nullptr);                                 // coarse.cu
 void solve_pcg(Handle& h, const double* b, double* x, const asm_solve_opts& o, asm_solve_info& info,
                cudaStream_t s);
+// auto_restart: the caller left the restart length to the library (it may be
+// shortened to fit the basis in device memory)
 void solve_fgmres(Handle& h, const double* b, double* x, const asm_solve_opts& o,
-                  asm_solve_info& info, cudaStream_t s);
+                  asm_solve_info& info, cudaStream_t s, bool auto_restart);
 
 // coarse_nd.cu: nested-dissection multifrontal factorisation of E
 void nd_setup(Handle& h, const std::vector<std::vector<int>>& adj, cudaStream_t s);

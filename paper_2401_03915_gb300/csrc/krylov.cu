@@ -437,20 +437,33 @@ __global__ void k_backsolve(const double* H, int ldh, int khost, const int32_t* 
 }  // namespace
 
 void solve_fgmres(Handle& h, const double* b, double* x, const asm_solve_opts& o, asm_solve_info& info,
-                  cudaStream_t s) {
+                  cudaStream_t s, bool auto_restart) {
   ensure_krylov(h, s);
   Krylov& kr = h.kr;
   const int n = h.n;
-  const int m = std::max(1, std::min(o.restart, MAXV - 1));
-  const int ldh = m + 1;
+  // basis length: the restart length, at most max_it and 512; the automatic
+  // length also fits the basis (2m + 1 vectors) in 3/4 of the free memory
+  int m = std::max(1, std::min(std::min(o.restart, MAXV - 1), o.max_it));
+  if (auto_restart && m > kr.restart) {
+    size_t fr = 0, tot = 0;
+    CK(cudaMemGetInfo(&fr, &tot));
+    const double per = 2.0 * 8.0 * (double)n;
+    const int fit = (int)std::min<double>(m, std::floor((0.75 * (double)fr - 8.0 * n) / per));
+    m = std::max(std::min(m, 30), fit);
+  }
   DevMem& mem = h.mem;
-  if (!kr.V || kr.restart != m) {
+  if (!kr.V || m > kr.restart) {
+    // grow the basis; a shorter restart later reuses it
+    mem.free(kr.V);
+    mem.free(kr.ZB);
+    mem.free(kr.H);
     kr.V = mem.alloc<double>((int64_t)(m + 1) * n);
     kr.ZB = mem.alloc<double>((int64_t)m * n);
-    kr.H = mem.alloc<double>((int64_t)ldh * m + 4 * ldh + 16);
-    kr.mpart = mem.alloc<double>((int64_t)MD_MAXB * MAXV);
+    kr.H = mem.alloc<double>((int64_t)(m + 1) * m + 4 * (m + 1) + 16);
+    if (!kr.mpart) kr.mpart = mem.alloc<double>((int64_t)MD_MAXB * MAXV);
     kr.restart = m;
   }
+  const int ldh = m + 1;
   double* H = kr.H;
   double* cs = H + (int64_t)ldh * m;
   double* sn = cs + ldh;
