@@ -79,9 +79,19 @@ typedef struct {
   int32_t oversample;       /* extra block columns of the subspace iteration   */
   int32_t max_sweeps;       /* cap on subspace-iteration sweeps                 */
   double eig_tol;           /* relative eigen-residual tolerance                */
-  double nu;                /* > 1: also add eigenvectors of eq. uppergevp with
-                               lambda > nu; <= 0: off (as in Section 6)         */
-  int32_t nev_lift;         /* at most this many eq. uppergevp vectors          */
+  double nu;                /* >= 1 (SPD only): also add to each Z_i the
+                               eigenvectors u of eq. uppergevp (Section 3.3,
+                               D_i A_ii D_i u = lambda A_ii u, Boolean D_i)
+                               with lambda > nu, A_ii-normalised, restricted
+                               to I_i (eq. Z_i / coarse_space_2), after the
+                               eq. gevpsvd columns; 0: off, as in Section 6.
+                               Its eigenvalues are >= 1; 0 < nu < 1 is
+                               rejected.  With overlap 1 the two problems
+                               share one operator (lambda = 1 + the gevpsvd
+                               value), so only lifting vectors beyond the
+                               kept gevpsvd ones are added                    */
+  int32_t nev_lift;         /* at most this many eq. uppergevp vectors per
+                               subdomain (0: nev); nev + nev_lift <= 128      */
   int32_t coarse;           /* 1: two-level; 0: one-level (eq. onelevelasm)     */
   uint64_t seed;            /* counter-based random start of the iteration     */
   int32_t warm_start;       /* 1 (SPD only): the first columns of the start
@@ -165,9 +175,12 @@ void asm_default_solve_opts(asm_solve_opts* o);
  * (n entries, values 0..N-1, Section 2.1), `overlap` = delta >= 1 layers grown
  * through the graph of A + A^T, and `nev` coarse vectors per subdomain.
  * Steps (each a device stage): overlap index sets (Section 2.1), dense A_ii
- * (Section 2.3), local inverse by a blocked Gauss-Jordan sweep whose midpoint
- * gives X = -B^{-1}C and S = G - C^T B^{-1} C (eq. HOp), block subspace
- * iteration for eq. gevpsvd (SPD) or for the left singular vectors of
+ * (Section 2.3, symmetrically scaled to unit diagonal), local factor -- SPD:
+ * Cholesky A_ii = L L^T and W = L^{-1}, whose block W[Gamma_delta, I_i] gives
+ * the reduced form of eq. gevpsvd and W[Omega_i \ I_i, I_i] that of
+ * eq. uppergevp; general: a blocked Gauss-Jordan sweep whose midpoint gives
+ * X = -B^{-1}C (eq. HOp) -- block subspace iteration for eq. gevpsvd (SPD,
+ * plus eq. uppergevp when nu is set) or for the left singular vectors of
  * D_i Pi_i (general), Z and E = Z^T A Z (Section 4.1), FP64 factor of E.
  * A's arrays are copied; the caller may free them after the call.
  * Errors: INVALID_ARG for malformed input (checked on the host), NOT_SPD /
@@ -218,6 +231,12 @@ asm_status asm_get_overlap(const asm_handle* h, int32_t* sub_offsets, int32_t* l
  * descending; unused slots 0): lambda^2 of eq. gevpsvd (SPD) or singular
  * values of D_i Pi_i (general); counts[i] = number kept.  Either may be NULL. */
 asm_status asm_get_local_values(const asm_handle* h, double* values, int32_t* counts);
+
+/* Retained eigenvalues of eq. uppergevp (Section 3.3; nu set), host outputs
+ * of N*nev_lift entries (row i = subdomain i, descending, lambda > nu; unused
+ * slots 0); counts[i] = number kept.  Either may be NULL; nothing is written
+ * to values when lifting is off and nev_lift is 0. */
+asm_status asm_get_lift_values(const asm_handle* h, double* values, int32_t* counts);
 
 /* Subspace-iteration diagnostics, host outputs: resid (N*nev) the relative
  * eigen-residual of each kept pair at exit (row i = subdomain i, 0 beyond the

@@ -88,6 +88,7 @@ def load(path: str | None = None) -> C.CDLL:
     L.asm_get_info.argtypes = [vp, C.POINTER(asm_setup_info)]
     L.asm_get_overlap.argtypes = [vp, vp, vp, vp]
     L.asm_get_local_values.argtypes = [vp, vp, vp]
+    L.asm_get_lift_values.argtypes = [vp, vp, vp]
     L.asm_get_eigen_stats.argtypes = [vp, vp, vp]
     L.asm_get_coarse_basis.argtypes = [vp, vp, vp]
     L.asm_get_coarse_matrix.argtypes = [vp, vp]
@@ -115,7 +116,7 @@ def load(path: str | None = None) -> C.CDLL:
     L.asm_stage_name.restype = C.c_char_p
     L.asm_stage_name.argtypes = [i32]
     for f in ("asm_setup", "asm_apply", "asm_spmv", "asm_solve", "asm_get_info", "asm_get_overlap",
-              "asm_get_local_values", "asm_get_eigen_stats", "asm_get_coarse_basis", "asm_get_coarse_matrix", "asm_mlp_create",
+              "asm_get_local_values", "asm_get_lift_values", "asm_get_eigen_stats", "asm_get_coarse_basis", "asm_get_coarse_matrix", "asm_mlp_create",
               "asm_mlp_get_params", "asm_mlp_set_params", "asm_mlp_forward", "asm_mlp_loss_grad",
               "asm_mlp_train_step", "asm_get_warm_data"):
         getattr(L, f).restype = C.c_int
@@ -214,6 +215,15 @@ def asm_get_local_values(h: int):
     cnt = np.zeros(inf.N, dtype=np.int32)
     _check(load().asm_get_local_values(h, vals.ctypes.data if inf.nev else None, cnt.ctypes.data))
     return vals[:, :inf.nev], cnt
+
+
+def asm_get_lift_values(h: int, nev_lift: int):
+    """Kept eigenvalues of eq. uppergevp per subdomain (N x nev_lift, descending) and counts."""
+    inf = asm_get_info(h)
+    vals = np.zeros((inf.N, max(nev_lift, 1)), dtype=np.float64)
+    cnt = np.zeros(inf.N, dtype=np.int32)
+    _check(load().asm_get_lift_values(h, vals.ctypes.data if nev_lift else None, cnt.ctypes.data))
+    return vals[:, :nev_lift], cnt
 
 
 def asm_get_eigen_stats(h: int):

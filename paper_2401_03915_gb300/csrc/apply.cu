@@ -957,10 +957,10 @@ const double* apply_coarse(Handle& h, const double* r, cudaStream_t s, const int
   double* y = co.cvec + round_up(co.n_C, 64);
   if (co.Zf)
     k_coarse_restrict_cf<<<h.N, NT, 0, s>>>(co.Zf, co.z_off, co.count, co.col_off, h.ov.sub_off, h.dev_p,
-                                            h.ov.omega, h.nev, r, c, done);
+                                            h.ov.omega, co.zld, r, c, done);
   else
     k_coarse_restrict<<<h.N, NT, 0, s>>>(co.Z, co.z_off, co.count, co.col_off, h.ov.sub_off, h.dev_p, h.ov.omega,
-                                         h.nev, r, c, done);
+                                         co.zld, r, c, done);
   coarse_solve(h, c, y, s, done);
   if (co.Zf)
     k_split_vector<<<(unsigned)std::min<int64_t>(ceil_div(co.n_C, NT), 152 * 4), NT, 0, s>>>(co.n_C, y, co.ycf,
@@ -980,11 +980,11 @@ void apply_pull(Handle& h, const double* yc, double* z, cudaStream_t s, const in
   unsigned gp = (unsigned)std::min<int64_t>(ceil_div(h.n, NT), 152 * 16);
   if (co.Zf)
     k_apply_pull<float><<<gp, NT, 0, s>>>(h.n, ras, qadd, h.ov.occ_ptr, h.ov.occ_pos, yp, h.part, h.ov.own_pos,
-                                          h.ov.sub_off, co.Zf, co.z_off, co.count, co.col_off, h.nev, yc, co.ycf,
+                                          h.ov.sub_off, co.Zf, co.z_off, co.count, co.col_off, co.zld, yc, co.ycf,
                                           h.dscale, z, done, dot ? *dot : ApplyDot());
   else
     k_apply_pull<double><<<gp, NT, 0, s>>>(h.n, ras, qadd, h.ov.occ_ptr, h.ov.occ_pos, yp, h.part, h.ov.own_pos,
-                                           h.ov.sub_off, co.Z, co.z_off, co.count, co.col_off, h.nev, yc, nullptr,
+                                           h.ov.sub_off, co.Z, co.z_off, co.count, co.col_off, co.zld, yc, nullptr,
                                            h.dscale, z, done, dot ? *dot : ApplyDot());
 }
 

@@ -150,6 +150,12 @@ asm_status asm_setup(const asm_csr* A, const int32_t* part, int32_t N, int32_t o
   if (o.one_level != 0 && o.one_level != 1) return set_error(ASM_ERR_INVALID_ARG, "one_level must be 0 or 1");
   if (!(o.tau >= 0) || !std::isfinite(o.tau)) return set_error(ASM_ERR_INVALID_ARG, "tau must be finite and >= 0");
   if (o.coarse_mode != 0 && o.coarse_mode != 1) return set_error(ASM_ERR_INVALID_ARG, "coarse_mode must be 0 or 1");
+  if (!(o.nu == 0 || o.nu >= 1) || !std::isfinite(o.nu))
+    return set_error(ASM_ERR_INVALID_ARG, "nu must be 0 (off) or >= 1 (eigenvalues of eq. uppergevp are >= 1)");
+  if (o.nu > 0 && !o.spd) return set_error(ASM_ERR_INVALID_ARG, "nu (eq. uppergevp) needs the SPD method");
+  if (o.nev_lift < 0 || o.nev_lift > 120) return set_error(ASM_ERR_INVALID_ARG, "nev_lift must be in 0..120");
+  if (o.nu > 0 && nev + (o.nev_lift > 0 ? o.nev_lift : nev) > 128)
+    return set_error(ASM_ERR_UNSUPPORTED, "nev + nev_lift exceeds 128");
   asm_handle* H = new (std::nothrow) asm_handle();
   if (!H) return set_error(ASM_ERR_OOM, "host allocation failed");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -160,6 +166,9 @@ asm_status asm_setup(const asm_csr* A, const int32_t* part, int32_t N, int32_t o
     h.host_io = A->on_device == 0;
     h.fp32 = o.local_precision != ASM_PREC_FP64;
     h.s16 = o.local_precision == ASM_PREC_FP32_H16 && o.spd;
+    h.lift = o.nu > 0 && o.spd && o.coarse;
+    h.nev_lift = h.lift ? (o.nev_lift > 0 ? o.nev_lift : nev) : 0;
+    if (h.lift && h.nev_lift == 0) h.lift = false;
     {
       int dev = 0, sms = 0;
       CK(cudaGetDevice(&dev));
@@ -346,8 +355,23 @@ asm_status asm_get_local_values(const asm_handle* H, double* values, int32_t* co
       else std::memset(values, 0, sizeof(double) * h.N * h.nev);
     }
     if (counts) {
-      for (int i = 0; i < h.N; ++i) counts[i] = i < (int)h.co.h_count.size() ? h.co.h_count[i] : 0;
+      for (int i = 0; i < h.N; ++i) counts[i] = i < (int)h.co.h_count_g.size() ? h.co.h_count_g[i] : 0;
     }
+  });
+}
+
+asm_status asm_get_lift_values(const asm_handle* H, double* values, int32_t* counts) {
+  if (!H) return set_error(ASM_ERR_INVALID_ARG, "null argument");
+  const Handle& h = H->h;
+  return guarded([&] {
+    const int nl = std::max(h.nev_lift, 1);
+    if (values) {
+      if (h.co.lift_values)
+        CK(cudaMemcpy(values, h.co.lift_values, sizeof(double) * h.N * h.nev_lift, cudaMemcpyDeviceToHost));
+      else std::memset(values, 0, sizeof(double) * h.N * nl);
+    }
+    if (counts)
+      for (int i = 0; i < h.N; ++i) counts[i] = i < (int)h.co.h_lift_count.size() ? h.co.h_lift_count[i] : 0;
   });
 }
 
@@ -380,7 +404,7 @@ asm_status asm_get_coarse_basis(const asm_handle* H, double* Z, int32_t* col_off
       for (int i = 0; i < h.N; ++i) {
         int k = h.co.h_count[i], p = h.h_p[i];
         for (int r = 0; r < p; ++r)
-          for (int j = 0; j < k; ++j) Z[o++] = buf[h.co.h_z_off[i] + (int64_t)r * h.nev + j];
+          for (int j = 0; j < k; ++j) Z[o++] = buf[h.co.h_z_off[i] + (int64_t)r * h.co.zld + j];
       }
     }
   });

@@ -107,12 +107,16 @@ __global__ void __launch_bounds__(NT) k_assemble_E(
 
 void build_coarse(Handle& h, cudaStream_t s) {
   Coarse& co = h.co;
-  const int N = h.N, nev = h.nev;
+  const int N = h.N, nev = co.zld;  // the row stride of the Z_i blocks
   DevMem& mem = h.mem;
   co.h_count.assign(N, 0);
+  co.h_count_g.assign(N, 0);
+  co.h_lift_count.assign(N, 0);
   co.h_sweeps.assign(N, 0);
-  if (h.nev > 0 && h.opt.coarse) {
+  if (co.count) {
     CK(cudaMemcpyAsync(co.h_count.data(), co.count, 4 * N, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(co.h_count_g.data(), co.count_g, 4 * N, cudaMemcpyDeviceToHost, s));
+    if (co.lift_count) CK(cudaMemcpyAsync(co.h_lift_count.data(), co.lift_count, 4 * N, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(co.h_sweeps.data(), co.sweeps, 4 * N, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
   }

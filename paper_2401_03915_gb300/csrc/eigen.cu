@@ -335,6 +335,19 @@ __device__ void fill_random(T* Y, int L, int s, int sp, int j0, uint64_t seed, u
   __syncthreads();
 }
 
+// Where a run of the subspace iteration writes its results.  The gevpsvd
+// run keeps up to nkeep = nev pairs from column 0 of each Z_i block; the
+// lifting run (eq. uppergevp, lift = 1) keeps up to nkeep = nev_lift pairs
+// after them (zcol0[i] = the gevpsvd count), skipping the skip[i] leading pairs
+// that overlap 1 shares with eq. gevpsvd.
+struct EigOut {
+  int zld;                  // row stride of the Z_i blocks (all runs)
+  int nkeep;                // pairs kept at most; leading dimension of values, resid
+  const int32_t* zcol0;     // first column of this run in Z_i (null: 0)
+  const int32_t* skip;      // leading Ritz pairs left out (null: none)
+  int lift;                 // 1: report 1 + mu and scale the vectors by sqrt((1 + mu) / mu)
+};
+
 template <typename T, bool SPD>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 4 : 1) k_subspace(
     const T* __restrict__ XpT_all, const int64_t* __restrict__ xs_off, const T* __restrict__ S_all,
@@ -349,7 +362,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 4 : 1) k_subspace(
     const float* __restrict__ warm, int wld, int wk, const int64_t* __restrict__ wseg, float* __restrict__ tgt,
     double* __restrict__ values,
     double* __restrict__ resid, int32_t* __restrict__ count, int32_t* __restrict__ sweeps_out,
-    double* __restrict__ Z, const int64_t* __restrict__ z_off) {
+    double* __restrict__ Z, const int64_t* __restrict__ z_off, EigOut eo) {
   COUNT_LAUNCH();
   extern __shared__ double shd[];
   __shared__ int perm[128];
@@ -362,10 +375,15 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 4 : 1) k_subspace(
   const int dim = SPD ? g : p;
   const int s = min(nev + over, dim);
   const int k = min(nev, min(s, min(p, g)));
+  const int zc0 = eo.zcol0 ? eo.zcol0[i] : 0;
   if (k <= 0 || s <= 0) {
     if (threadIdx.x == 0) { count[i] = 0; sweeps_out[i] = 0; }
-    for (int j = threadIdx.x; j < nev; j += NT) { values[(int64_t)i * nev + j] = 0; resid[(int64_t)i * nev + j] = 0; }
-    for (int64_t idx = threadIdx.x; idx < (int64_t)p * nev; idx += NT) Z[z_off[i] + idx] = 0;
+    for (int j = threadIdx.x; j < eo.nkeep; j += NT) {
+      values[(int64_t)i * eo.nkeep + j] = 0;
+      resid[(int64_t)i * eo.nkeep + j] = 0;
+    }
+    for (int64_t idx = threadIdx.x; idx < (int64_t)p * eo.nkeep; idx += NT)
+      Z[z_off[i] + (idx / eo.nkeep) * eo.zld + zc0 + idx % eo.nkeep] = 0;
     return;
   }
   const int sp = (s + 3) & ~3;
@@ -639,21 +657,25 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 4 : 1) k_subspace(
     }
   }
   __syncthreads();
+  // kept: the leading numerically nonzero values (after the skipped ones);
+  // with a threshold (tau^2: eigenvalues of eq. gevpsvd, squared singular
+  // values of D_i Pi_i; lifting: lambda - 1 = mu above nu - 1) only those above it
+  const int sk = eo.skip ? min(eo.skip[i], k) : 0;
   int kept = 0;
   {
     const T mu0 = mu[perm[0]] > T(0) ? mu[perm[0]] : T(0);
-    // numerically nonzero values; with a threshold (tau^2: eigenvalues of
-    // eq. gevpsvd, squared singular values of D_i Pi_i) only those above it
-    for (int j = 0; j < k; ++j)
-      if (mu[perm[j]] > T(sizeof(T) == 8 ? 1e-12 : 1e-6) * mu0 && (thresh <= 0 || (double)mu[perm[j]] > thresh))
-        kept = j + 1;
+    for (int j = sk; j < k && kept < eo.nkeep; ++j) {
+      if (mu[perm[j]] > T(sizeof(T) == 8 ? 1e-12 : 1e-6) * mu0 && (thresh <= 0 || (double)mu[perm[j]] > thresh)) ++kept;
+      else break;
+    }
   }
   if (threadIdx.x == 0) { count[i] = kept; sweeps_out[i] = sweep; }
-  for (int j = threadIdx.x; j < nev; j += NT) {
-    const int c = j < kept ? perm[j] : 0;
-    double v = j < kept ? (SPD ? (double)mu[c] : sqrt(fmax((double)mu[c], 0.0))) : 0.0;
-    values[(int64_t)i * nev + j] = v;
-    resid[(int64_t)i * nev + j] = j < kept ? (double)rn[c] : 0.0;
+  for (int j = threadIdx.x; j < eo.nkeep; j += NT) {
+    const int c = j < kept ? perm[sk + j] : 0;
+    double v = 0.0;
+    if (j < kept) v = eo.lift ? 1.0 + (double)mu[c] : (SPD ? (double)mu[c] : sqrt(fmax((double)mu[c], 0.0)));
+    values[(int64_t)i * eo.nkeep + j] = v;
+    resid[(int64_t)i * eo.nkeep + j] = j < kept ? (double)rn[c] : 0.0;
   }
   if (tgt != nullptr && SPD) {
     // converged Ritz vectors z (Gamma_delta rows), the network's training targets
@@ -665,16 +687,23 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 4 : 1) k_subspace(
   }
   double* Zi = Z + z_off[i];
   if (SPD) {
-    // Z_i = S_I U^T z (undo the diagonal scaling), FP64 output p x nev
+    // Z_i = S_I U^T z (undo the diagonal scaling), FP64 output; lifting: the
+    // A_ii-normalised u_I = sqrt((1 + mu) / mu) U^T z
     cta_gemm<T, true>(p, s, g, U, ld, Y, sp, V, sp, gsm);
-    for (int64_t idx = threadIdx.x; idx < (int64_t)p * nev; idx += NT) {
-      int r = (int)(idx / nev), j = (int)(idx % nev);
-      Zi[idx] = j < kept ? (double)V[(int64_t)r * sp + perm[j]] * ds[omega[pos0 + r]] : 0.0;
+    for (int64_t idx = threadIdx.x; idx < (int64_t)p * eo.nkeep; idx += NT) {
+      const int r = (int)(idx / eo.nkeep), j = (int)(idx % eo.nkeep);
+      double z = 0.0;
+      if (j < kept) {
+        const int c = perm[sk + j];
+        z = (double)V[(int64_t)r * sp + c] * ds[omega[pos0 + r]];
+        if (eo.lift) z *= sqrt((1.0 + (double)mu[c]) / (double)mu[c]);
+      }
+      Zi[(int64_t)r * eo.zld + zc0 + j] = z;
     }
   } else {
-    for (int64_t idx = threadIdx.x; idx < (int64_t)p * nev; idx += NT) {
-      int r = (int)(idx / nev), j = (int)(idx % nev);
-      Zi[idx] = j < kept ? (double)Y[(int64_t)r * sp + perm[j]] : 0.0;
+    for (int64_t idx = threadIdx.x; idx < (int64_t)p * eo.nkeep; idx += NT) {
+      const int r = (int)(idx / eo.nkeep), j = (int)(idx % eo.nkeep);
+      Zi[(int64_t)r * eo.zld + zc0 + j] = j < kept ? (double)Y[(int64_t)r * sp + perm[j]] : 0.0;
     }
   }
 }
@@ -808,6 +837,14 @@ __global__ void k_round_z(double* __restrict__ Z, float* __restrict__ Zf, int64_
   }
 }
 
+// coarse vectors per subdomain: eq. gevpsvd's and the lifting ones
+__global__ void k_total_count(int N, const int32_t* __restrict__ cg, const int32_t* __restrict__ cl,
+                              int32_t* __restrict__ c) {
+  COUNT_LAUNCH();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) c[i] = cg[i] + (cl ? cl[i] : 0);
+}
+
 template <typename T>
 void run_eigen(Handle& h, cudaStream_t s) {
   const int N = h.N, nev = h.nev;
@@ -816,8 +853,14 @@ void run_eigen(Handle& h, cudaStream_t s) {
   DevMem& mem = h.mem;
   const bool spd = h.opt.spd != 0;
   const int over = std::max(0, h.opt.oversample);
-  std::vector<int64_t> scr(N), zo(N + 1);
-  int64_t tot = 0, zt = 0;
+  // eq. uppergevp (lifting) vectors: up to nev_lift more columns per Z_i;
+  // with overlap 1 its operator is the one of eq. gevpsvd, so that run's
+  // leading pairs are skipped (the lifting iteration computes nev + nev_lift)
+  const int nlift = h.lift ? h.nev_lift : 0;
+  const int lift_nev = h.delta == 1 ? nev + nlift : nlift;
+  co.zld = std::max(1, nev + nlift);
+  std::vector<int64_t> scr(N), zo(N + 1), scl(N);
+  int64_t tot = 0, zt = 0, totl = 0;
   int smax = 1;
   for (int i = 0; i < N; ++i) {
     int p = h.h_p[i], g = h.h_g[i];
@@ -828,10 +871,17 @@ void run_eigen(Handle& h, cudaStream_t s) {
     scr[i] = tot;
     tot += 7LL * std::max(p, g) * sp;
     zo[i] = zt;
-    zt += (int64_t)p * nev;
+    zt += (int64_t)p * co.zld;
+    if (nlift > 0) {
+      const int gl = h.h_n[i] - p;  // the lifting operator lives on Omega_i minus I_i
+      const int sl = std::max(1, std::min(lift_nev + over, gl));
+      smax = std::max(smax, sl);
+      scl[i] = totl;
+      totl += 7LL * std::max(p, gl) * ((sl + 3) & ~3);
+    }
   }
   zo[N] = zt;
-  if (smax > 96) fail(ASM_ERR_UNSUPPORTED, "nev + oversample exceeds 96");
+  if (smax > 96) fail(ASM_ERR_UNSUPPORTED, "nev (+ nev_lift) + oversample exceeds 96");
   co.s_max = smax;
   co.h_z_off = zo;
   co.scratch = mem.alloc<T>(tot);
@@ -841,6 +891,7 @@ void run_eigen(Handle& h, cudaStream_t s) {
   co.values = mem.alloc<double>((int64_t)N * std::max(nev, 1));
   co.resid = mem.alloc<double>((int64_t)N * std::max(nev, 1));
   co.count = mem.alloc<int32_t>(N);
+  co.count_g = mem.alloc<int32_t>(N);
   co.sweeps = mem.alloc<int32_t>(N);
   CK(cudaMemcpyAsync(co.scr_off, scr.data(), 8 * N, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(co.z_off, zo.data(), 8 * (N + 1), cudaMemcpyHostToDevice, s));
@@ -902,16 +953,47 @@ void run_eigen(Handle& h, cudaStream_t s) {
   }
   auto launch = [&](auto kern) {
     CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    EigOut eo{co.zld, nev, nullptr, nullptr, 0};
     kern<<<N, NT, smem, s>>>((const T*)dn.XpT, dn.xs_off, (const T*)dn.S, dn.s_off, (const T*)dn.work, dn.work_off,
                              dn.np, h.dev_n, h.dev_m, h.dev_p, h.ov.sub_off, h.ov.ent_off, h.ov.lcol, h.ov.omega,
                              h.row_ptr, h.col_idx, h.val, h.dscale, aval, (T*)co.scratch, co.scr_off, nev, over, maxsw,
                              degree, tol, h.opt.tau > 0 ? h.opt.tau * h.opt.tau : 0.0, h.opt.seed, warm, wld, wk,
-                             h.wseg, h.wtgt, co.values, co.resid, co.count,
-                             co.sweeps, co.Z, co.z_off);
+                             h.wseg, h.wtgt, co.values, co.resid, co.count_g,
+                             co.sweeps, co.Z, co.z_off, eo);
   };
-  if (spd) launch(k_subspace<T, true>);
-  else launch(k_subspace<T, false>);
+  if (nev > 0) {
+    if (spd) launch(k_subspace<T, true>);
+    else launch(k_subspace<T, false>);
+  } else {
+    CK(cudaMemsetAsync(co.count_g, 0, 4 * N, s));
+    CK(cudaMemsetAsync(co.sweeps, 0, 4 * N, s));
+  }
   CK_LAUNCH("subspace iteration");
+  if (nlift > 0) {
+    // eq. uppergevp in its reduced form: with A_ii = L L^T and W = L^{-1}
+    // (I_i first), lambda = 1 + sigma^2 for the singular values sigma of
+    // W21 L11, whose squares are the eigenvalues of W21 A^_II W21^T,
+    // W21 = W[Omega_i minus I_i, I_i]; the A_ii-normalised lifting vector on
+    // I_i is sqrt((1 + sigma^2) / sigma^2) W21^T z (proof of Theorem 3.4)
+    co.lift_values = mem.alloc<double>((int64_t)N * nlift);
+    co.lift_resid = mem.alloc<double>((int64_t)N * nlift);
+    co.lift_count = mem.alloc<int32_t>(N);
+    co.lift_sweeps = mem.alloc<int32_t>(N);
+    T* lscr = mem.alloc<T>(std::max<int64_t>(totl, 1));
+    int64_t* lscr_off = mem.alloc<int64_t>(N);
+    CK(cudaMemcpyAsync(lscr_off, scl.data(), 8 * N, cudaMemcpyHostToDevice, s));
+    EigOut eo{co.zld, nlift, co.count_g, h.delta == 1 ? co.count_g : nullptr, 1};
+    auto kern = k_subspace<T, true>;
+    CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<N, NT, smem, s>>>((const T*)dn.XpT, dn.xs_off, (const T*)dn.S, dn.s_off, (const T*)dn.work, dn.work_off,
+                             dn.np, h.dev_n, h.dev_p, h.dev_p, h.ov.sub_off, h.ov.ent_off, h.ov.lcol, h.ov.omega,
+                             h.row_ptr, h.col_idx, h.val, h.dscale, aval, lscr, lscr_off, lift_nev, over, maxsw,
+                             degree, tol, h.opt.nu - 1.0, h.opt.seed ^ 0x6C1F7A3Dull, nullptr, 0, 0, nullptr, nullptr,
+                             co.lift_values, co.lift_resid, co.lift_count, co.lift_sweeps, co.Z, co.z_off, eo);
+    CK_LAUNCH("lifting subspace iteration");
+  }
+  k_total_count<<<(unsigned)ceil_div(N, NT), NT, 0, s>>>(N, co.count_g, nlift > 0 ? co.lift_count : nullptr, co.count);
+  CK_LAUNCH("coarse counts");
   if (h.fp32) {
     // the apply restricts and prolongs with an FP32 copy of Z; rounding the
     // FP64 master to the same values keeps E = Z^T A Z exact for that basis
@@ -925,7 +1007,7 @@ void run_eigen(Handle& h, cudaStream_t s) {
 }  // namespace
 
 void build_eigen(Handle& h, cudaStream_t s) {
-  if (h.nev <= 0 || !h.opt.coarse) {
+  if ((h.nev <= 0 && !h.lift) || !h.opt.coarse) {
     h.co.h_count.assign(h.N, 0);
     return;
   }

@@ -98,9 +98,16 @@ struct Coarse {
   int32_t s_max = 0;                  // block width of the subspace iteration
   std::vector<int32_t> h_count, h_col_off, h_sweeps;
   std::vector<int64_t> h_z_off;
-  int32_t* count = nullptr;           // kept vectors per subdomain
+  int32_t* count = nullptr;           // coarse vectors per subdomain (eq. gevpsvd + lifting)
+  int32_t* count_g = nullptr;         // of which from eq. gevpsvd (first columns of Z_i)
+  int32_t zld = 0;                    // columns of each Z_i block: nev + nev_lift
+  std::vector<int32_t> h_count_g, h_lift_count;
+  double* lift_values = nullptr;      // N * nev_lift: lambda of eq. uppergevp kept (descending)
+  double* lift_resid = nullptr;       // N * nev_lift eigen-residuals
+  int32_t* lift_count = nullptr;      // lifting vectors per subdomain
+  int32_t* lift_sweeps = nullptr;
   int32_t* col_off = nullptr;         // N+1 first coarse column
-  int64_t* z_off = nullptr;           // offset of Z_i (p_i x nev, row-major FP64)
+  int64_t* z_off = nullptr;           // offset of Z_i (p_i x zld, row-major FP64)
   double* Z = nullptr;
   float* Zf = nullptr;                // single-precision local work: Z rounded to FP32 for the
                                       // restriction and prolongation (Z itself holds the same values)
@@ -140,6 +147,8 @@ struct Handle {
   bool host_io = false;
   bool fp32 = false;
   bool s16 = false;                 // explicit local inverses stored in FP16 where the bound allows
+  bool lift = false;                // eq. uppergevp vectors added (opt.nu > 0, SPD)
+  int32_t nev_lift = 0;             // at most this many per subdomain
   DevMem mem;
   int32_t *row_ptr = nullptr, *col_idx = nullptr, *part = nullptr;
   double* val = nullptr;

@@ -62,5 +62,10 @@ def test_invalid_arguments_are_rejected_before_any_device_work(lib):
     with pytest.raises(P.AsmError) as e:
         P.asm_setup(rp, ci, va, part, 1, 1, 1, P.default_options(local_precision=7), on_device=False)
     assert e.value.name == "INVALID_ARG"
+    # eq. uppergevp options: its eigenvalues are >= 1, it is for SPD A, nev_lift in 0..120
+    for kw in (dict(nu=0.5), dict(nu=2.0, spd=0), dict(nu=2.0, nev_lift=-1), dict(nu=float("nan"))):
+        with pytest.raises(P.AsmError) as e:
+            P.asm_setup(rp, ci, va, part, 1, 1, 1, P.default_options(**kw), on_device=False)
+        assert e.value.name == "INVALID_ARG", kw
     assert L.asm_apply(None, None, None, None) == 1
     assert b"null" in L.asm_last_error()

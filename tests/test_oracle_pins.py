@@ -447,3 +447,33 @@ def test_nonsymmetric_fgmres_matches_direct():
     assert true <= 1e-7
     x = spla.spsolve(A.tocsc(), p.b)
     assert np.linalg.norm(res.x - x) / np.linalg.norm(x) < 1e-5
+
+
+@pytest.mark.parametrize("delta", [1, 2, 3])
+def test_reduced_lifting_form_matches_full_gevp(delta):
+    """Eq. uppergevp in the reduced form the CUDA path uses (I_i ordered first,
+    A_ii = L L^T, W = L^{-1}, W21 = W[Omega_i minus I_i, I_i]): its eigenvalues
+    are 1 + the eigenvalues of W21 A_II W21^T, and the A_ii-normalised
+    eigenvector restricted to I_i is sqrt((1 + s) / s) W21^T z for the unit
+    eigenvector z of eigenvalue s.  Checked against the full dense pencil
+    D_i A_ii D_i u = lambda A_ii u of the oracle."""
+    p = diffusion3d(12, (2, 2, 2), contrast=1e3, delta=delta, nev=4)
+    A = p.csr()
+    ov = O.overlap(A, p.part, p.N, delta)[3]
+    Aii = O.local_matrix(A, ov)
+    lam, U = O.lifting_gevp(Aii, ov)
+    pi = ov.p
+    W = np.linalg.inv(np.linalg.cholesky(Aii))
+    W21 = W[pi:, :pi]
+    s2, Zs = np.linalg.eigh(W21 @ Aii[:pi, :pi] @ W21.T)
+    s2, Zs = s2[::-1], Zs[:, ::-1]
+    k = 6
+    np.testing.assert_allclose(1.0 + s2[:k], lam[:k], rtol=1e-11)
+    assert np.all(lam[:k] > 1.0)
+    for j in range(k):
+        if (lam[j] - lam[j + 1]) / lam[j] < 1e-6:
+            continue
+        u = np.sqrt((1 + s2[j]) / s2[j]) * (W21.T @ Zs[:, j])
+        uo = U[:pi, j]
+        assert abs(abs(u @ uo) - np.linalg.norm(u) * np.linalg.norm(uo)) < 1e-10 * np.linalg.norm(uo) ** 2
+        np.testing.assert_allclose(np.linalg.norm(u), np.linalg.norm(uo), rtol=1e-10)
