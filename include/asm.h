@@ -203,6 +203,14 @@ asm_status asm_solve(asm_handle* h, const double* b, double* x, const asm_solve_
 /* y = A x with the handle's copy of A (device x, y). */
 asm_status asm_spmv(asm_handle* h, const double* x, double* y, void* stream);
 
+/* y = A x for a CSR matrix given by device arrays (n rows, nnz stored
+ * entries; int32 row_ptr (n+1) and col_idx, FP64 val), with the kernel the
+ * Krylov loop uses for that shape: rows of at most about 12 entries on
+ * average one thread per row, longer rows by lane groups.  No handle and no allocation; x and y (device, n) must not
+ * overlap.  Errors: INVALID_ARG (null pointer, negative size, x == y), CUDA. */
+asm_status asm_csr_spmv(int32_t n, int32_t nnz, const int32_t* row_ptr, const int32_t* col_idx,
+                        const double* val, const double* x, double* y, void* stream);
+
 asm_status asm_get_info(const asm_handle* h, asm_setup_info* info);
 
 /* Measurement helpers (no counterpart in the paper; used by the benchmark).
@@ -217,6 +225,10 @@ asm_status asm_get_info(const asm_handle* h, asm_setup_info* info);
  * as asm_apply runs it (coarse part overlapped on a side stream).
  * r, z: device. */
 uint64_t asm_kernel_launches(void);
+/* asm_time_spmv: mean milliseconds (ms[0]) of the PCG loop's fused
+ * q = A p, p.q launch on the handle's matrix over `iters` launches (after 3
+ * untimed ones), CUDA events on `stream`; p, q device vectors of length n. */
+asm_status asm_time_spmv(asm_handle* h, const double* p, double* q, int32_t iters, void* stream, double* ms);
 asm_status asm_time_apply(asm_handle* h, const double* r, double* z, int32_t iters, void* stream, double* ms);
 const char* asm_stage_name(int32_t stage);
 

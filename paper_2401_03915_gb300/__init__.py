@@ -96,6 +96,10 @@ def load(path: str | None = None) -> C.CDLL:
     L.asm_kernel_launches.argtypes = []
     L.asm_time_apply.argtypes = [vp, vp, vp, i32, vp, C.POINTER(C.c_double)]
     L.asm_time_apply.restype = C.c_int
+    L.asm_csr_spmv.argtypes = [i32, i32, vp, vp, vp, vp, vp, vp]
+    L.asm_csr_spmv.restype = C.c_int
+    L.asm_time_spmv.argtypes = [vp, vp, vp, i32, vp, C.POINTER(C.c_double)]
+    L.asm_time_spmv.restype = C.c_int
     L.asm_spmv_dot_noalloc.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp]
     L.asm_spmv_dot_noalloc.restype = C.c_int
     i64, f32 = C.c_int64, C.c_float
@@ -268,6 +272,28 @@ def asm_time_apply(h: int, r, z, iters: int = 10, stream=None) -> dict:
     _check(load().asm_time_apply(h, _ptr(r), _ptr(z), iters, _stream(stream), ms))
     return {"tile_pass": ms[0], "local": ms[1], "coarse": ms[2], "pull": ms[3], "sequential": ms[4],
             "apply": ms[5]}
+
+
+def asm_csr_spmv(row_ptr, col_idx, val, x, y, stream=None) -> None:
+    """y = A x for a CSR matrix held in CUDA tensors (int32 indices, float64
+    values and vectors), with the library's SpMV kernel; no handle."""
+    import torch
+    for name, t, dt in (("row_ptr", row_ptr, torch.int32), ("col_idx", col_idx, torch.int32),
+                        ("val", val, torch.float64), ("x", x, torch.float64), ("y", y, torch.float64)):
+        if not isinstance(t, torch.Tensor) or t.dtype != dt or not t.is_cuda or not t.is_contiguous():
+            raise TypeError(f"{name} must be a contiguous CUDA tensor of {dt}")
+    n = int(x.numel())
+    if row_ptr.numel() != n + 1 or y.numel() != n or col_idx.numel() != val.numel():
+        raise ValueError("sizes: row_ptr n + 1, y n, col_idx and val alike")
+    _check(load().asm_csr_spmv(n, int(val.numel()), _ptr(row_ptr), _ptr(col_idx), _ptr(val), _ptr(x), _ptr(y),
+                               _stream(stream)))
+
+
+def asm_time_spmv(h: int, p, q, iters: int = 100, stream=None) -> float:
+    """Mean ms of the PCG loop's fused q = A p, p.q launch on the handle's matrix."""
+    ms = (C.c_double * 1)()
+    _check(load().asm_time_spmv(h, _ptr(p), _ptr(q), iters, _stream(stream), ms))
+    return ms[0]
 
 
 def asm_spmv_dot_noalloc(row_ptr, col_idx, val, x, y, xty, stream=None) -> None:

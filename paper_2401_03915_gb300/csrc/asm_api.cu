@@ -329,6 +329,20 @@ asm_status asm_time_apply(asm_handle* H, const double* r, double* z, int32_t ite
   return guarded([&] { time_apply(H->h, r, z, iters, static_cast<cudaStream_t>(stream), ms); });
 }
 
+asm_status asm_csr_spmv(int32_t n, int32_t nnz, const int32_t* row_ptr, const int32_t* col_idx, const double* val,
+                        const double* x, double* y, void* stream) {
+  if (n < 0 || nnz < 0 || (n > 0 && (!row_ptr || !col_idx || !val || !x || !y)))
+    return set_error(ASM_ERR_INVALID_ARG, "asm_csr_spmv: null pointer or negative size");
+  if (n > 0 && x == y) return set_error(ASM_ERR_INVALID_ARG, "asm_csr_spmv: x and y must not alias");
+  return guarded([&] { csr_spmv(n, nnz, row_ptr, col_idx, val, x, y, static_cast<cudaStream_t>(stream)); });
+}
+
+asm_status asm_time_spmv(asm_handle* H, const double* p, double* q, int32_t iters, void* stream, double* ms) {
+  if (!H || !p || !q || !ms || iters < 1) return set_error(ASM_ERR_INVALID_ARG, "null argument or iters < 1");
+  if (p == q) return set_error(ASM_ERR_INVALID_ARG, "p and q must not alias");
+  return guarded([&] { time_pcg_spmv(H->h, p, q, iters, static_cast<cudaStream_t>(stream), ms); });
+}
+
 asm_status asm_get_info(const asm_handle* H, asm_setup_info* info) {
   if (!H || !info) return set_error(ASM_ERR_INVALID_ARG, "null argument");
   *info = H->h.info;

@@ -195,6 +195,11 @@ void apply_preconditioner(Handle& h, const double* r, double* z, cudaStream_t s,
 void time_apply(Handle& h, const double* r, double* z, int iters, cudaStream_t s, double* ms);
 void tune_apply(Handle& h, cudaStream_t s);                                       // apply.cu
 void spmv(Handle& h, const double* x, double* y, cudaStream_t s);                 // krylov.cu
+// y = A x for a caller's CSR matrix (device arrays), no handle, no allocation (krylov.cu)
+void csr_spmv(int n, int64_t nnz, const int32_t* rp, const int32_t* ci, const double* val, const double* x,
+              double* y, cudaStream_t s);
+// mean time of the PCG loop's fused q = A p, p.q over iters launches (krylov.cu)
+void time_pcg_spmv(Handle& h, const double* p, double* q, int iters, cudaStream_t s, double* ms);
 // y = b - A x (krylov.cu); nothing when *done is set
 void residual(Handle& h, const double* b, const double* x, double* y, cudaStream_t s, const int32_t* done);
 void coarse_solve(Handle& h, const double* c, double* y, cudaStream_t s,
