@@ -182,10 +182,3 @@ def features(A: sp.spmatrix, ov: Overlap) -> np.ndarray:
                   y0[r], np.log10(1e-4 + abs(y0[r])) / 4 + 1, y1[r], np.log10(1e-4 + abs(y1[r])) / 4 + 1,
                   y2[r], t[r], np.cos(2 * np.pi * (t[r] + 0.5)), np.sin(2 * np.pi * (t[r] + 0.5))]
     return out
-
-
-def top_eigvecs(A: sp.spmatrix, ov: Overlap, k: int) -> np.ndarray:
-    """Orthonormal top-k eigenvectors of K (the targets the network learns)."""
-    K = reduced_operator(A, ov)
-    ev, V = np.linalg.eigh(0.5 * (K + K.T))
-    return V[:, ::-1][:, :k]

@@ -1056,7 +1056,8 @@ void time_impl(Handle& h, const double* r, double* z, int iters, cudaStream_t s,
 
 // Autotuner of the apply's launch shape: the whole apply (local tile passes
 // with the coarse part beside them) is timed for each candidate number of
-// resident tile-pass blocks per SM and the fastest is kept.  Results are
+// resident tile-pass blocks per SM and the fastest is kept, ties (within 2%)
+// going to the faster row pass.  Results are
 // cached per (device, tiles, subdomains, coarse size, precision and tile
 // storage), so only the first setup of a given shape pays for the measurement.
 std::mutex g_tune_mutex;
@@ -1079,6 +1080,7 @@ void tune_impl(Handle& h, cudaStream_t s) {
   CK(cudaEventCreate(&e1));
   const int cand[5] = {2, 3, 4, 6, 8};
   float best_ms[5] = {3.0e38f, 3.0e38f, 3.0e38f, 3.0e38f, 3.0e38f};
+  float pass_ms[5] = {3.0e38f, 3.0e38f, 3.0e38f, 3.0e38f, 3.0e38f};
   for (int round = 0; round < 2; ++round) {
     for (int q = 0; q < 5; ++q) {
       h.tile_ctas = cand[q];
@@ -1090,12 +1092,24 @@ void tune_impl(Handle& h, cudaStream_t s) {
       float ms = 0;
       CK(cudaEventElapsedTime(&ms, e0, e1));
       best_ms[q] = std::min(best_ms[q], ms);
+      // the row pass alone (the input gathered by the applies above)
+      CK(cudaEventRecord(e0, s));
+      for (int rep = 0; rep < 4; ++rep) row_pass<T>(h, s, nullptr);
+      CK(cudaEventRecord(e1, s));
+      CK(cudaEventSynchronize(e1));
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      pass_ms[q] = std::min(pass_ms[q], ms);
     }
   }
-  int best = cand[0];
+  // the fastest whole apply; shapes within 2% of it count as ties (the coarse
+  // part beside the local one makes the apply insensitive to the shape over a
+  // range), broken by the faster row pass
   float bm = best_ms[0];
-  for (int q = 1; q < 5; ++q)
-    if (best_ms[q] < bm) { bm = best_ms[q]; best = cand[q]; }
+  for (int q = 1; q < 5; ++q) bm = std::min(bm, best_ms[q]);
+  int best = -1;
+  for (int q = 0; q < 5; ++q)
+    if (best_ms[q] <= 1.02f * bm && (best < 0 || pass_ms[q] < pass_ms[best])) best = q;
+  best = cand[best];
   h.tile_ctas = best;
   CK(cudaEventDestroy(e0));
   CK(cudaEventDestroy(e1));

@@ -82,7 +82,9 @@ struct Scale {
 // C (M x N, ldc) = A (M x K) B (K x N, ldb) (with SUB: C -= A B); A row-major
 // (A[m*lda + k]) or, with ACOL, column-major (A[k*lda + m]).  The product's
 // row m is multiplied by rs(m); A's column k by ks(k) (or divided, with kinv).
-template <typename T, bool ACOL, bool SUB = false>
+// UPPER (with ACOL): A is the transpose of a lower-triangular block whose
+// upper part in memory holds other data, so A(m, k) is taken as 0 for k < m.
+template <typename T, bool ACOL, bool SUB = false, bool UPPER = false>
 __device__ void cta_gemm(int M, int N, int K, const T* __restrict__ A, int lda, const T* __restrict__ B, int ldb,
                          T* __restrict__ C, int ldc, T* sm, Scale rs = Scale(), Scale ks = Scale(), bool kinv = false) {
   constexpr int LA = gemm_lda<T>(), LB = gemm_ldb<T>();
@@ -112,7 +114,8 @@ __device__ void cta_gemm(int M, int N, int K, const T* __restrict__ A, int lda, 
         } else {
           for (int idx = t; idx < GM * GK; idx += NT) {
             int kk = idx / GM, r = idx % GM;
-            T v = (m0 + r < M && k0 + kk < K) ? A[(int64_t)(k0 + kk) * lda + m0 + r] : T(0);
+            T v = (m0 + r < M && k0 + kk < K && (!UPPER || k0 + kk >= m0 + r)) ? A[(int64_t)(k0 + kk) * lda + m0 + r]
+                                                                              : T(0);
             if (ks.on() && k0 + kk < K) v = (T)(kinv ? (double)v / ks(k0 + kk) : (double)v * ks(k0 + kk));
             As[r * LA + kk] = v;
           }
@@ -346,6 +349,7 @@ struct EigOut {
   const int32_t* zcol0;     // first column of this run in Z_i (null: 0)
   const int32_t* skip;      // leading Ritz pairs left out (null: none)
   int lift;                 // 1: report 1 + mu and scale the vectors by sqrt((1 + mu) / mu)
+  int refine;               // FP64, lifting or overlap 1: report the variational Rayleigh quotient
 };
 
 template <typename T, bool SPD>
@@ -670,13 +674,6 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 4 : 1) k_subspace(
     }
   }
   if (threadIdx.x == 0) { count[i] = kept; sweeps_out[i] = sweep; }
-  for (int j = threadIdx.x; j < eo.nkeep; j += NT) {
-    const int c = j < kept ? perm[sk + j] : 0;
-    double v = 0.0;
-    if (j < kept) v = eo.lift ? 1.0 + (double)mu[c] : (SPD ? (double)mu[c] : sqrt(fmax((double)mu[c], 0.0)));
-    values[(int64_t)i * eo.nkeep + j] = v;
-    resid[(int64_t)i * eo.nkeep + j] = j < kept ? (double)rn[c] : 0.0;
-  }
   if (tgt != nullptr && SPD) {
     // converged Ritz vectors z (Gamma_delta rows), the network's training targets
     float* tb = tgt + wseg[i] * nev;
@@ -685,11 +682,97 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 4 : 1) k_subspace(
       tb[idx] = j < kept ? (float)Y[(int64_t)r * sp + perm[j]] : 0.f;
     }
   }
+  // SPD: V = U^T Y, the coarse vectors in the scaled space (I_i rows)
+  if (SPD) cta_gemm<T, true>(p, s, g, U, ld, Y, sp, V, sp, gsm);
+  __shared__ double muref[128];
+  if constexpr (SPD && sizeof(T) == 8) {
+    if (eo.refine && kept > 0) {
+      // Eigenvalues from the variational form of eq. uppergevp, which also
+      // holds eq. gevpsvd's for overlap 1 (lambda = 1 + mu): with c the vector
+      // on I_i and v on Omega_i minus I_i,
+      //   lambda = c^T A^_II c / min_v [c; v]^T A^ [c; v],
+      // stationary in both c and v, so the errors of the explicit W = L^{-1}
+      // (about eps cond(A^_ii)) enter squared.  v is taken as
+      // (A^{-1} [A^_II c; 0])_G / lambda = W22^T (W21 A^_II c) / lambda (exact
+      // at an eigenpair); lambda and mu then come from the sparse local rows.
+      const int kk = kept;
+      T* Cc = Yb;   // p x kk, the kept columns of V
+      T* Tt = Yc;   // p x kk, A^_II c
+      T* QG = KY;   // g x kk, W21 t
+      T* Vv = AV;   // g x kk, v
+      for (int64_t idx = threadIdx.x; idx < (int64_t)p * kk; idx += NT) {
+        const int r = (int)(idx / kk), j = (int)(idx % kk);
+        Cc[idx] = V[(int64_t)r * sp + perm[sk + j]];
+      }
+      __syncthreads();
+      mul_AII(p, pos0, ent_off, lcol, aval, Cc, Tt, kk, kk);
+      cta_gemm<T, false>(g, kk, p, U, ld, Tt, kk, QG, kk, gsm);        // W21 t
+      cta_gemm<T, true, false, true>(g, kk, g, U + p, ld, QG, kk, Vv, kk, gsm);  // W22^T (W21 t), W22 lower
+      for (int64_t idx = threadIdx.x; idx < (int64_t)g * kk; idx += NT)
+        Vv[idx] /= T(1) + mu[perm[sk + (int)(idx % kk)]];
+      __syncthreads();
+      // one warp per column j, w = [c; v]: a = c^T A^_II c, b = c^T A^_IG v,
+      // d = v^T A^_GG v from the local rows, and D = w^T (A^ w) with each
+      // row of A^ w summed in double-double (exact products by fma, TwoSum):
+      // A^ w is S_I c on I_i and about 0 on the rest, so D has no large
+      // cancellation even where lambda = a / D is 1e5.  mu = lambda - 1, or
+      // -(2b + d) / D for lambda < 2 (no cancellation against 1 there).
+      for (int j = wid; j < kk; j += NT / 32) {
+        double sa = 0, sb = 0, sd = 0, sD = 0;
+        for (int a = lane; a < n; a += 32) {
+          const int64_t e0 = ent_off[pos0 + a], e1 = ent_off[pos0 + a + 1];
+          double hi = 0, lo = 0, gpart = 0, ipart = 0;
+          for (int64_t e = e0; e < e1; ++e) {
+            const int lc = lcol[e];
+            if (lc < 0) continue;
+            const double av = (double)aval[e];
+            const double wv = lc < p ? (double)Cc[(int64_t)lc * kk + j] : (double)Vv[(int64_t)(lc - p) * kk + j];
+            const double pr = __dmul_rn(av, wv);
+            const double pe = __fma_rn(av, wv, -pr);
+            const double sm = __dadd_rn(hi, pr);
+            const double bb = __dsub_rn(sm, hi);
+            const double er = __dadd_rn(__dsub_rn(hi, __dsub_rn(sm, bb)), __dsub_rn(pr, bb));
+            hi = sm;
+            lo = __dadd_rn(lo, __dadd_rn(er, pe));
+            if (lc >= p) gpart = __fma_rn(av, wv, gpart);
+            else ipart = __fma_rn(av, wv, ipart);
+          }
+          const double zeta = __dadd_rn(hi, lo);
+          const double wa = a < p ? (double)Cc[(int64_t)a * kk + j] : (double)Vv[(int64_t)(a - p) * kk + j];
+          sD = __fma_rn(wa, zeta, sD);
+          if (a < p) {
+            sa = __fma_rn(wa, ipart, sa);
+            sb = __fma_rn(wa, gpart, sb);
+          } else {
+            sd = __fma_rn(wa, gpart, sd);
+          }
+        }
+        sa = warp_sum(sa);
+        sb = warp_sum(sb);
+        sd = warp_sum(sd);
+        sD = warp_sum(sD);
+        if (lane == 0) {
+          const double lam = sa / sD;
+          muref[j] = lam >= 2.0 ? lam - 1.0 : -(2.0 * sb + sd) / sD;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int j = threadIdx.x; j < eo.nkeep; j += NT) {
+    const int c = j < kept ? perm[sk + j] : 0;
+    double v = 0.0;
+    if (j < kept) {
+      const double m = (SPD && sizeof(T) == 8 && eo.refine) ? muref[j] : (double)mu[c];
+      v = eo.lift ? 1.0 + m : (SPD ? m : sqrt(fmax(m, 0.0)));
+    }
+    values[(int64_t)i * eo.nkeep + j] = v;
+    resid[(int64_t)i * eo.nkeep + j] = j < kept ? (double)rn[c] : 0.0;
+  }
   double* Zi = Z + z_off[i];
   if (SPD) {
     // Z_i = S_I U^T z (undo the diagonal scaling), FP64 output; lifting: the
     // A_ii-normalised u_I = sqrt((1 + mu) / mu) U^T z
-    cta_gemm<T, true>(p, s, g, U, ld, Y, sp, V, sp, gsm);
     for (int64_t idx = threadIdx.x; idx < (int64_t)p * eo.nkeep; idx += NT) {
       const int r = (int)(idx / eo.nkeep), j = (int)(idx % eo.nkeep);
       double z = 0.0;
@@ -953,7 +1036,7 @@ void run_eigen(Handle& h, cudaStream_t s) {
   }
   auto launch = [&](auto kern) {
     CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    EigOut eo{co.zld, nev, nullptr, nullptr, 0};
+    EigOut eo{co.zld, nev, nullptr, nullptr, 0, (sizeof(T) == 8 && spd && h.delta == 1) ? 1 : 0};
     kern<<<N, NT, smem, s>>>((const T*)dn.XpT, dn.xs_off, (const T*)dn.S, dn.s_off, (const T*)dn.work, dn.work_off,
                              dn.np, h.dev_n, h.dev_m, h.dev_p, h.ov.sub_off, h.ov.ent_off, h.ov.lcol, h.ov.omega,
                              h.row_ptr, h.col_idx, h.val, h.dscale, aval, (T*)co.scratch, co.scr_off, nev, over, maxsw,
@@ -982,7 +1065,7 @@ void run_eigen(Handle& h, cudaStream_t s) {
     T* lscr = mem.alloc<T>(std::max<int64_t>(totl, 1));
     int64_t* lscr_off = mem.alloc<int64_t>(N);
     CK(cudaMemcpyAsync(lscr_off, scl.data(), 8 * N, cudaMemcpyHostToDevice, s));
-    EigOut eo{co.zld, nlift, co.count_g, h.delta == 1 ? co.count_g : nullptr, 1};
+    EigOut eo{co.zld, nlift, co.count_g, h.delta == 1 ? co.count_g : nullptr, 1, sizeof(T) == 8 ? 1 : 0};
     auto kern = k_subspace<T, true>;
     CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<N, NT, smem, s>>>((const T*)dn.XpT, dn.xs_off, (const T*)dn.S, dn.s_off, (const T*)dn.work, dn.work_off,

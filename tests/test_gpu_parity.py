@@ -113,6 +113,32 @@ def test_fp64_eigenvalues_and_subspaces(P, case):
     pre.close()
 
 
+def test_fp64_elasticity_values_apply_and_solve(P):
+    """The vector-valued operator (Q1 elasticity, 3 dofs per node, clamped
+    identity rows) in FP64: every subdomain's values within 1e-10, the
+    two-level apply within 1e-10 (the cuts have spectral gaps above 2%), and
+    the oracle's PCG iteration count within one."""
+    prob = elasticity3d(6, (2, 2, 2), nev=8)
+    A, st, pre = _oracle_and_gpu(P, prob, 8, **FP64)
+    vals, cnt = P.asm_get_local_values(pre.h)
+    for i, loc in enumerate(st.locals):
+        k = len(loc.values)
+        assert cnt[i] == k
+        np.testing.assert_allclose(vals[i, :k], loc.values, rtol=1e-10, atol=0)
+        v = loc.all_values
+        assert (v[k - 1] - v[k]) / v[k - 1] > 2e-2
+    r = SplitMix64(23).normal(prob.n)
+    z = pre.apply(torch.as_tensor(r, device="cuda")).cpu().numpy()
+    zr = st.apply(r)
+    np.testing.assert_allclose(z, zr, rtol=0, atol=1e-10 * np.abs(zr).max())
+    ref = O.solve(st, prob.b)
+    x, info = pre.solve(torch.as_tensor(prob.b, device="cuda"))
+    rel = np.linalg.norm(prob.b - A @ x.cpu().numpy()) / np.linalg.norm(prob.b)
+    assert info.converged and rel <= 1.5e-8
+    assert abs(info.iterations - ref.iterations) <= 1, (info.iterations, ref.iterations)
+    pre.close()
+
+
 def test_fp64_apply_matches_oracle(P):
     prob = diffusion3d(16, (2, 2, 2), contrast=1e4, nev=6)
     A, st, pre = _oracle_and_gpu(P, prob, prob.nev, **FP64)
@@ -370,21 +396,12 @@ def test_c2_full_size_fp64(P):
     vals, cnt = P.asm_get_local_values(pre.h)
     ev = np.array(ref["eigenvalues"])
     assert pre.info.n_C == ref["n_C"]
-    # 1e-10 relative, except where the explicit local inverse W = L^{-1}
-    # (FP64) bounds the attainable accuracy: to first order the eigenvalues of
-    # U A^_II U^T then carry a relative error of a few eps * cond(A^_ii).  Such
-    # exceptions are checked against that bound, one by one, and must stay rare.
-    rel = np.abs(vals - ev) / ev
-    bad = np.argwhere(rel > 1e-10)
-    assert len(bad) <= 1e-3 * rel.size, len(bad)
-    ovs = O.overlap(A, prob.part, prob.N, 1)
-    dg = 1.0 / np.sqrt(np.abs(A.diagonal()))
-    for i in sorted(set(int(t) for t in bad[:, 0])):
-        Aii = O.local_matrix(A, ovs[i])
-        s = dg[ovs[i].omega]
-        w = np.linalg.eigvalsh(s[:, None] * Aii * s[None, :])
-        cond = w[-1] / w[0]
-        assert rel[i].max() <= 1e-10 + 16 * np.finfo(float).eps * cond, (i, rel[i].max(), cond)
+    # every value within 1e-10 relative: the FP64 path reports the variational
+    # Rayleigh quotient of eq. uppergevp (overlap 1: lambda = 1 + mu), whose
+    # error is the square of the explicit inverse W = L^{-1}'s (eps cond(A^_ii),
+    # up to 1e-9 here with cond ~ 1e7)
+    np.testing.assert_array_equal(cnt, (ev > 0).sum(axis=1))
+    np.testing.assert_allclose(vals, ev, rtol=1e-10, atol=0)
     x, info = pre.solve(torch.as_tensor(prob.b, device="cuda"))
     rel = np.linalg.norm(prob.b - A @ x.cpu().numpy()) / np.linalg.norm(prob.b)
     assert info.converged and rel <= 1e-8
@@ -406,7 +423,9 @@ def test_c2_full_size_fp32(P):
     # single-precision local work: typical error ~1e-6; subdomains whose top
     # eigenvalue is ~1e5 times the others resolve the rest only to ~1e-2
     assert np.median(err) < 1e-4
-    assert cnt.sum() >= 0.95 * ref["n_C"]
+    # the same kept count as the oracle in every subdomain (its smallest kept
+    # value is 1.4e-6 of its subdomain's largest: above the FP32 cut of 1e-6)
+    np.testing.assert_array_equal(cnt, (ev > 0).sum(axis=1))
     x, info = pre.solve(torch.as_tensor(prob.b, device="cuda"))
     rel = np.linalg.norm(prob.b - A @ x.cpu().numpy()) / np.linalg.norm(prob.b)
     assert info.converged and rel <= 1e-8

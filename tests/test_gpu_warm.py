@@ -167,5 +167,7 @@ def test_training_reduces_loss_and_warm_start_gains():
     sw0, sw1 = np.concatenate(sweeps[0]).mean(), np.concatenate(sweeps[1]).mean()
     r0, r1 = np.median(np.concatenate(resid[0])), np.median(np.concatenate(resid[1]))
     print(f"mean sweeps random {sw0:.2f} warm {sw1:.2f}; median residual after 3 sweeps random {r0:.3e} warm {r1:.3e}")
-    assert sw1 < sw0 and r1 < r0
+    # measured on GB300: mean sweeps 5.98 -> 5.24, median residual after three
+    # sweeps 9.7e-2 -> 2.1e-2; the margins leave room for run-to-run spread
+    assert sw1 <= 0.95 * sw0 and r1 <= 0.5 * r0, (sw0, sw1, r0, r1)
     net.close()
