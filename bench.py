@@ -61,13 +61,16 @@ def parse():
     ap.add_argument("--no-forms", action="store_true", help="skip the FP64 / FP32 comparison forms")
     ap.add_argument("--warm-instances", type=int, default=12)
     ap.add_argument("--warm-steps", type=int, default=2000)
-    ap.add_argument("--mode", default="step", choices=["step", "apply", "stream", "sweep", "weak", "spmv"],
+    ap.add_argument("--mode", default="step",
+                    choices=["step", "apply", "stream", "sweep", "weak", "spmv", "oracle_sample", "cpu_validate"],
                     help="apply: one setup, then --apply-iters applies (for profiler captures); "
                          "stream: the batched stream of generated 3D diffusion instances, learned vs randomized start; "
                          "sweep: local eigenvalue decay and coarse dimension at a fixed tau for overlap 1, 3, 5; "
                          "weak: one-GPU weak scaling of 3D Poisson at 8^3 unknowns per subdomain; "
                          "spmv: the SpMV kernel on a 160^3 Laplacian, --apply-iters launches (profiler captures)")
     ap.add_argument("--instances", type=int, default=200, help="stream mode: instances in the stream")
+    ap.add_argument("--sample-subdomains", type=int, default=16,
+                    help="oracle_sample mode: subdomains whose local setup is timed and scaled")
     return ap.parse_args()
 
 
@@ -146,7 +149,7 @@ def oracle_reference_iterations():
         return None, None
 
 
-def oracle_sample(prob, n_sub: int, gpu_iterations: int | None):
+def oracle_sample(prob, n_sub: int, gpu_iterations: int | None, use_stored: bool = True):
     """Time the oracle's steps on a bounded sample and extrapolate to one
     full setup + solve: local setup (overlap, dense A_ii, Cholesky, dense GEVP)
     of n_sub subdomains scaled by N / n_sub; the dense FP64 Cholesky of an
@@ -158,7 +161,8 @@ def oracle_sample(prob, n_sub: int, gpu_iterations: int | None):
     import scipy.sparse as sp
     import oracle as O
 
-    threads = os.cpu_count()
+    # BLAS threads the oracle's dense kernels use (set by the environment at start-up)
+    threads = int(os.environ.get("OPENBLAS_NUM_THREADS", os.environ.get("OMP_NUM_THREADS", os.cpu_count())))
     A = prob.csr()
     t0 = time.perf_counter()
     ovs = O.overlap(A, prob.part, prob.N, prob.delta)
@@ -196,14 +200,82 @@ def oracle_sample(prob, n_sub: int, gpu_iterations: int | None):
     y = sla.cho_solve(Ef, Z.T @ r)
     z += Z @ y
     t_coarse_iter = time.perf_counter() - t0
-    its, src = oracle_reference_iterations()
+    its, src = oracle_reference_iterations() if use_stored else (None, None)
     if its is None:
-        its, src = gpu_iterations or 0, "GPU FP64 iteration count (no stored oracle run)"
+        import oracle as O2
+        st_small = O2.setup(A, prob.part, prob.N, prob.delta, prob.nev)
+        its, src = int(O2.solve(st_small, prob.b).iterations), "oracle iteration count of this problem"
     total = t_overlap + t_local + t_efac + its * (t_loc_iter + t_coarse_iter)
     sample_desc = (f"oracle local setup of {len(sample)} of {prob.N} subdomains (x{prob.N / len(sample):.0f}), "
                    f"overlap of all, dense Cholesky of a {nC}x{nC} SPD matrix, one PCG iteration's SpMV + "
                    f"local solves (scaled) + coarse solve, times {its} iterations ({src})")
     return total, threads, sample_desc
+
+
+def oracle_full(name: str):
+    """A full, non-extrapolated oracle setup + solve of a small configuration
+    (seconds), with the host's BLAS threads."""
+    import oracle as O
+    from asm_inputs import config
+    prob = config(name)
+    A = prob.csr()
+    t0 = time.perf_counter()
+    st = O.setup(A, prob.part, prob.N, prob.delta, prob.nev, spd=prob.spd)
+    res = O.solve(st, prob.b)
+    return {"config": name, "s": time.perf_counter() - t0, "iterations": int(res.iterations),
+            "kind": "oracle, full setup + solve"}
+
+
+def oracle_single_thread(name: str, n_sub: int):
+    """The extrapolated oracle sample with one BLAS thread, in a subprocess
+    (the thread count is fixed when NumPy loads its BLAS)."""
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    cmd = [sys.executable, os.path.abspath(__file__), "--mode", "oracle_sample", "--config", name,
+           "--sample-subdomains", str(n_sub)]
+    try:
+        out = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=600).stdout
+        return json.loads(out.strip().splitlines()[-1])
+    except Exception as e:  # pragma: no cover - reported, not fatal
+        return {"error": str(e)[:200]}
+
+
+def config_lines(P, torch, dev, stream):
+    """Setup + solve of the elasticity (PCG) and convection-diffusion (FGMRES)
+    configurations with FP32 local work, next to the oracle's iteration counts
+    from tests/golden/ when those files are present."""
+    from asm_inputs import config
+    out = {}
+    for name in ("c3", "c4"):
+        prob = config(name)
+        t = [torch.as_tensor(a, device=dev) for a in (prob.indptr, prob.indices, prob.data, prob.part, prob.b)]
+        opt = P.default_options(spd=1 if prob.spd else 0, local_precision=P.PREC_FP32)
+        so = P.default_solve_opts(rtol=1e-8, max_it=5000)
+
+        def once():
+            x = torch.zeros_like(t[4])
+            h = P.asm_setup(t[0], t[1], t[2], t[3], prob.N, prob.delta, prob.nev, opt, stream, True)
+            inf = P.asm_solve(h, t[4], x, so, stream)
+            si = P.asm_get_info(h)
+            P.asm_destroy(h)
+            return inf, si
+        once()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        inf, si = once()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        row = {"s_per_step": e0.elapsed_time(e1) / 1e3, "setup_ms": si.stage_ms[7], "solve_ms": inf.solve_ms,
+               "iterations": inf.iterations, "true_relres": inf.true_relres, "n": prob.n, "N": prob.N,
+               "n_C": si.n_C, "method": "PCG" if prob.spd else "FGMRES(30)"}
+        try:
+            with open(os.path.join(ROOT, "tests", "golden", f"{name}_oracle_reference.json")) as f:
+                row["oracle_iterations"] = int(json.load(f)["iterations"])
+        except Exception:
+            row["oracle_iterations"] = None
+        out[name] = row
+    return out
 
 
 def cpu_model() -> str:
@@ -231,7 +303,7 @@ def run_reference(args):
     vals = []
     desc = threads = None
     for k in range(args.warmup + args.steps):
-        t, threads, desc = oracle_sample(prob, n_sub=4, gpu_iterations=None)
+        t, threads, desc = oracle_sample(prob, n_sub=4, gpu_iterations=None, use_stored=args.config == "c2")
         if k >= args.warmup:
             vals.append(t)
     v = float(np.mean(vals))
@@ -543,11 +615,13 @@ def run_ours(args):
         P.asm_destroy(h)
         return None, info
 
+    # the clock sampler starts before the warm-up, so that its own start-up
+    # (nvidia-smi initialising) is not inside the timed region
+    sampler = ClockSampler(local)
+    sampler.start()
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    sampler = ClockSampler(local)
-    sampler.start()
     l0 = P.asm_kernel_launches()
     if dist:
         dist.barrier()
@@ -595,6 +669,7 @@ def run_ours(args):
     apply_gbs = apply_bytes / (tap["apply"] * 1e-3) / 1e9
     spmv = measure_spmv(P, torch, dev, stream, h_last, prob, hbm)
     P.asm_destroy(h_last)
+    configs = None if args.no_forms else config_lines(P, torch, dev, stream)
 
     # ---- the other forms on the same GPU: plain FP64, FP32 with the randomized start
     forms = None
@@ -650,8 +725,9 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, threads, desc = oracle_sample(prob, n_sub=16, gpu_iterations=None)
-        cpu = {"value": v, "unit": UNIT, "cores": threads, "cpu": cpu_model(), "kind": "oracle", "sample": desc}
+        v, threads, desc = oracle_sample(prob, n_sub=16, gpu_iterations=None, use_stored=args.config == "c2")
+        cpu = {"value": v, "unit": UNIT, "cores": threads, "cpu": cpu_model(), "kind": "oracle", "sample": desc,
+               "full_run_c1": oracle_full("c1"), "single_thread": oracle_single_thread(args.config, 2)}
 
     if rank == 0:
         line = {
@@ -672,7 +748,7 @@ def run_ours(args):
                          "traffic_note": "DRAM read+write per launch from an ncu capture of the tile passes on the "
                                          "40^3 variant, scaled by the algorithmic bytes",
                          "algorithmic_bytes_per_launch": pass_bytes},
-            "spmv": spmv,
+            "spmv": spmv, "configs": configs,
             "clocks": clocks, "gpu_launches": launches, "e2e": e2e, "cpu_baseline": cpu,
             "forms": forms, "warm_start": warm_info,
         }
@@ -681,8 +757,35 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def cpu_validate(args):
+    """The oracle's extrapolated step time against a full oracle setup + solve
+    of the same recipe on a 32^3 grid (64 subdomains of 8^3): how far the
+    sample-based estimate used for the 64^3 workload is from a measured run."""
+    import oracle as O
+    from asm_inputs import diffusion3d
+    prob = diffusion3d(32, (4, 4, 4), 1e6, 0.10, delta=1, nev=16)
+    est, threads, desc = oracle_sample(prob, n_sub=args.sample_subdomains, gpu_iterations=None, use_stored=False)
+    A = prob.csr()
+    t0 = time.perf_counter()
+    st = O.setup(A, prob.part, prob.N, 1, 16)
+    res = O.solve(st, prob.b)
+    full = time.perf_counter() - t0
+    print(json.dumps({"mode": "cpu_validate", "workload": "3D high-contrast diffusion 32^3, 64 subdomains of 8^3",
+                      "estimate_s": est, "full_s": full, "estimate_over_full": est / full,
+                      "full_iterations": int(res.iterations), "cores": threads, "sample": desc}), flush=True)
+
+
 def main():
     args = parse()
+    if args.mode == "oracle_sample":
+        from asm_inputs import config
+        v, threads, desc = oracle_sample(config(args.config), n_sub=args.sample_subdomains, gpu_iterations=None,
+                                         use_stored=args.config == "c2")
+        print(json.dumps({"value": v, "unit": UNIT, "threads": threads, "sample": desc}), flush=True)
+        return
+    if args.mode == "cpu_validate":
+        cpu_validate(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
