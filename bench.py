@@ -36,11 +36,11 @@ import numpy as np  # noqa: E402
 
 METRIC = "setup+solve s to 1e-8 rel resid; apply GB/s; mixed/learned vs FP64 same GPU"
 # DRAM bytes (read + write) of the tile pass per algorithmic byte, measured by
-# ncu on the 40^3 variant of the workload (125 subdomains, 169 MB algorithmic,
-# 187 MB moved: the stored tiles include the full diagonal tiles, plus the
-# vector reads and the row-part and column-slot writes); the pass moves bytes
-# in proportion to its tiles.
-TILE_PASS_TRAFFIC_RATIO = 1.11
+# ncu on the 40^3 variant of the workload (125 subdomains, 168.7 MB algorithmic,
+# 188.9 MB moved: the stored tiles include the full diagonal tiles, plus the
+# vector reads and the row-part and column-slot writes; profiles/
+# k_tile_pass_cf_c2-40_fp32.md); the pass moves bytes in proportion to its tiles.
+TILE_PASS_TRAFFIC_RATIO = 1.12
 UNIT = "s"
 WORKLOAD = ("3D 7-point high-contrast diffusion 64^3 (n=262144, contrast 1e6 channels/inclusions 10%), "
             "512 subdomains 8^3, overlap 1, nev 16")
