@@ -211,6 +211,36 @@ asm_status asm_spmv(asm_handle* h, const double* x, double* y, void* stream);
 asm_status asm_csr_spmv(int32_t n, int32_t nnz, const int32_t* row_ptr, const int32_t* col_idx,
                         const double* val, const double* x, double* y, void* stream);
 
+/* Batched 64 x 64 single-precision tile products on the tensor cores, the
+ * building block of the local factorisation's single-precision path (the
+ * blocked Cholesky, triangular inverse and W^T W of Section 2.3's local
+ * solves, by levels): for every job,
+ *   C = alpha sum_{t < nprod} op(A_t) op(B_t)^T (+ C_in),  alpha = -1 with
+ *   ASM_TILE_NEG, else +1,
+ * where A_t is the 64 x 64 tile at a + a0 + t a_step (row stride lda) and
+ * op(A_t)(m, k) = A_t[m][k], or A_t[k][m] with ASM_TILE_AT (B likewise with
+ * ASM_TILE_BT; the product contracts over k), C_in the tile at cin + c_in
+ * (stride ldc_in, ASM_TILE_BETA), C written at cout + c_out (stride ldc_out).
+ * Offsets and strides are in elements (FP32); every row start must be 16-byte
+ * aligned (offsets and strides multiples of 4).  Products use the 3xTF32
+ * split (single-precision accuracy) with FP32 accumulation.  The jobs of one
+ * call must be independent (no job reads a tile another job writes); a job's
+ * output may be one of its own operands.  jobs: host array (copied); a, b,
+ * cin, cout: device.  Errors: INVALID_ARG (null pointer, nprod < 1,
+ * misaligned offset or stride), TIMEOUT, CUDA. */
+typedef struct asm_tile_job {
+  int64_t a0, b0, a_step, b_step;
+  int64_t c_in, c_out;
+  int32_t lda, ldb, ldc_in, ldc_out;
+  int32_t nprod;
+  int32_t flags;   /* ASM_TILE_* */
+  int32_t sub;     /* unused here (0) */
+  int32_t unused;
+} asm_tile_job;
+enum { ASM_TILE_AT = 1, ASM_TILE_BT = 2, ASM_TILE_BETA = 4, ASM_TILE_NEG = 8 };
+asm_status asm_tile_products(const asm_tile_job* jobs, int64_t njobs, const float* a, const float* b,
+                             const float* cin, float* cout, void* stream);
+
 asm_status asm_get_info(const asm_handle* h, asm_setup_info* info);
 
 /* Measurement helpers (no counterpart in the paper; used by the benchmark).

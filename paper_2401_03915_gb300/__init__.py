@@ -103,6 +103,8 @@ def load(path: str | None = None) -> C.CDLL:
     L.asm_spmv_dot_noalloc.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp]
     L.asm_spmv_dot_noalloc.restype = C.c_int
     i64, f32 = C.c_int64, C.c_float
+    L.asm_tile_products.argtypes = [vp, i64, vp, vp, vp, vp, vp]
+    L.asm_tile_products.restype = C.c_int
     L.asm_mlp_create.argtypes = [i32, i32, C.c_uint64, pp]
     L.asm_mlp_destroy.argtypes = [vp]
     L.asm_mlp_destroy.restype = None
@@ -287,6 +289,29 @@ def asm_csr_spmv(row_ptr, col_idx, val, x, y, stream=None) -> None:
         raise ValueError("sizes: row_ptr n + 1, y n, col_idx and val alike")
     _check(load().asm_csr_spmv(n, int(val.numel()), _ptr(row_ptr), _ptr(col_idx), _ptr(val), _ptr(x), _ptr(y),
                                _stream(stream)))
+
+
+TILE_AT, TILE_BT, TILE_BETA, TILE_NEG = 1, 2, 4, 8
+# mirrors asm_tile_job (include/asm.h)
+TILE_JOB_DTYPE = [("a0", "<i8"), ("b0", "<i8"), ("a_step", "<i8"), ("b_step", "<i8"), ("c_in", "<i8"),
+                  ("c_out", "<i8"), ("lda", "<i4"), ("ldb", "<i4"), ("ldc_in", "<i4"), ("ldc_out", "<i4"),
+                  ("nprod", "<i4"), ("flags", "<i4"), ("sub", "<i4"), ("unused", "<i4")]
+
+
+def asm_tile_products(jobs, a, b, cin, cout, stream=None) -> None:
+    """Batched 64 x 64 tile products on the tensor cores (asm_tile_products):
+    jobs is a NumPy array of TILE_JOB_DTYPE records; a, b, cin (or None) and
+    cout contiguous float32 CUDA tensors, offsets in elements."""
+    import numpy as np
+    import torch
+    jobs = np.ascontiguousarray(np.asarray(jobs, dtype=TILE_JOB_DTYPE))
+    for name, t in (("a", a), ("b", b), ("cin", cin), ("cout", cout)):
+        if t is None and name == "cin":
+            continue
+        if not isinstance(t, torch.Tensor) or t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous():
+            raise TypeError(f"{name} must be a contiguous CUDA tensor of float32")
+    _check(load().asm_tile_products(jobs.ctypes.data, len(jobs), _ptr(a), _ptr(b),
+                                    _ptr(cin) if cin is not None else None, _ptr(cout), _stream(stream)))
 
 
 def asm_time_spmv(h: int, p, q, iters: int = 100, stream=None) -> float:

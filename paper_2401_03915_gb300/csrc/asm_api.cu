@@ -4,6 +4,7 @@
 #include <new>
 
 #include "handle.cuh"
+#include "tcgemm.cuh"
 
 using namespace asmgpu;
 
@@ -341,6 +342,44 @@ asm_status asm_time_spmv(asm_handle* H, const double* p, double* q, int32_t iter
   if (!H || !p || !q || !ms || iters < 1) return set_error(ASM_ERR_INVALID_ARG, "null argument or iters < 1");
   if (p == q) return set_error(ASM_ERR_INVALID_ARG, "p and q must not alias");
   return guarded([&] { time_pcg_spmv(H->h, p, q, iters, static_cast<cudaStream_t>(stream), ms); });
+}
+
+asm_status asm_tile_products(const asm_tile_job* jobs, int64_t njobs, const float* a, const float* b,
+                             const float* cin, float* cout, void* stream) {
+  static_assert(sizeof(asm_tile_job) == sizeof(TcJob), "asm_tile_job must mirror TcJob");
+  if (njobs < 0 || (njobs > 0 && (!jobs || !a || !b || !cout)))
+    return set_error(ASM_ERR_INVALID_ARG, "asm_tile_products: null pointer or negative count");
+  for (int64_t k = 0; k < njobs; ++k) {
+    const asm_tile_job& j = jobs[k];
+    const bool beta = (j.flags & ASM_TILE_BETA) != 0;
+    if (j.nprod < 1 || (j.flags & ~15) || (beta && !cin))
+      return set_error(ASM_ERR_INVALID_ARG, "asm_tile_products: nprod < 1, unknown flag or missing C_in");
+    const int64_t al[] = {j.a0, j.b0, j.a_step, j.b_step, j.c_in, j.c_out, j.lda, j.ldb, j.ldc_in, j.ldc_out};
+    for (int64_t v : al)
+      if (v % 4 != 0) return set_error(ASM_ERR_INVALID_ARG, "asm_tile_products: offsets and strides must be multiples of 4");
+    if (j.lda < 64 || j.ldb < 64 || j.ldc_out < 64 || (beta && j.ldc_in < 64))
+      return set_error(ASM_ERR_INVALID_ARG, "asm_tile_products: a row stride below 64");
+  }
+  return guarded([&] {
+    if (njobs == 0) return;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    TcJob* d = nullptr;
+    int32_t* err = nullptr;
+    CK(cudaMallocAsync(&d, sizeof(TcJob) * njobs, s));
+    CK(cudaMallocAsync(&err, sizeof(int32_t), s));
+    CK(cudaMemsetAsync(err, 0, sizeof(int32_t), s));
+    CK(cudaMemcpyAsync(d, jobs, sizeof(TcJob) * njobs, cudaMemcpyHostToDevice, s));
+    int dev = 0, sms = 152;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    tc_tiles(d, njobs, a, b, cin, cout, nullptr, err, sms, s);
+    int32_t e = 0;
+    CK(cudaMemcpyAsync(&e, err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaFreeAsync(d, s));
+    CK(cudaFreeAsync(err, s));
+    CK(cudaStreamSynchronize(s));
+    if (e & DERR_TIMEOUT) fail(ASM_ERR_TIMEOUT, "asm_tile_products: a bounded device wait gave up");
+  });
 }
 
 asm_status asm_get_info(const asm_handle* H, asm_setup_info* info) {

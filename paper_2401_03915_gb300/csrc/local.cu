@@ -1,8 +1,9 @@
 // Local dense stage: gather A_ii out of CSR A (Section 2.3), factor it, and
 // pack the result into the tiles the apply streams.
 //
-// SPD A: blocked Cholesky and triangular inverse W = L^{-1} (k_chol_trtri);
-// the apply multiplies by W^T W and the eigen stage reads the block
+// SPD A: blocked Cholesky and triangular inverse W = L^{-1} (FP64: k_chol_trtri;
+// single precision: factor_spd_levels, tensor-core tile jobs by levels); the apply
+// multiplies by W^T W and the eigen stage reads the block
 // W[Gamma_delta, I_i].  General A: blocked Gauss-Jordan sweep (k_sweep).
 //
 // What is gathered is the symmetrically scaled A^_ii = D^{-1/2} A_ii D^{-1/2},
@@ -25,6 +26,7 @@
 #include <cuda_fp16.h>
 
 #include "handle.cuh"
+#include "tcgemm.cuh"
 
 namespace asmgpu {
 namespace {
@@ -227,40 +229,22 @@ __global__ void __launch_bounds__(NT) k_sweep(T* __restrict__ work, const int64_
   }
 }
 
-// SPD local factor: blocked Cholesky A^_ii = L L^T (right-looking) followed by
-// the blocked triangular inverse W = L^{-1}, both in place in the lower
-// triangle, one block per subdomain, 64 x 64 blocks.  The apply multiplies by
-// W^T W = A^_ii^{-1}: symmetric positive definite for any rounding of W, and
-// accurate to about cond(A^_ii) * eps (an explicitly inverted A^_ii^{-1} would
-// only be accurate to cond^2 * eps).  Dinv receives the inverses of the
-// diagonal blocks of L (which are the diagonal blocks of W).
+// SPD local factor in FP64: blocked Cholesky A^_ii = L L^T (right-looking)
+// followed by the blocked triangular inverse W = L^{-1}, both in place in the
+// lower triangle, one block per subdomain, 64 x 64 blocks.  The apply
+// multiplies by W^T W = A^_ii^{-1}: symmetric positive definite for any
+// rounding of W, and accurate to about cond(A^_ii) * eps (an explicitly
+// inverted A^_ii^{-1} would only be accurate to cond^2 * eps).  Dinv receives
+// the inverses of the diagonal blocks of L (which are the diagonal blocks of
+// W).  The single-precision factor runs the same steps by levels of tile
+// products on the tensor cores (factor_spd_levels below).
 // 64 x 64 x 64 block products acc (+)= Am * (btrans ? Bm^T : Bm) from shared
-// memory ([64][65] layout), behind one interface for both precisions.
-//  FP64: CUDA-core FMAs, thread (tx, ty) owns rows ty + 16a, columns tx + 16b.
-//  FP32: tensor cores, mma.sync m16n8k8 TF32 with the 3xTF32 split
-//        (a = a_hi + a_lo, products a_hi b_hi + a_hi b_lo + a_lo b_hi, FP32
-//        accumulation), which keeps single-precision accuracy; warp w owns
-//        rows 16 (w % 4) .. +15 and columns 32 (w / 4) .. +31.
+// memory ([64][65] layout) on CUDA-core FMAs, thread (tx, ty) owning rows
+// ty + 16a, columns tx + 16b.
 template <typename T>
 struct BlockAcc {
   T v[4][4];
 };
-
-__device__ __forceinline__ uint32_t to_tf32(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return r;
-}
-__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
-  hi = to_tf32(x);
-  lo = to_tf32(x - __uint_as_float(hi));
-}
-__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
 
 template <typename T>
 __device__ __forceinline__ void acc_zero(BlockAcc<T>& acc) {
@@ -286,33 +270,6 @@ __device__ __forceinline__ void acc_mma(BlockAcc<double>& acc, const double (*Am
   }
 }
 
-__device__ __forceinline__ void acc_mma(BlockAcc<float>& acc, const float (*Am)[TILE + 1],
-                                        const float (*Bm)[TILE + 1], bool btrans) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int g = lane >> 2, t = lane & 3;
-  const int r0 = 16 * (w & 3), c0 = 32 * (w >> 2);
-#pragma unroll 2
-  for (int k0 = 0; k0 < TILE; k0 += 8) {
-    uint32_t ah[4], al[4];
-    split_tf32(Am[r0 + g][k0 + t], ah[0], al[0]);
-    split_tf32(Am[r0 + g + 8][k0 + t], ah[1], al[1]);
-    split_tf32(Am[r0 + g][k0 + t + 4], ah[2], al[2]);
-    split_tf32(Am[r0 + g + 8][k0 + t + 4], ah[3], al[3]);
-#pragma unroll
-    for (int nt = 0; nt < 4; ++nt) {
-      const int n = c0 + 8 * nt + g;
-      const float x0 = btrans ? Bm[n][k0 + t] : Bm[k0 + t][n];
-      const float x1 = btrans ? Bm[n][k0 + t + 4] : Bm[k0 + t + 4][n];
-      uint32_t bh0, bl0, bh1, bl1;
-      split_tf32(x0, bh0, bl0);
-      split_tf32(x1, bh1, bl1);
-      mma_tf32(acc.v[nt], al, bh0, bh1);
-      mma_tf32(acc.v[nt], ah, bl0, bl1);
-      mma_tf32(acc.v[nt], ah, bh0, bh1);
-    }
-  }
-}
-
 // f(row, col, value) for every element of the thread's share of the block
 template <typename F>
 __device__ __forceinline__ void acc_for_each(const BlockAcc<double>& acc, F&& f) {
@@ -322,17 +279,6 @@ __device__ __forceinline__ void acc_for_each(const BlockAcc<double>& acc, F&& f)
 #pragma unroll
     for (int b = 0; b < 4; ++b) f(ty + 16 * a, tx + 16 * b, acc.v[a][b]);
 }
-template <typename F>
-__device__ __forceinline__ void acc_for_each(const BlockAcc<float>& acc, F&& f) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int g = lane >> 2, t = lane & 3;
-  const int r0 = 16 * (w & 3), c0 = 32 * (w >> 2);
-#pragma unroll
-  for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-    for (int q = 0; q < 4; ++q) f(r0 + g + (q >= 2 ? 8 : 0), c0 + 8 * nt + 2 * t + (q & 1), acc.v[nt][q]);
-}
-
 template <typename T>
 __global__ void __launch_bounds__(NT) k_chol_trtri(T* __restrict__ work, const int64_t* __restrict__ work_off,
                                                    const int32_t* __restrict__ np_arr,
@@ -489,50 +435,224 @@ __global__ void __launch_bounds__(NT) k_chol_trtri(T* __restrict__ work, const i
       });
     }
   }
-  // The pivot ratio max/min of the Cholesky bounds cond(A^_ii) from below;
-  // within sym_max_ratio the subdomain gets the explicit inverse S = W^T W
-  // (k_lauum); past it, it keeps the two-pass W^T W form, which stays SPD
-  // whatever the rounding (an explicit FP32 inverse would not).
+  // The pivot ratio max/min of the Cholesky bounds cond(A^_ii) from below
+  // (a positive ratio asks for the explicit-inverse decision; FP64 passes 0).
   if (tid == 0) sym[i] = (sym_max_ratio > 0 && piv_max <= sym_max_ratio * piv_min) ? 1 : 0;
 }
 
-// S = W^T W for the subdomains flagged in sym, one block per lower tile:
-// S_IJ = sum_{K >= I} W_KI^T W_KJ from the W left in the working matrix,
-// written to the apply tile of (I, J).  Many small independent blocks hide
-// the tile loads that bound a one-block-per-subdomain loop.
-template <typename T>
-__global__ void __launch_bounds__(NT) k_lauum(const T* __restrict__ work, const int64_t* __restrict__ work_off,
-                                              const int32_t* __restrict__ np_arr, const int32_t* __restrict__ n_arr,
-                                              const int4* __restrict__ desc, int64_t ntiles,
-                                              const int8_t* __restrict__ sym, T* __restrict__ tiles) {
+// ---------------------------------------------------------------------------
+// Single-precision SPD factor by levels.  Level kb of the Cholesky:
+//   (1) C_rk = A_rk - sum_{j<kb} L_rj L_kj^T for every row block r >= kb
+//       (tile jobs, one per (subdomain, r));
+//   (2) the 64 x 64 diagonal block: C_kk = L_kk L_kk^T and Dinv_kk = L_kk^{-1}
+//       (k_diag_chol, one block per subdomain);
+//   (3) L_rk = C_rk Dinv_kk^T for r > kb (tile jobs).
+// Then W = L^{-1} by row levels i: T_ij = sum_{k=j}^{i-1} L_ik W_kj for every
+// j < i, W_ij = -Dinv_i T_ij (W_jj = Dinv_j), and for the subdomains that get
+// the explicit inverse, S_IJ = sum_{K >= I} W_KI^T W_KJ.  Every step but (2)
+// is a batch of 64 x 64 tile products on the tensor cores (tcgemm.cu).  L_kk
+// itself is never read again: the diagonal tile of the working matrix
+// receives W_kk = Dinv_kk (lower triangle, zero above and in the padding).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(NT) k_diag_chol(int kb, const int32_t* __restrict__ subs, float* __restrict__ work,
+                                                  const int64_t* __restrict__ work_off,
+                                                  const int32_t* __restrict__ np_arr, const int32_t* __restrict__ n_arr,
+                                                  float* __restrict__ dinv_all, const int64_t* __restrict__ dinv_off,
+                                                  double* __restrict__ piv_lo, double* __restrict__ piv_hi,
+                                                  int32_t* err) {
   COUNT_LAUNCH();
-  __shared__ T Xm[TILE][TILE + 1];
-  __shared__ T Ym[TILE][TILE + 1];
+  __shared__ float Dm[TILE][TILE + 1];
+  __shared__ float Xm[TILE][TILE + 1];
+  __shared__ int bad;
+  __shared__ double pmin, pmax;
+  const int i = subs[blockIdx.x];
+  const int n = n_arr[i], ld = np_arr[i];
+  const int kw = min(TILE, n - kb * TILE);
+  float* B = work + work_off[i] + (int64_t)kb * TILE * ld + kb * TILE;
   const int tid = threadIdx.x;
-  for (int64_t tt = blockIdx.x; tt < ntiles; tt += gridDim.x) {
-    const int4 d = desc[tt];
-    const int i = d.x, I = d.y, J = d.z;
-    if (!sym[i]) continue;
-    const int n = n_arr[i], ld = np_arr[i], nt = (n + TILE - 1) / TILE;
-    const T* M = work + work_off[i];
-    BlockAcc<T> acc;
-    acc_zero(acc);
-    for (int K = I; K < nt; ++K) {
-      __syncthreads();
-      const T* BI = M + (int64_t)K * TILE * ld + I * TILE;
-      const T* BJ = M + (int64_t)K * TILE * ld + J * TILE;
-      const int kw = min(TILE, n - K * TILE);
-      for (int idx = tid; idx < TILE * TILE; idx += NT) {
-        const int q = idx / TILE, r = idx % TILE;
-        const bool in = q < kw;
-        Ym[r][q] = (in && I * TILE + r < n) ? BI[(int64_t)q * ld + r] : T(0);  // W_KI^T
-        Xm[q][r] = (in && J * TILE + r < n) ? BJ[(int64_t)q * ld + r] : T(0);  // W_KJ
-      }
-      __syncthreads();
-      acc_mma(acc, Ym, Xm, false);
+  if (tid == 0) {
+    bad = 0;
+    pmin = kb == 0 ? 3.0e300 : piv_lo[i];
+    pmax = kb == 0 ? 0.0 : piv_hi[i];
+  }
+  for (int idx = tid; idx < TILE * TILE; idx += NT) {
+    const int r = idx / TILE, c = idx % TILE;
+    Dm[r][c] = (r < kw && c < kw) ? B[(int64_t)max(r, c) * ld + min(r, c)] : (r == c ? 1.f : 0.f);
+  }
+  __syncthreads();
+  for (int j = 0; j < TILE; ++j) {
+    if (tid == 0) {
+      float d = Dm[j][j];
+      if (!(d > 0.f) || !isfinite(d)) { bad = 1; d = 1.f; }
+      if (j < kw) { pmin = fmin(pmin, (double)d); pmax = fmax(pmax, (double)d); }
+      Dm[j][j] = sqrtf(d);
     }
-    T* o = tiles + tt * (TILE * TILE);
-    acc_for_each(acc, [&](int r, int c, T v) { o[r * TILE + c] = v; });
+    __syncthreads();
+    for (int r = j + 1 + tid; r < TILE; r += NT) Dm[r][j] /= Dm[j][j];
+    __syncthreads();
+    for (int idx = tid; idx < TILE * TILE; idx += NT) {
+      const int r = idx / TILE, c = idx % TILE;
+      if (c > j && r >= c) Dm[r][c] -= Dm[r][j] * Dm[c][j];
+    }
+    __syncthreads();
+  }
+  // inverse of the lower diagonal block (column c by thread c)
+  if (tid < TILE) {
+    const int c = tid;
+    for (int r = 0; r < c; ++r) Xm[r][c] = 0.f;
+    for (int r = c; r < TILE; ++r) {
+      float v = r == c ? 1.f : 0.f;
+      for (int t = c; t < r; ++t) v -= Dm[r][t] * Xm[t][c];
+      Xm[r][c] = v / Dm[r][r];
+    }
+  }
+  __syncthreads();
+  float* Dv = dinv_all + dinv_off[i] + (int64_t)kb * TILE * TILE;
+  for (int idx = tid; idx < TILE * TILE; idx += NT) {
+    const int r = idx / TILE, c = idx % TILE;
+    Dv[idx] = Xm[r][c];
+    B[(int64_t)r * ld + c] = (r < kw && c < kw && c <= r) ? Xm[r][c] : 0.f;
+  }
+  if (tid == 0) {
+    if (bad) atomicOr(err, DERR_NOT_SPD);
+    piv_lo[i] = pmin;
+    piv_hi[i] = pmax;
+  }
+}
+
+// The pivot ratio max/min of the Cholesky bounds cond(A^_ii) from below;
+// within ratio the subdomain gets the explicit inverse S = W^T W; past it, it
+// keeps the two-pass W^T W form, which stays SPD whatever the rounding (an
+// explicit FP32 inverse would not).
+__global__ void k_sym_decide(int N, const double* __restrict__ piv_lo, const double* __restrict__ piv_hi,
+                             double ratio, int8_t* __restrict__ sym) {
+  COUNT_LAUNCH();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) sym[i] = (ratio > 0 && piv_hi[i] <= ratio * piv_lo[i]) ? 1 : 0;
+}
+
+void factor_spd_levels(Handle& h, float* work, const int32_t* d_n, double ratio, cudaStream_t s) {
+  const int N = h.N;
+  Dense& dn = h.dn;
+  DevMem& mem = h.mem;
+  const int64_t T2 = (int64_t)TILE * TILE;
+  int ntmax = 0;
+  for (int i = 0; i < N; ++i) ntmax = std::max(ntmax, dn.h_nt[i]);
+  // one launch of tile jobs: [first, first + count) of the job array and the
+  // bases it reads and writes (0 work, 1 dinv, 2 scratch, 3 apply tiles)
+  struct Step {
+    int kind;  // 0 tile jobs, 1 diagonal blocks of level kb, 2 explicit-inverse decision
+    int64_t first, count;
+    int a, b, c, kb;
+  };
+  std::vector<TcJob> jobs;
+  std::vector<int32_t> subs;
+  std::vector<Step> steps;
+  auto tile_at = [&](int i, int r, int c) { return dn.h_work_off[i] + (int64_t)r * TILE * dn.h_np[i] + c * TILE; };
+  auto job = [&](int64_t a0, int64_t a_step, int lda, int64_t b0, int64_t b_step, int ldb, int64_t c0, int ldc,
+                 int nprod, int flags, int sub) {
+    TcJob J{};
+    J.a0 = a0; J.a_step = a_step; J.lda = lda;
+    J.b0 = b0; J.b_step = b_step; J.ldb = ldb;
+    J.c_in = c0; J.c_out = c0; J.ldc_in = ldc; J.ldc_out = ldc;
+    J.nprod = nprod; J.flags = flags; J.sub = sub;
+    jobs.push_back(J);
+  };
+  auto close = [&](int64_t first, int a, int b, int c) {
+    if ((int64_t)jobs.size() > first) steps.push_back({0, first, (int64_t)jobs.size() - first, a, b, c, 0});
+  };
+  // Cholesky levels
+  for (int kb = 0; kb < ntmax; ++kb) {
+    int64_t f = (int64_t)jobs.size();
+    if (kb > 0) {
+      for (int i = 0; i < N; ++i) {
+        const int nt = dn.h_nt[i], ld = dn.h_np[i];
+        if (nt <= kb) continue;
+        for (int r = kb; r < nt; ++r)
+          job(tile_at(i, r, 0), TILE, ld, tile_at(i, kb, 0), TILE, ld, tile_at(i, r, kb), ld, kb,
+              TCF_NEG | TCF_BETA, i);
+      }
+      close(f, 0, 0, 0);
+    }
+    const int64_t s0 = (int64_t)subs.size();
+    for (int i = 0; i < N; ++i)
+      if (dn.h_nt[i] > kb) subs.push_back(i);
+    steps.push_back({1, s0, (int64_t)subs.size() - s0, 0, 0, 0, kb});
+    f = (int64_t)jobs.size();
+    for (int i = 0; i < N; ++i) {
+      const int nt = dn.h_nt[i], ld = dn.h_np[i];
+      for (int r = kb + 1; r < nt; ++r)
+        job(tile_at(i, r, kb), 0, ld, dn.h_s_off[i] + kb * T2, 0, TILE, tile_at(i, r, kb), ld, 1, 0, i);
+    }
+    close(f, 0, 1, 0);
+  }
+  // the pivots are known: the explicit-inverse decision (read by the W^T W jobs)
+  steps.push_back({2, 0, 0, 0, 0, 0, 0});
+  // triangular inverse by row levels; T_ij in the scratch, then W_ij
+  int64_t scratch_tiles = 0;
+  for (int il = 1; il < ntmax; ++il) {
+    const int64_t f = (int64_t)jobs.size();
+    int64_t q = 0;
+    for (int i = 0; i < N; ++i) {
+      const int ld = dn.h_np[i];
+      if (dn.h_nt[i] <= il) continue;
+      for (int j = 0; j < il; ++j, ++q)
+        job(tile_at(i, il, j), TILE, ld, tile_at(i, j, j), (int64_t)TILE * ld, ld, q * T2, TILE, il - j, TCF_BT, i);
+    }
+    close(f, 0, 0, 2);
+    scratch_tiles = std::max(scratch_tiles, q);
+    const int64_t g = (int64_t)jobs.size();
+    q = 0;
+    for (int i = 0; i < N; ++i) {
+      const int ld = dn.h_np[i];
+      if (dn.h_nt[i] <= il) continue;
+      for (int j = 0; j < il; ++j, ++q) {
+        TcJob J{};
+        J.a0 = dn.h_s_off[i] + il * T2; J.lda = TILE;
+        J.b0 = q * T2; J.ldb = TILE;
+        J.c_out = tile_at(i, il, j); J.ldc_out = ld; J.ldc_in = ld;
+        J.nprod = 1; J.flags = TCF_BT | TCF_NEG; J.sub = i;
+        jobs.push_back(J);
+      }
+    }
+    close(g, 1, 2, 0);
+  }
+  // S = W^T W for the explicit-inverse subdomains, into the apply tiles
+  {
+    const int64_t f = (int64_t)jobs.size();
+    for (int i = 0; i < N; ++i) {
+      const int nt = dn.h_nt[i], ld = dn.h_np[i];
+      for (int I = 0; I < nt; ++I)
+        for (int J = 0; J <= I; ++J) {
+          TcJob Jb{};
+          Jb.a0 = tile_at(i, I, I); Jb.a_step = (int64_t)TILE * ld; Jb.lda = ld;
+          Jb.b0 = tile_at(i, I, J); Jb.b_step = (int64_t)TILE * ld; Jb.ldb = ld;
+          Jb.c_out = (dn.h_tile_off[i] + (int64_t)I * (I + 1) / 2 + J) * T2; Jb.ldc_out = TILE; Jb.ldc_in = TILE;
+          Jb.nprod = nt - I; Jb.flags = TCF_AT | TCF_BT | TCF_SYMONLY; Jb.sub = i;
+          jobs.push_back(Jb);
+        }
+    }
+    close(f, 0, 0, 3);
+  }
+  TcJob* d_jobs = mem.alloc<TcJob>(std::max<size_t>(jobs.size(), 1));
+  int32_t* d_subs = mem.alloc<int32_t>(std::max<size_t>(subs.size(), 1));
+  float* scratch = mem.alloc<float>(std::max<int64_t>(scratch_tiles, 1) * T2);
+  double* piv = mem.alloc<double>(2 * N);
+  if (!jobs.empty()) CK(cudaMemcpyAsync(d_jobs, jobs.data(), sizeof(TcJob) * jobs.size(), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(d_subs, subs.data(), sizeof(int32_t) * subs.size(), cudaMemcpyHostToDevice, s));
+  float* bases[4] = {work, (float*)dn.dinv, scratch, (float*)dn.tiles};
+  for (const Step& st : steps) {
+    if (st.kind == 1) {
+      k_diag_chol<<<(unsigned)st.count, NT, 0, s>>>(st.kb, d_subs + st.first, work, dn.work_off, dn.np, d_n,
+                                                    (float*)dn.dinv, dn.dinv_off, piv, piv + N, dn.err);
+      CK_LAUNCH("diagonal blocks of the local Cholesky");
+    } else if (st.kind == 2) {
+      k_sym_decide<<<(unsigned)ceil_div(N, 256), 256, 0, s>>>(N, piv, piv + N, ratio, dn.sym);
+      CK_LAUNCH("explicit-inverse decision");
+    } else {
+      tc_tiles(d_jobs + st.first, st.count, bases[st.a], bases[st.b], bases[st.c], bases[st.c], dn.sym, dn.err,
+               h.num_sms, s);
+    }
   }
 }
 
@@ -798,16 +918,15 @@ void run_local(Handle& h, cudaStream_t s) {
   if (h.events) CK(cudaEventRecord(h.ev[3], s));
   // -- local factor
   if (spd) {
-    const size_t sm3 = sizeof(T) * 3 * TILE * (TILE + 1);
-    CK(cudaFuncSetAttribute(k_chol_trtri<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3));
-    // single precision: subdomains whose Cholesky pivots span at most three
-    // decades get the explicit inverse (one pass in the apply)
-    const double ratio = sizeof(T) == 4 ? 1e3 : 0.0;
-    k_chol_trtri<T><<<N, NT, sm3, s>>>(work, dn.work_off, dn.np, d_n, (T*)dn.dinv, dn.dinv_off, dn.err, dn.sym,
-                                       ratio);
     if constexpr (sizeof(T) == 4) {
-      const unsigned gl = (unsigned)std::min<int64_t>(std::max<int64_t>(tl, 1), 152 * 64);
-      k_lauum<T><<<gl, NT, 0, s>>>(work, dn.work_off, dn.np, d_n, dn.tile_desc, tl, dn.sym, (T*)dn.tiles);
+      // single precision: subdomains whose Cholesky pivots span at most three
+      // decades get the explicit inverse (one pass in the apply)
+      factor_spd_levels(h, work, d_n, 1e3, s);
+    } else {
+      const size_t sm3 = sizeof(T) * 3 * TILE * (TILE + 1);
+      CK(cudaFuncSetAttribute(k_chol_trtri<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3));
+      k_chol_trtri<T><<<N, NT, sm3, s>>>(work, dn.work_off, dn.np, d_n, (T*)dn.dinv, dn.dinv_off, dn.err, dn.sym,
+                                         0.0);
     }
   } else {
     k_sweep<T, false><<<N, NT, 0, s>>>(work, dn.work_off, dn.np, d_n, d_m, d_p, (T*)dn.XpT, dn.xs_off,
