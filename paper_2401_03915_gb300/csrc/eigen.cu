@@ -50,9 +50,16 @@ template <typename T>
 __host__ __device__ constexpr int gemm_lda() { return sizeof(T) == 4 ? GK + 4 : GK + 1; }
 template <typename T>
 __host__ __device__ constexpr int gemm_ldb() { return sizeof(T) == 4 ? GN + 8 : GN; }
+// The single-precision products without column scaling whose operands are
+// both in global memory double-buffer K chunks of GKA columns with cp.async (the next chunk streams in while the
+// current one is multiplied); A row stride GKA + 4, B row stride GN + 8.
+constexpr int GKA = 16;
+constexpr int ASYNC_BUF = GM * (GKA + 4) + GKA * (GN + 8);
 template <typename T>
 __host__ __device__ constexpr size_t gemm_smem_bytes() {
-  return ((sizeof(T) * (GM * gemm_lda<T>() + GK * gemm_ldb<T>()) + 7) / 8) * 8;
+  return sizeof(T) == 4 ? std::max<size_t>(((sizeof(T) * (GM * gemm_lda<T>() + GK * gemm_ldb<T>()) + 7) / 8) * 8,
+                                           sizeof(float) * 2 * ASYNC_BUF)
+                        : ((sizeof(T) * (GM * gemm_lda<T>() + GK * gemm_ldb<T>()) + 7) / 8) * 8;
 }
 
 __device__ __forceinline__ uint32_t f2tf32(float x) {
@@ -79,6 +86,97 @@ struct Scale {
   __device__ bool on() const { return ds != nullptr; }
 };
 
+__device__ __forceinline__ void cp_async4(float* dst, const float* src, bool ok) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src), "r"(ok ? 4 : 0)
+               : "memory");
+}
+
+// The FP32 product of cta_gemm without column scaling: the 3xTF32 mma.sync
+// tile loop of cta_gemm fed by a two-stage cp.async pipeline (masked elements
+// are zero-filled without a read).
+template <bool ACOL, bool SUB, bool UPPER>
+__device__ void cta_gemm_f32_async(int M, int N, int K, const float* __restrict__ A, int lda,
+                                   const float* __restrict__ B, int ldb, float* __restrict__ C, int ldc, float* sm,
+                                   Scale rs) {
+  constexpr int LA = GKA + 4, LB = GN + 8;
+  const int t = threadIdx.x;
+  const int lane = t & 31, w = t >> 5, g = lane >> 2, tq = lane & 3;
+  const int nk = (K + GKA - 1) / GKA;
+  for (int n0 = 0; n0 < N; n0 += GN) {
+    const int nw = min(GN, N - n0);
+    for (int m0 = 0; m0 < M; m0 += GM) {
+      auto issue = [&](int k0, int b) {
+        float* As = sm + b * ASYNC_BUF;
+        float* Bs = As + GM * LA;
+#pragma unroll
+        for (int j = 0; j < GM * GKA / NT; ++j) {
+          const int idx = t + NT * j;
+          int r, kk;
+          if (!ACOL) { r = idx / GKA; kk = idx % GKA; } else { kk = idx / GM; r = idx % GM; }
+          const bool ok = m0 + r < M && k0 + kk < K && (!UPPER || k0 + kk >= m0 + r);
+          const float* src = !ok ? A : (!ACOL ? A + (int64_t)(m0 + r) * lda + k0 + kk : A + (int64_t)(k0 + kk) * lda + m0 + r);
+          cp_async4(As + r * LA + kk, src, ok);
+        }
+#pragma unroll
+        for (int j = 0; j < GKA * GN / NT; ++j) {
+          const int idx = t + NT * j, kk = idx / GN, c = idx % GN;
+          const bool ok = k0 + kk < K && c < nw;
+          cp_async4(Bs + kk * LB + c, ok ? B + (int64_t)(k0 + kk) * ldb + n0 + c : B, ok);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+      };
+      float acc[4][4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[a][q] = 0.f;
+      issue(0, 0);
+      for (int c = 0; c < nk; ++c) {
+        if (c + 1 < nk) {
+          issue((c + 1) * GKA, (c + 1) & 1);
+          asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else {
+          asm volatile("cp.async.wait_group 0;" ::: "memory");
+        }
+        __syncthreads();
+        const float* Ar = sm + (c & 1) * ASYNC_BUF + (16 * w) * LA;
+        const float* Bf = sm + (c & 1) * ASYNC_BUF + GM * LA;
+#pragma unroll
+        for (int kk = 0; kk < GKA; kk += 8) {
+          uint32_t ah[4], al[4];
+          split3(Ar[g * LA + kk + tq], ah[0], al[0]);
+          split3(Ar[(g + 8) * LA + kk + tq], ah[1], al[1]);
+          split3(Ar[g * LA + kk + tq + 4], ah[2], al[2]);
+          split3(Ar[(g + 8) * LA + kk + tq + 4], ah[3], al[3]);
+#pragma unroll
+          for (int nt = 0; nt < 4; ++nt) {
+            uint32_t bh0, bl0, bh1, bl1;
+            split3(Bf[(kk + tq) * LB + 8 * nt + g], bh0, bl0);
+            split3(Bf[(kk + tq + 4) * LB + 8 * nt + g], bh1, bl1);
+            mma_tf32(acc[nt], al, bh0, bh1);
+            mma_tf32(acc[nt], ah, bl0, bl1);
+            mma_tf32(acc[nt], ah, bh0, bh1);
+          }
+        }
+        __syncthreads();
+      }
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int row = m0 + 16 * w + g + (q >= 2 ? 8 : 0);
+          const int c = 8 * a + 2 * tq + (q & 1);
+          if (row >= M || c >= nw) continue;
+          const float f = rs.on() ? (float)rs(row) : 1.f;
+          float* cp = C + (int64_t)row * ldc + n0 + c;
+          if (SUB) *cp -= acc[a][q] * f; else *cp = acc[a][q] * f;
+        }
+    }
+  }
+  __syncthreads();
+}
+
 // C (M x N, ldc) = A (M x K) B (K x N, ldb) (with SUB: C -= A B); A row-major
 // (A[m*lda + k]) or, with ACOL, column-major (A[k*lda + m]).  The product's
 // row m is multiplied by rs(m); A's column k by ks(k) (or divided, with kinv).
@@ -87,6 +185,14 @@ struct Scale {
 template <typename T, bool ACOL, bool SUB = false, bool UPPER = false>
 __device__ void cta_gemm(int M, int N, int K, const T* __restrict__ A, int lda, const T* __restrict__ B, int ldb,
                          T* __restrict__ C, int ldc, T* sm, Scale rs = Scale(), Scale ks = Scale(), bool kinv = false) {
+  if constexpr (sizeof(T) == 4) {
+    // cp.async reads global memory only: operands held in shared memory (the
+    // small projected matrices) take the synchronous loop below
+    if (!ks.on() && __isGlobal(A) && __isGlobal(B)) {
+      cta_gemm_f32_async<ACOL, SUB, UPPER>(M, N, K, A, lda, B, ldb, C, ldc, sm, rs);
+      return;
+    }
+  }
   constexpr int LA = gemm_lda<T>(), LB = gemm_ldb<T>();
   T* As = sm;             // GM x LA
   T* Bs = sm + GM * LA;   // GK x LB
