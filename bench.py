@@ -69,6 +69,10 @@ def parse():
                          "weak: one-GPU weak scaling of 3D Poisson at 8^3 unknowns per subdomain; "
                          "spmv: the SpMV kernel on a 160^3 Laplacian, --apply-iters launches (profiler captures)")
     ap.add_argument("--instances", type=int, default=200, help="stream mode: instances in the stream")
+    ap.add_argument("--no-stream", action="store_true",
+                    help="step mode: skip the batched stream of 200 instances (learned vs randomized start)")
+    ap.add_argument("--stream-batch", type=int, default=20,
+                    help="stream mode: instances per batched setup (block-diagonal system); 0 skips the batched pass")
     ap.add_argument("--sample-subdomains", type=int, default=16,
                     help="oracle_sample mode: subdomains whose local setup is timed and scaled")
     return ap.parse_args()
@@ -405,9 +409,83 @@ def run_stream(args, P, torch, dev, stream):
         torch.cuda.synchronize()
         out[name] = {"s_total": e0.elapsed_time(e1) / 1e3, "iterations_total": int(np.sum(its)),
                      "mean_sweeps": float(np.mean(sweeps)), "subdomains": subs, "unknowns": rows}
+    batched = run_stream_batched(args, P, torch, dev, stream, insts, net) if args.stream_batch > 0 else None
     print(json.dumps({"mode": "stream", "instances": args.instances, "warm_start": warm_info, **out,
-                      "learned_vs_random": out["random"]["s_total"] / out["learned"]["s_total"]}), flush=True)
+                      "learned_vs_random": out["random"]["s_total"] / out["learned"]["s_total"],
+                      "batched": batched}), flush=True)
     net.close()
+
+
+def run_stream_batched(args, P, torch, dev, stream, insts, net):
+    """The stream in batches: G instances at a time form one block-diagonal
+    system (their subdomains concatenated, uneven sizes in the same launches),
+    set up by one asm_setup and solved by one asm_solve_segments call, which
+    runs one PCG recurrence per instance, each to its own 1e-8.  The true
+    per-instance residuals are checked on the host after the timed region."""
+    import scipy.sparse as sp
+    G = args.stream_batch
+    groups = []
+    for g0 in range(0, len(insts), G):
+        chunk = insts[g0:g0 + G]
+        mats, parts, offs = [], [], [0]
+        off = 0
+        for p, *_ in chunk:
+            mats.append(p.csr())
+            parts.append(np.asarray(p.part, dtype=np.int32) + off)
+            off += p.N
+            offs.append(offs[-1] + p.n)
+        A = sp.block_diag(mats, format="csr")
+        A.sort_indices()
+        bnp = np.concatenate([np.asarray(p.b) for p, *_ in chunk])
+        groups.append({
+            "A": A, "N": off, "offs": np.asarray(offs, dtype=np.int32), "bnp": bnp,
+            "rp": torch.as_tensor(A.indptr.astype(np.int32), device=dev),
+            "ci": torch.as_tensor(A.indices.astype(np.int32), device=dev),
+            "va": torch.as_tensor(A.data.astype(np.float64), device=dev),
+            "pa": torch.as_tensor(np.concatenate(parts), device=dev),
+            "b": torch.as_tensor(bnp, device=dev),
+            "delta": chunk[0][0].delta, "nev": chunk[0][0].nev})
+    sopt = P.default_solve_opts(rtol=1e-8, max_it=5000)
+    res = {"instances_per_setup": G, "setups": len(groups), "solve": "asm_solve_segments (one PCG per instance)"}
+    for name, warm in (("random", False), ("learned", True)):
+        opt = P.default_options(local_precision=P.PREC_FP32, warm_start=1 if warm else 0,
+                                warm_net=net.ptr if warm else None)
+        g = groups[0]  # warm-up
+        x = torch.zeros_like(g["b"])
+        h = P.asm_setup(g["rp"], g["ci"], g["va"], g["pa"], g["N"], g["delta"], g["nev"], opt, stream, True)
+        P.asm_solve_segments(h, g["b"], x, g["offs"], sopt, stream)
+        P.asm_destroy(h)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        xs, its, sev = [], [], []
+        e0.record(stream)
+        for g in groups:
+            x = torch.zeros_like(g["b"])
+            es = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            es[0].record(stream)
+            h = P.asm_setup(g["rp"], g["ci"], g["va"], g["pa"], g["N"], g["delta"], g["nev"], opt, stream, True)
+            es[1].record(stream)
+            sev.append(es)
+            infos = P.asm_solve_segments(h, g["b"], x, g["offs"], sopt, stream)
+            its.append([int(i.iterations) for i in infos])
+            P.asm_destroy(h)
+            xs.append(x)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        worst = 0.0
+        for g, x in zip(groups, xs):
+            r = g["bnp"] - g["A"] @ x.cpu().numpy()
+            o = g["offs"]
+            for k in range(len(o) - 1):
+                worst = max(worst, float(np.linalg.norm(r[o[k]:o[k + 1]]) / np.linalg.norm(g["bnp"][o[k]:o[k + 1]])))
+        flat = [v for row in its for v in row]
+        setup_ms = [a.elapsed_time(b_) for a, b_ in sev]
+        res[name] = {"s_total": e0.elapsed_time(e1) / 1e3, "setup_ms_total": float(np.sum(setup_ms)),
+                     "iterations_total": int(np.sum(flat)), "max_iterations_per_setup": [max(r) for r in its],
+                     "max_instance_relres": worst}
+    res["learned_vs_random"] = res["random"]["s_total"] / res["learned"]["s_total"]
+    return res
 
 
 def run_sweep(args, P, torch, dev, stream):
@@ -723,6 +801,17 @@ def run_ours(args):
         e2e = {"value": te, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(8 * prob.n)}
         e2e["value"] = max_over_ranks(te, dist, dev)
 
+    # the stream of 200 uneven instances, set up in batches of block-diagonal
+    # systems and solved one PCG per instance, learned against randomized start
+    stream_line = None
+    if rank == 0 and world == 1 and net is not None and not args.no_stream:
+        from asm_inputs import stream_instance
+        insts = [(stream_instance(k, base_seed=0),) for k in range(args.instances)]
+        stream_line = run_stream_batched(args, P, torch, dev, stream, insts, net)
+        stream_line["instances"] = args.instances
+        stream_line["subdomains"] = int(sum(p.N for p, in insts))
+        stream_line["unknowns"] = int(sum(p.n for p, in insts))
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, threads, desc = oracle_sample(prob, n_sub=16, gpu_iterations=None, use_stored=args.config == "c2")
@@ -750,7 +839,7 @@ def run_ours(args):
                          "algorithmic_bytes_per_launch": pass_bytes},
             "spmv": spmv, "configs": configs,
             "clocks": clocks, "gpu_launches": launches, "e2e": e2e, "cpu_baseline": cpu,
-            "forms": forms, "warm_start": warm_info,
+            "forms": forms, "warm_start": warm_info, "stream": stream_line,
         }
         print(json.dumps(line), flush=True)
     if dist:

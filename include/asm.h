@@ -200,6 +200,24 @@ asm_status asm_apply(asm_handle* h, const double* r, double* z, void* stream);
 asm_status asm_solve(asm_handle* h, const double* b, double* x, const asm_solve_opts* o,
                      asm_solve_info* info, void* stream);
 
+/* Independent SPD systems that share one handle: rows [seg_off[k],
+ * seg_off[k+1]) form segment k, and A couples no two segments and no
+ * subdomain has rows in two of them (so A, every local solve and the coarse
+ * correction are block diagonal over the segments; checked on the device,
+ * INVALID_ARG otherwise).  PCG runs one recurrence per segment (its own
+ * step lengths and stopping test ||b_k - A_k x_k|| / ||b_k|| <= rtol, x0 = 0)
+ * while the SpMV and the two-level apply are launched once for all segments:
+ * a stream of problems of uneven sizes set up by one asm_setup on their
+ * block-diagonal matrix is solved in one call, each to its own tolerance.
+ * seg_off: host, nseg + 1 non-decreasing offsets from 0 to n (1 <= nseg <=
+ * 65535); b, x as in asm_solve (device, or host for a host-built handle);
+ * info: host array of nseg entries (iterations = those of segment k until it
+ * converged, solve_ms the whole call).  The additive SPD preconditioner only
+ * (UNSUPPORTED otherwise).  Returns NO_CONVERGENCE if a segment reaches
+ * max_it; NOT_SPD if a step length's denominator is not positive. */
+asm_status asm_solve_segments(asm_handle* h, const double* b, double* x, int32_t nseg, const int32_t* seg_off,
+                              const asm_solve_opts* o, asm_solve_info* info, void* stream);
+
 /* y = A x with the handle's copy of A (device x, y). */
 asm_status asm_spmv(asm_handle* h, const double* x, double* y, void* stream);
 

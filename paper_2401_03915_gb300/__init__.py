@@ -105,6 +105,8 @@ def load(path: str | None = None) -> C.CDLL:
     i64, f32 = C.c_int64, C.c_float
     L.asm_tile_products.argtypes = [vp, i64, vp, vp, vp, vp, vp]
     L.asm_tile_products.restype = C.c_int
+    L.asm_solve_segments.argtypes = [vp, vp, vp, i32, vp, C.POINTER(asm_solve_opts), vp, vp]
+    L.asm_solve_segments.restype = C.c_int
     L.asm_mlp_create.argtypes = [i32, i32, C.c_uint64, pp]
     L.asm_mlp_destroy.argtypes = [vp]
     L.asm_mlp_destroy.restype = None
@@ -197,6 +199,21 @@ def asm_solve(h: int, b, x, opts: asm_solve_opts | None = None, stream=None,
         return info
     _check(st)
     return info
+
+
+def asm_solve_segments(h: int, b, x, seg_off, opts: asm_solve_opts | None = None, stream=None,
+                       raise_on_no_convergence: bool = True):
+    """PCG on the independent systems of the row segments [seg_off[k],
+    seg_off[k+1]) of a block-diagonal handle, each to its own tolerance
+    (asm_solve_segments); returns one asm_solve_info per segment."""
+    off = np.ascontiguousarray(np.asarray(seg_off, dtype=np.int32))
+    nseg = len(off) - 1
+    infos = (asm_solve_info * max(nseg, 1))()
+    st = load().asm_solve_segments(h, _ptr(b), _ptr(x), nseg, off.ctypes.data, C.byref(opts) if opts else None,
+                                   infos, _stream(stream))
+    if not (st == 6 and not raise_on_no_convergence):
+        _check(st)
+    return [infos[k] for k in range(nseg)]
 
 
 def asm_get_info(h: int) -> asm_setup_info:

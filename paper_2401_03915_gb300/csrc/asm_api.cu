@@ -344,6 +344,45 @@ asm_status asm_time_spmv(asm_handle* H, const double* p, double* q, int32_t iter
   return guarded([&] { time_pcg_spmv(H->h, p, q, iters, static_cast<cudaStream_t>(stream), ms); });
 }
 
+asm_status asm_solve_segments(asm_handle* H, const double* b, double* x, int32_t nseg, const int32_t* seg_off,
+                              const asm_solve_opts* o, asm_solve_info* info, void* stream) {
+  if (!H || !b || !x || !seg_off || !info) return set_error(ASM_ERR_INVALID_ARG, "null argument");
+  if (nseg < 1 || nseg > 65535) return set_error(ASM_ERR_INVALID_ARG, "nseg must be in 1 .. 65535");
+  Handle& h = H->h;
+  if (seg_off[0] != 0 || seg_off[nseg] != h.n)
+    return set_error(ASM_ERR_INVALID_ARG, "seg_off must start at 0 and end at n");
+  for (int k = 0; k < nseg; ++k)
+    if (seg_off[k + 1] < seg_off[k]) return set_error(ASM_ERR_INVALID_ARG, "seg_off must be non-decreasing");
+  asm_solve_opts so;
+  if (o) so = *o; else asm_default_solve_opts(&so);
+  if (!(so.rtol > 0) || so.max_it < 1) return set_error(ASM_ERR_INVALID_ARG, "rtol must be > 0 and max_it >= 1");
+  const bool symmetric = h.opt.spd && h.opt.one_level == 0 && (h.opt.coarse_mode == 0 || h.co.n_C == 0);
+  if (!symmetric || (so.method != 0 && so.method != 1))
+    return set_error(ASM_ERR_UNSUPPORTED, "asm_solve_segments: PCG with the additive SPD preconditioner only");
+  std::memset(info, 0, sizeof(asm_solve_info) * nseg);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  bool conv = true;
+  asm_status st = guarded([&] {
+    const double* db = b;
+    double* dx = x;
+    if (h.host_io) {
+      if (!h.kr.bx) h.kr.bx = h.mem.alloc<double>(2LL * h.n);
+      db = h.kr.bx;
+      dx = h.kr.bx + h.n;
+      CK(cudaMemcpyAsync(h.kr.bx, b, sizeof(double) * h.n, cudaMemcpyHostToDevice, s));
+    }
+    solve_pcg_segments(h, db, dx, nseg, seg_off, so, info, s);
+    check_device_error(h, s, "segmented solve");
+    if (h.host_io) {
+      CK(cudaMemcpyAsync(x, dx, sizeof(double) * h.n, cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+    }
+    for (int k = 0; k < nseg; ++k) conv = conv && info[k].converged != 0;
+  });
+  if (st != ASM_OK) return st;
+  return conv ? ASM_OK : set_error(ASM_ERR_NO_CONVERGENCE, "asm_solve_segments: max_it reached on a segment");
+}
+
 asm_status asm_tile_products(const asm_tile_job* jobs, int64_t njobs, const float* a, const float* b,
                              const float* cin, float* cout, void* stream) {
   static_assert(sizeof(asm_tile_job) == sizeof(TcJob), "asm_tile_job must mirror TcJob");

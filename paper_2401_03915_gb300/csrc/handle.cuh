@@ -206,6 +206,12 @@ void coarse_solve(Handle& h, const double* c, double* y, cudaStream_t s,
                   const int32_t* done = nullptr);                                 // coarse.cu
 void solve_pcg(Handle& h, const double* b, double* x, const asm_solve_opts& o, asm_solve_info& info,
                cudaStream_t s);
+// PCG on the independent systems of contiguous row segments h_off[0..nseg]
+// (host offsets), one recurrence and one stopping test per segment, info[k]
+// per segment (krylov_seg.cu)
+void solve_pcg_segments(Handle& h, const double* b, double* x, int nseg, const int32_t* h_off,
+                        const asm_solve_opts& o, asm_solve_info* info, cudaStream_t s);
+void krylov_buffers(Handle& h, cudaStream_t s);  // the Krylov vectors and pinned flags (krylov.cu)
 // auto_restart: the caller left the restart length to the library (it may be
 // shortened to fit the basis in device memory)
 void solve_fgmres(Handle& h, const double* b, double* x, const asm_solve_opts& o,

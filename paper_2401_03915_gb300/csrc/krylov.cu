@@ -278,6 +278,8 @@ void spmv(Handle& h, const double* x, double* y, cudaStream_t s) {
   CK_LAUNCH("spmv");
 }
 
+void krylov_buffers(Handle& h, cudaStream_t s) { ensure_krylov(h, s); }
+
 void csr_spmv(int n, int64_t nnz, const int32_t* rp, const int32_t* ci, const double* val, const double* x,
               double* y, cudaStream_t s) {
   if (n <= 0) return;
