@@ -245,38 +245,57 @@ def oracle_single_thread(name: str, n_sub: int):
 
 def config_lines(P, torch, dev, stream):
     """Setup + solve of the elasticity (PCG) and convection-diffusion (FGMRES)
-    configurations with FP32 local work, next to the oracle's iteration counts
-    from tests/golden/ when those files are present."""
+    configurations with FP32 local work, and of the elasticity with the BF16
+    subspace iteration (ASM_PREC_FP32_B16), next to the oracle's iteration
+    counts and local values from tests/golden/ when those files are present."""
     from asm_inputs import config
     out = {}
-    for name in ("c3", "c4"):
-        prob = config(name)
+    for name, cname, prec in (("c3", "c3", P.PREC_FP32), ("c3_bf16", "c3", P.PREC_FP32_B16),
+                              ("c4", "c4", P.PREC_FP32)):
+        prob = config(cname)
         t = [torch.as_tensor(a, device=dev) for a in (prob.indptr, prob.indices, prob.data, prob.part, prob.b)]
-        opt = P.default_options(spd=1 if prob.spd else 0, local_precision=P.PREC_FP32)
+        opt = P.default_options(spd=1 if prob.spd else 0, local_precision=prec)
         so = P.default_solve_opts(rtol=1e-8, max_it=5000)
 
-        def once():
+        def once(keep=False):
             x = torch.zeros_like(t[4])
             h = P.asm_setup(t[0], t[1], t[2], t[3], prob.N, prob.delta, prob.nev, opt, stream, True)
             inf = P.asm_solve(h, t[4], x, so, stream)
             si = P.asm_get_info(h)
+            vals = P.asm_get_local_values(h) if keep else None
             P.asm_destroy(h)
-            return inf, si
+            return inf, si, vals
         once()
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        inf, si = once()
+        inf, si, _ = once()
         e1.record(stream)
         torch.cuda.synchronize()
-        row = {"s_per_step": e0.elapsed_time(e1) / 1e3, "setup_ms": si.stage_ms[7], "solve_ms": inf.solve_ms,
-               "iterations": inf.iterations, "true_relres": inf.true_relres, "n": prob.n, "N": prob.N,
-               "n_C": si.n_C, "method": "PCG" if prob.spd else "FGMRES(30)"}
+        row = {"s_per_step": e0.elapsed_time(e1) / 1e3, "setup_ms": si.stage_ms[7], "eigen_ms": si.stage_ms[4],
+               "solve_ms": inf.solve_ms, "iterations": inf.iterations, "true_relres": inf.true_relres,
+               "n": prob.n, "N": prob.N, "n_C": si.n_C, "method": "PCG" if prob.spd else "FGMRES(30)",
+               "local_precision": {P.PREC_FP32: "fp32", P.PREC_FP32_B16: "fp32, bf16 subspace iteration"}[prec]}
         try:
-            with open(os.path.join(ROOT, "tests", "golden", f"{name}_oracle_reference.json")) as f:
-                row["oracle_iterations"] = int(json.load(f)["iterations"])
-        except Exception:
+            with open(os.path.join(ROOT, "tests", "golden", f"{cname}_oracle_reference.json")) as f:
+                ref = json.load(f)
+            row["oracle_iterations"] = int(ref["iterations"])
+            # local values against the oracle's, every subdomain
+            _, _, (vals, cnt) = once(keep=True)
+            rel, scaled = [], []
+            for i, rv in enumerate(ref["values"]):
+                rv = np.asarray(rv)
+                k = min(len(rv), int(cnt[i]))
+                if k == 0:
+                    continue
+                d = np.abs(vals[i, :k] - rv[:k])
+                rel.extend((d / rv[:k]).tolist())
+                scaled.append(float(d.max() / rv[0]))
+            row["values_vs_oracle"] = {"counts_equal": bool(all(int(cnt[i]) == len(v) for i, v in enumerate(ref["values"]))),
+                                       "median_rel_err": float(np.median(rel)), "max_rel_err": float(np.max(rel)),
+                                       "max_err_over_top_value": float(np.max(scaled))}
+        except (OSError, KeyError, ValueError):
             row["oracle_iterations"] = None
         out[name] = row
     return out

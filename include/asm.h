@@ -56,7 +56,14 @@ typedef enum {
  * wherever 2^-11 ||S_i||_inf ||A^_ii||_inf + |Omega_i| 2^-25 ||A^_ii||_inf <= 1/4,
  * which keeps the eigenvalues of the stored inverse times A^_ii within
  * [3/4, 5/4]; the other subdomains keep FP32 tiles. */
-typedef enum { ASM_PREC_FP64 = 0, ASM_PREC_FP32 = 1, ASM_PREC_FP32_H16 = 2 } asm_precision;
+/* ASM_PREC_FP32_B16: single-precision local work, and for SPD A the
+ * subspace iteration's operator applications K Y = U (A^_II (U^T Y)) (the
+ * block products with U = W[Gamma_delta, I_i]) multiply BF16-rounded operands
+ * with FP32 accumulation; its Gram, Rayleigh-Ritz and output products and
+ * everything else stay as ASM_PREC_FP32.  The eigen-residual test is that of
+ * the BF16 operator (relative accuracy about 2^-8), so the kept vectors
+ * approximate those of eq. gevpsvd to that level.  General A: as FP32. */
+typedef enum { ASM_PREC_FP64 = 0, ASM_PREC_FP32 = 1, ASM_PREC_FP32_H16 = 2, ASM_PREC_FP32_B16 = 3 } asm_precision;
 
 /* Sparse matrix A (eq. Ax=b).  row_ptr has n+1 entries, col_idx and val nnz.
  * on_device != 0: the three arrays (and the partition passed to asm_setup)

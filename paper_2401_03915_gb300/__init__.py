@@ -19,7 +19,7 @@ from . import build as _build
 ASM_OK = 0
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "NOT_SPD", 3: "ZERO_PIVOT", 4: "COARSE_SINGULAR",
           5: "NONFINITE", 6: "NO_CONVERGENCE", 7: "TIMEOUT", 8: "CUDA", 9: "OOM", 10: "UNSUPPORTED"}
-PREC_FP64, PREC_FP32, PREC_FP32_H16 = 0, 1, 2
+PREC_FP64, PREC_FP32, PREC_FP32_H16, PREC_FP32_B16 = 0, 1, 2, 3
 
 
 class AsmError(RuntimeError):
@@ -507,7 +507,7 @@ class TwoLevelSchwarz:
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required")
-        prec = {"fp64": PREC_FP64, "fp32": PREC_FP32, "fp32h": PREC_FP32_H16}[precision]
+        prec = {"fp64": PREC_FP64, "fp32": PREC_FP32, "fp32h": PREC_FP32_H16, "fp32b": PREC_FP32_B16}[precision]
         o = default_options(spd=1 if spd else 0, local_precision=prec, **opts)
         self.device = device
         self.n = len(indptr) - 1

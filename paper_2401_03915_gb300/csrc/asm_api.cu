@@ -143,8 +143,9 @@ asm_status asm_setup(const asm_csr* A, const int32_t* part, int32_t N, int32_t o
   asm_options o;
   if (opt) o = *opt; else asm_default_options(&o);
   if (o.local_precision != ASM_PREC_FP64 && o.local_precision != ASM_PREC_FP32 &&
-      o.local_precision != ASM_PREC_FP32_H16)
-    return set_error(ASM_ERR_INVALID_ARG, "local_precision must be ASM_PREC_FP64, ASM_PREC_FP32 or ASM_PREC_FP32_H16");
+      o.local_precision != ASM_PREC_FP32_H16 && o.local_precision != ASM_PREC_FP32_B16)
+    return set_error(ASM_ERR_INVALID_ARG,
+                     "local_precision must be ASM_PREC_FP64, ASM_PREC_FP32, ASM_PREC_FP32_H16 or ASM_PREC_FP32_B16");
   if (o.oversample < 0 || o.oversample > 64) return set_error(ASM_ERR_INVALID_ARG, "oversample must be in 0..64");
   if (o.warm_start && (!o.warm_net || !o.spd))
     return set_error(ASM_ERR_INVALID_ARG, "warm_start needs warm_net and the SPD method");
@@ -167,6 +168,7 @@ asm_status asm_setup(const asm_csr* A, const int32_t* part, int32_t N, int32_t o
     h.host_io = A->on_device == 0;
     h.fp32 = o.local_precision != ASM_PREC_FP64;
     h.s16 = o.local_precision == ASM_PREC_FP32_H16 && o.spd;
+    h.b16eig = o.local_precision == ASM_PREC_FP32_B16 && o.spd;
     h.lift = o.nu > 0 && o.spd && o.coarse;
     h.nev_lift = h.lift ? (o.nev_lift > 0 ? o.nev_lift : nev) : 0;
     if (h.lift && h.nev_lift == 0) h.lift = false;

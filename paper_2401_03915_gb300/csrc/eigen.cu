@@ -33,6 +33,8 @@
 // Dense block products go through a shared-memory tiled CTA GEMM.
 #include <algorithm>
 
+#include <cuda_bf16.h>
+
 #include "handle.cuh"
 
 namespace asmgpu {
@@ -78,6 +80,19 @@ __device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], 
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
+// two FP32 values rounded to BF16 and packed, the first in the low half (the
+// lower k index of an mma.sync fragment pair)
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
 // Optional diagonal scalings (general path): factor for index q.
 struct Scale {
   const double* ds = nullptr;
@@ -95,7 +110,7 @@ __device__ __forceinline__ void cp_async4(float* dst, const float* src, bool ok)
 // The FP32 product of cta_gemm without column scaling: the 3xTF32 mma.sync
 // tile loop of cta_gemm fed by a two-stage cp.async pipeline (masked elements
 // are zero-filled without a read).
-template <bool ACOL, bool SUB, bool UPPER>
+template <bool ACOL, bool SUB, bool UPPER, bool B16>
 __device__ void cta_gemm_f32_async(int M, int N, int K, const float* __restrict__ A, int lda,
                                    const float* __restrict__ B, int ldb, float* __restrict__ C, int ldc, float* sm,
                                    Scale rs) {
@@ -142,6 +157,20 @@ __device__ void cta_gemm_f32_async(int M, int N, int K, const float* __restrict_
         __syncthreads();
         const float* Ar = sm + (c & 1) * ASYNC_BUF + (16 * w) * LA;
         const float* Bf = sm + (c & 1) * ASYNC_BUF + GM * LA;
+        if constexpr (B16) {
+          // one m16n8k16 per n tile: operands rounded to BF16, FP32 accumulation
+          uint32_t a[4];
+          a[0] = pack_bf16(Ar[g * LA + 2 * tq], Ar[g * LA + 2 * tq + 1]);
+          a[1] = pack_bf16(Ar[(g + 8) * LA + 2 * tq], Ar[(g + 8) * LA + 2 * tq + 1]);
+          a[2] = pack_bf16(Ar[g * LA + 2 * tq + 8], Ar[g * LA + 2 * tq + 9]);
+          a[3] = pack_bf16(Ar[(g + 8) * LA + 2 * tq + 8], Ar[(g + 8) * LA + 2 * tq + 9]);
+#pragma unroll
+          for (int nt = 0; nt < 4; ++nt) {
+            const uint32_t b0 = pack_bf16(Bf[(2 * tq) * LB + 8 * nt + g], Bf[(2 * tq + 1) * LB + 8 * nt + g]);
+            const uint32_t b1 = pack_bf16(Bf[(2 * tq + 8) * LB + 8 * nt + g], Bf[(2 * tq + 9) * LB + 8 * nt + g]);
+            mma_bf16(acc[nt], a, b0, b1);
+          }
+        } else {
 #pragma unroll
         for (int kk = 0; kk < GKA; kk += 8) {
           uint32_t ah[4], al[4];
@@ -158,6 +187,7 @@ __device__ void cta_gemm_f32_async(int M, int N, int K, const float* __restrict_
             mma_tf32(acc[nt], ah, bl0, bl1);
             mma_tf32(acc[nt], ah, bh0, bh1);
           }
+        }
         }
         __syncthreads();
       }
@@ -182,14 +212,14 @@ __device__ void cta_gemm_f32_async(int M, int N, int K, const float* __restrict_
 // row m is multiplied by rs(m); A's column k by ks(k) (or divided, with kinv).
 // UPPER (with ACOL): A is the transpose of a lower-triangular block whose
 // upper part in memory holds other data, so A(m, k) is taken as 0 for k < m.
-template <typename T, bool ACOL, bool SUB = false, bool UPPER = false>
+template <typename T, bool ACOL, bool SUB = false, bool UPPER = false, bool B16 = false>
 __device__ void cta_gemm(int M, int N, int K, const T* __restrict__ A, int lda, const T* __restrict__ B, int ldb,
                          T* __restrict__ C, int ldc, T* sm, Scale rs = Scale(), Scale ks = Scale(), bool kinv = false) {
   if constexpr (sizeof(T) == 4) {
     // cp.async reads global memory only: operands held in shared memory (the
     // small projected matrices) take the synchronous loop below
     if (!ks.on() && __isGlobal(A) && __isGlobal(B)) {
-      cta_gemm_f32_async<ACOL, SUB, UPPER>(M, N, K, A, lda, B, ldb, C, ldc, sm, rs);
+      cta_gemm_f32_async<ACOL, SUB, UPPER, B16>(M, N, K, A, lda, B, ldb, C, ldc, sm, rs);
       return;
     }
   }
@@ -458,7 +488,10 @@ struct EigOut {
   int refine;               // FP64, lifting or overlap 1: report the variational Rayleigh quotient
 };
 
-template <typename T, bool SPD>
+// B16 (single precision, SPD): the operator applications K Y = U (A^_II (U^T Y))
+// multiply BF16-rounded operands with FP32 accumulation; the Gram,
+// Rayleigh-Ritz and output products stay 3xTF32.
+template <typename T, bool SPD, bool B16 = false>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 4 : 1) k_subspace(
     const T* __restrict__ XpT_all, const int64_t* __restrict__ xs_off, const T* __restrict__ S_all,
     const int64_t* __restrict__ s_off, const T* __restrict__ work, const int64_t* __restrict__ work_off,
@@ -528,9 +561,9 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 4 : 1) k_subspace(
   // Column c0.. c0+nc-1 of the blocks (stride sp).
   auto applyK = [&](const T* Yin, T* out, int c0, int nc) {
     if (SPD) {
-      cta_gemm<T, true>(p, nc, g, U, ld, Yin + c0, sp, V + c0, sp, gsm);           // V = U^T Y
+      cta_gemm<T, true, false, false, B16>(p, nc, g, U, ld, Yin + c0, sp, V + c0, sp, gsm);    // V = U^T Y
       mul_AII(p, pos0, ent_off, lcol, aval, V + c0, AV + c0, nc, sp);
-      cta_gemm<T, false>(g, nc, p, U, ld, AV + c0, sp, out + c0, sp, gsm);         // U (A^_II V)
+      cta_gemm<T, false, false, false, B16>(g, nc, p, U, ld, AV + c0, sp, out + c0, sp, gsm);  // U (A^_II V)
     } else {
       // W = X_p^T Y = S_G^{-1} X^_p^T S_I Y ; out = X_p W = S_I X^_p S_G^{-1} W
       cta_gemm<T, false>(g, nc, p, XpT, p, Yin + c0, sp, AV + c0, sp, gsm, Scale(), sI, false);
@@ -1151,8 +1184,14 @@ void run_eigen(Handle& h, cudaStream_t s) {
                              co.sweeps, co.Z, co.z_off, eo);
   };
   if (nev > 0) {
-    if (spd) launch(k_subspace<T, true>);
-    else launch(k_subspace<T, false>);
+    if constexpr (sizeof(T) == 4) {
+      if (spd && h.b16eig) launch(k_subspace<T, true, true>);
+      else if (spd) launch(k_subspace<T, true>);
+      else launch(k_subspace<T, false>);
+    } else {
+      if (spd) launch(k_subspace<T, true>);
+      else launch(k_subspace<T, false>);
+    }
   } else {
     CK(cudaMemsetAsync(co.count_g, 0, 4 * N, s));
     CK(cudaMemsetAsync(co.sweeps, 0, 4 * N, s));

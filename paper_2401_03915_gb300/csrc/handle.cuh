@@ -147,6 +147,7 @@ struct Handle {
   bool host_io = false;
   bool fp32 = false;
   bool s16 = false;                 // explicit local inverses stored in FP16 where the bound allows
+  bool b16eig = false;              // SPD subspace iteration: operator applications on BF16 operands
   bool lift = false;                // eq. uppergevp vectors added (opt.nu > 0, SPD)
   int32_t nev_lift = 0;             // at most this many per subdomain
   DevMem mem;

@@ -109,3 +109,29 @@ def test_c4_convdiff_full_size(P):
     assert info.converged and rel <= 1e-7, (info.iterations, rel)
     assert abs(info.iterations - ref["iterations"]) <= 0.1 * ref["iterations"], (info.iterations, ref["iterations"])
     pre.close()
+
+
+def test_c3_elasticity_bf16_subspace_iteration(P):
+    """ASM_PREC_FP32_B16: the subspace iteration's operator applications on
+    BF16 operands with FP32 accumulation.  Rounding U and the block to BF16
+    (2^-9 relative each) perturbs the operator K = U A^_II U^T by at most
+    about 2^-7 ||K|| (two roundings in each of its two products), so each kept
+    value moves by at most that much: |mu~_k - mu_k| <= 2^-6 mu_1 per
+    subdomain with a factor-two margin; counts, n_C and the iteration count
+    within 10% of the oracle's as for FP32."""
+    prob = config("c3")
+    ref = _golden("c3")
+    pre = _setup(P, prob, precision="fp32b")
+    vals, cnt = P.asm_get_local_values(pre.h)
+    errs = []
+    for i, rv in enumerate(ref["values"]):
+        rv = np.asarray(rv)
+        assert int(cnt[i]) == len(rv), (i, int(cnt[i]), len(rv))
+        errs.append(np.max(np.abs(vals[i, :len(rv)] - rv)) / rv[0])
+    assert max(errs) <= 2.0 ** -6, max(errs)
+    assert pre.info.n_C == ref["n_C"]
+    x, info = pre.solve(torch.as_tensor(prob.b, device="cuda"))
+    rel = _true_relres(prob, x.cpu().numpy())
+    assert info.converged and rel <= 1.5e-8, (info.iterations, rel)
+    assert abs(info.iterations - ref["iterations"]) <= 0.1 * ref["iterations"], (info.iterations, ref["iterations"])
+    pre.close()
