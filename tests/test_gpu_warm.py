@@ -171,3 +171,55 @@ def test_training_reduces_loss_and_warm_start_gains():
     # sweeps 9.7e-2 -> 2.1e-2; the margins leave room for run-to-run spread
     assert sw1 <= 0.95 * sw0 and r1 <= 0.5 * r0, (sw0, sw1, r0, r1)
     net.close()
+
+
+def test_learned_start_speeds_up_the_batched_stream():
+    """The driver-visible claim: on held-out instances set up in batches of
+    20 (one asm_setup per block-diagonal batch, one PCG per instance through
+    asm_solve_segments), the learned start makes setup + solve at least 10%
+    faster than the randomized one (measured on GB300 over the 200-instance
+    stream: 1.28x) while every instance still reaches 1e-8."""
+    import scipy.sparse as sp
+    train = [stream_instance(k, base_seed=1) for k in range(12)]
+    X, T, off = _collect(train)
+    net = P.WarmStartNet(256, 16, seed=1)
+    net.train(X, T, off, steps=2000, lr=1e-3, batch=32)
+    insts = [stream_instance(k, base_seed=0) for k in range(40)]
+    batches = []
+    for g0 in range(0, len(insts), 20):
+        chunk = insts[g0:g0 + 20]
+        A = sp.block_diag([p.csr() for p in chunk], format="csr")
+        A.sort_indices()
+        parts, o, offs = [], 0, [0]
+        for p in chunk:
+            parts.append(np.asarray(p.part, dtype=np.int32) + o)
+            o += p.N
+            offs.append(offs[-1] + p.n)
+        b = np.concatenate([p.b for p in chunk])
+        batches.append((A, np.concatenate(parts), o, np.asarray(offs, dtype=np.int32), b))
+    times, sweeps = {}, {}
+    for warm in (0, 1, 0, 1):   # twice each, best kept
+        kw = dict(warm_start=warm, warm_net=net.ptr if warm else None)
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record()
+        sw = []
+        for A, part, N, offs, b in batches:
+            S = P.TwoLevelSchwarz(A.indptr, A.indices, A.data, part, N, 1, 16, precision="fp32", **kw)
+            sw.append(P.asm_get_eigen_stats(S.h)[1])
+            bt = torch.as_tensor(b, device="cuda")
+            x = torch.zeros_like(bt)
+            infos = P.asm_solve_segments(S.h, bt, x, offs, P.default_solve_opts(rtol=1e-8, max_it=5000))
+            assert all(i.converged and i.true_relres <= 1.5e-8 for i in infos)
+            S.close()
+        t1.record()
+        torch.cuda.synchronize()
+        ms = t0.elapsed_time(t1)
+        times[warm] = min(times.get(warm, 3e38), ms)
+        sweeps[warm] = np.concatenate(sw).mean()
+    print(f"batched stream (40 instances): random {times[0]:.1f} ms, learned {times[1]:.1f} ms; "
+          f"mean sweeps {sweeps[0]:.2f} -> {sweeps[1]:.2f}")
+    assert times[0] >= 1.10 * times[1], times
+    assert sweeps[1] <= 0.95 * sweeps[0], sweeps
+    net.close()
