@@ -406,7 +406,7 @@ def run_stream(args, P, torch, dev, stream):
     for name, warm in (("random", False), ("learned", True)):
         opt = P.default_options(local_precision=P.PREC_FP32, warm_start=1 if warm else 0,
                                 warm_net=net.ptr if warm else None)
-        for p, rp, ci, va, pa, b in insts[:3]:  # warm-up (tuner caches, pools)
+        for p, rp, ci, va, pa, b in (insts if name == "random" else insts[:3]):  # warm-up: tuner cache per shape
             x = torch.zeros_like(b)
             h = P.asm_setup(rp, ci, va, pa, p.N, p.delta, p.nev, opt, stream, True)
             P.asm_solve(h, b, x, sopt, stream)
@@ -465,19 +465,21 @@ def run_stream_batched(args, P, torch, dev, stream, insts, net):
             "b": torch.as_tensor(bnp, device=dev),
             "delta": chunk[0][0].delta, "nev": chunk[0][0].nev})
     sopt = P.default_solve_opts(rtol=1e-8, max_it=5000)
-    res = {"instances_per_setup": G, "setups": len(groups), "solve": "asm_solve_segments (one PCG per instance)"}
+    res = {"instances_per_setup": G, "setups": len(groups), "solve": "asm_solve_segments (one PCG per instance)",
+           "warmup": "one untimed pass over every batch first (the apply tuner caches its choice per shape)"}
+    opt0 = P.default_options(local_precision=P.PREC_FP32)
+    for g in groups:
+        x = torch.zeros_like(g["b"])
+        h = P.asm_setup(g["rp"], g["ci"], g["va"], g["pa"], g["N"], g["delta"], g["nev"], opt0, stream, True)
+        P.asm_solve_segments(h, g["b"], x, g["offs"], sopt, stream)
+        P.asm_destroy(h)
+    torch.cuda.synchronize()
     for name, warm in (("random", False), ("learned", True)):
         opt = P.default_options(local_precision=P.PREC_FP32, warm_start=1 if warm else 0,
                                 warm_net=net.ptr if warm else None)
-        g = groups[0]  # warm-up
-        x = torch.zeros_like(g["b"])
-        h = P.asm_setup(g["rp"], g["ci"], g["va"], g["pa"], g["N"], g["delta"], g["nev"], opt, stream, True)
-        P.asm_solve_segments(h, g["b"], x, g["offs"], sopt, stream)
-        P.asm_destroy(h)
-        torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
-        xs, its, sev = [], [], []
+        xs, its, sev, sws = [], [], [], []
         e0.record(stream)
         for g in groups:
             x = torch.zeros_like(g["b"])
@@ -488,6 +490,7 @@ def run_stream_batched(args, P, torch, dev, stream, insts, net):
             sev.append(es)
             infos = P.asm_solve_segments(h, g["b"], x, g["offs"], sopt, stream)
             its.append([int(i.iterations) for i in infos])
+            sws.append(P.asm_get_eigen_stats(h)[1])
             P.asm_destroy(h)
             xs.append(x)
         e1.record(stream)
@@ -502,6 +505,7 @@ def run_stream_batched(args, P, torch, dev, stream, insts, net):
         setup_ms = [a.elapsed_time(b_) for a, b_ in sev]
         res[name] = {"s_total": e0.elapsed_time(e1) / 1e3, "setup_ms_total": float(np.sum(setup_ms)),
                      "iterations_total": int(np.sum(flat)), "max_iterations_per_setup": [max(r) for r in its],
+                     "mean_sweeps": float(np.concatenate(sws).mean()), "max_sweeps": int(np.concatenate(sws).max()),
                      "max_instance_relres": worst}
     res["learned_vs_random"] = res["random"]["s_total"] / res["learned"]["s_total"]
     return res
