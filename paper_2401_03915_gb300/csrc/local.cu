@@ -22,6 +22,7 @@
 // operator Pi_i (eq. HOp).  Its first |I_i| rows X_p = -(B^{-1}C)[:p] are
 // copied out; the sweep then continues over Gamma_delta and leaves A_ii^{-1}.
 #include <algorithm>
+#include <mutex>
 
 #include <cuda_fp16.h>
 
@@ -480,22 +481,44 @@ __global__ void __launch_bounds__(NT) k_diag_chol(int kb, const int32_t* __restr
     Dm[r][c] = (r < kw && c < kw) ? B[(int64_t)max(r, c) * ld + min(r, c)] : (r == c ? 1.f : 0.f);
   }
   __syncthreads();
+  // outer-product form with the unscaled pivot column (one barrier per
+  // column): a_rc -= a_rj a_cj / a_jj for r >= c > j, the columns scaled by
+  // 1 / sqrt(a_jj) at the end; a non-positive pivot is flagged and taken as 1
   for (int j = 0; j < TILE; ++j) {
+    float d = Dm[j][j];
+    const bool ok = d > 0.f && isfinite(d);
+    if (!ok) d = 1.f;
     if (tid == 0) {
-      float d = Dm[j][j];
-      if (!(d > 0.f) || !isfinite(d)) { bad = 1; d = 1.f; }
+      if (!ok) bad = 1;
       if (j < kw) { pmin = fmin(pmin, (double)d); pmax = fmax(pmax, (double)d); }
-      Dm[j][j] = sqrtf(d);
     }
-    __syncthreads();
-    for (int r = j + 1 + tid; r < TILE; r += NT) Dm[r][j] /= Dm[j][j];
-    __syncthreads();
-    for (int idx = tid; idx < TILE * TILE; idx += NT) {
-      const int r = idx / TILE, c = idx % TILE;
-      if (c > j && r >= c) Dm[r][c] -= Dm[r][j] * Dm[c][j];
+    const float inv = 1.f / d;
+    const int m = TILE - 1 - j;  // trailing size
+    for (int idx = tid; idx < m * m; idx += NT) {
+      const int r = j + 1 + idx / m, c = j + 1 + idx % m;
+      if (r >= c) Dm[r][c] -= Dm[r][j] * (Dm[c][j] * inv);
     }
     __syncthreads();
   }
+  for (int idx = tid; idx < TILE * TILE; idx += NT) {
+    const int r = idx / TILE, c = idx % TILE;
+    if (r > c) {
+      float d = Dm[c][c];
+      if (!(d > 0.f && isfinite(d))) d = 1.f;
+      Xm[r][c] = Dm[r][c] / sqrtf(d);
+    }
+  }
+  __syncthreads();
+  for (int idx = tid; idx < TILE * TILE; idx += NT) {
+    const int r = idx / TILE, c = idx % TILE;
+    if (r > c) Dm[r][c] = Xm[r][c];
+    else if (r == c) {
+      float d = Dm[r][r];
+      if (!(d > 0.f && isfinite(d))) d = 1.f;
+      Dm[r][r] = sqrtf(d);
+    }
+  }
+  __syncthreads();
   // inverse of the lower diagonal block (column c by thread c)
   if (tid < TILE) {
     const int c = tid;
@@ -531,13 +554,41 @@ __global__ void k_sym_decide(int N, const double* __restrict__ piv_lo, const dou
   if (i < N) sym[i] = (ratio > 0 && piv_hi[i] <= ratio * piv_lo[i]) ? 1 : 0;
 }
 
+// The job descriptors are written straight into a pinned host buffer that
+// persists across setups (grown as needed), then copied in one transfer.
+std::mutex g_jobs_mutex;
+TcJob* g_jobs_pin = nullptr;
+size_t g_jobs_cap = 0;
+
 void factor_spd_levels(Handle& h, float* work, const int32_t* d_n, double ratio, cudaStream_t s) {
   const int N = h.N;
   Dense& dn = h.dn;
   DevMem& mem = h.mem;
   const int64_t T2 = (int64_t)TILE * TILE;
   int ntmax = 0;
-  for (int i = 0; i < N; ++i) ntmax = std::max(ntmax, dn.h_nt[i]);
+  size_t bound = 0;  // at most nt^2 updates + panels, nt^2 inverse jobs, nt (nt + 1) / 2 W^T W jobs
+  for (int i = 0; i < N; ++i) {
+    ntmax = std::max(ntmax, dn.h_nt[i]);
+    bound += 3 * (size_t)dn.h_nt[i] * dn.h_nt[i] + 2 * (size_t)dn.h_nt[i] + 1;
+  }
+  std::lock_guard<std::mutex> jobs_lock(g_jobs_mutex);
+  if (bound > g_jobs_cap) {
+    if (g_jobs_pin) CK(cudaFreeHost(g_jobs_pin));
+    g_jobs_pin = nullptr;
+    CK(cudaMallocHost(&g_jobs_pin, sizeof(TcJob) * bound));
+    g_jobs_cap = bound;
+  }
+  struct PinnedJobs {
+    TcJob* p;
+    size_t n, cap;
+    size_t size() const { return n; }
+    void push_back(const TcJob& J) {
+      if (n >= cap) fail(ASM_ERR_CUDA, "tile job bound exceeded");
+      p[n++] = J;
+    }
+    bool empty() const { return n == 0; }
+    const TcJob* data() const { return p; }
+  };
   // one launch of tile jobs: [first, first + count) of the job array and the
   // bases it reads and writes (0 work, 1 dinv, 2 scratch, 3 apply tiles)
   struct Step {
@@ -545,7 +596,7 @@ void factor_spd_levels(Handle& h, float* work, const int32_t* d_n, double ratio,
     int64_t first, count;
     int a, b, c, kb;
   };
-  std::vector<TcJob> jobs;
+  PinnedJobs jobs{g_jobs_pin, 0, g_jobs_cap};
   std::vector<int32_t> subs;
   std::vector<Step> steps;
   auto tile_at = [&](int i, int r, int c) { return dn.h_work_off[i] + (int64_t)r * TILE * dn.h_np[i] + c * TILE; };
@@ -640,6 +691,7 @@ void factor_spd_levels(Handle& h, float* work, const int32_t* d_n, double ratio,
   double* piv = mem.alloc<double>(2 * N);
   if (!jobs.empty()) CK(cudaMemcpyAsync(d_jobs, jobs.data(), sizeof(TcJob) * jobs.size(), cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(d_subs, subs.data(), sizeof(int32_t) * subs.size(), cudaMemcpyHostToDevice, s));
+  CK(cudaStreamSynchronize(s));  // the pinned buffer is reused by the next setup
   float* bases[4] = {work, (float*)dn.dinv, scratch, (float*)dn.tiles};
   for (const Step& st : steps) {
     if (st.kind == 1) {
