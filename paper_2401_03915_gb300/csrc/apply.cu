@@ -14,6 +14,9 @@
 #include <algorithm>
 
 #include <map>
+#include <string>
+#include <cstdlib>
+#include <cstdio>
 #include <mutex>
 #include <tuple>
 
@@ -1063,6 +1066,48 @@ void time_impl(Handle& h, const double* r, double* z, int iters, cudaStream_t s,
 std::mutex g_tune_mutex;
 std::map<std::tuple<int, int64_t, int, int, int>, int> g_tune_cache;
 
+// Optional persistent cache of the tuner's choices: with ASM_TUNE_CACHE set
+// to a file path, choices are read from it (one JSON object per line, keyed by
+// the device's name and SM count, the tile count, N, n_C and the storage) and
+// each new one is appended, so later processes skip the timing.
+struct TuneFile {
+  bool loaded = false;
+  std::string path, device;
+};
+TuneFile g_tune_file;
+
+void tune_file_load(int dev) {
+  if (g_tune_file.loaded) return;
+  g_tune_file.loaded = true;
+  const char* p = std::getenv("ASM_TUNE_CACHE");
+  if (!p || !*p) return;
+  g_tune_file.path = p;
+  cudaDeviceProp prop{};
+  CK(cudaGetDeviceProperties(&prop, dev));
+  g_tune_file.device = std::string(prop.name) + "/" + std::to_string(prop.multiProcessorCount);
+  FILE* f = std::fopen(p, "r");
+  if (!f) return;
+  char line[512], name[256];
+  long long tiles;
+  int N, nC, st, ctas;
+  while (std::fgets(line, sizeof line, f)) {
+    if (std::sscanf(line, "{\"device\": \"%255[^\"]\", \"n_tiles\": %lld, \"N\": %d, \"n_C\": %d, \"storage\": %d, "
+                          "\"tile_ctas\": %d}", name, &tiles, &N, &nC, &st, &ctas) == 6 &&
+        g_tune_file.device == name && ctas >= 1 && ctas <= 32)
+      g_tune_cache[std::make_tuple(dev, (int64_t)tiles, N, nC, st)] = ctas;
+  }
+  std::fclose(f);
+}
+
+void tune_file_append(const std::tuple<int, int64_t, int, int, int>& k, int ctas) {
+  if (g_tune_file.path.empty()) return;
+  FILE* f = std::fopen(g_tune_file.path.c_str(), "a");
+  if (!f) return;
+  std::fprintf(f, "{\"device\": \"%s\", \"n_tiles\": %lld, \"N\": %d, \"n_C\": %d, \"storage\": %d, \"tile_ctas\": %d}\n",
+               g_tune_file.device.c_str(), (long long)std::get<1>(k), std::get<2>(k), std::get<3>(k), std::get<4>(k), ctas);
+  std::fclose(f);
+}
+
 template <typename T>
 void tune_impl(Handle& h, cudaStream_t s) {
   int dev = 0;
@@ -1070,6 +1115,7 @@ void tune_impl(Handle& h, cudaStream_t s) {
   const auto key = std::make_tuple(dev, h.dn.n_tiles, h.N, h.co.n_C, (h.fp32 ? 1 : 0) + (h.dn.n_row_items_h > 0 ? 2 : 0));
   {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
+    tune_file_load(dev);
     auto it = g_tune_cache.find(key);
     if (it != g_tune_cache.end()) { h.tile_ctas = it->second; return; }
   }
@@ -1115,6 +1161,7 @@ void tune_impl(Handle& h, cudaStream_t s) {
   CK(cudaEventDestroy(e1));
   std::lock_guard<std::mutex> lock(g_tune_mutex);
   g_tune_cache[key] = best;
+  tune_file_append(key, best);
 }
 
 }  // namespace

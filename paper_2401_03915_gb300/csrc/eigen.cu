@@ -486,6 +486,7 @@ struct EigOut {
   const int32_t* skip;      // leading Ritz pairs left out (null: none)
   int lift;                 // 1: report 1 + mu and scale the vectors by sqrt((1 + mu) / mu)
   int refine;               // FP64, lifting or overlap 1: report the variational Rayleigh quotient
+  const int32_t* order;     // block b works on subdomain order[b] (largest first; null: b)
 };
 
 // B16 (single precision, SPD): the operator applications K Y = U (A^_II (U^T Y))
@@ -512,7 +513,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 4 : 1) k_subspace(
   __shared__ int badcol[128];
   __shared__ int nbad;
   __shared__ T red[NT / 32];
-  const int i = blockIdx.x;
+  const int i = eo.order ? eo.order[blockIdx.x] : (int)blockIdx.x;
   const int n = n_arr[i], m = m_arr[i], p = p_arr[i], ld = np_arr[i];
   const int g = n - m, pos0 = sub_off[i];
   const int dim = SPD ? g : p;
@@ -1173,9 +1174,19 @@ void run_eigen(Handle& h, cudaStream_t s) {
       wk = net.K;
     }
   }
+  // size buckets: the blocks take the subdomains in decreasing order of the
+  // iteration's work per sweep (|I_i| |Gamma_i| for SPD, |I_i|^2 otherwise), so
+  // that a launch with more subdomains than resident blocks starts the longest
+  // ones first and its tail is short
+  std::vector<int32_t> ord(N);
+  for (int i = 0; i < N; ++i) ord[i] = i;
+  auto work_of = [&](int i) { return (int64_t)h.h_p[i] * (spd ? std::max(h.h_g[i], 1) : std::max(h.h_p[i], 1)); };
+  std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return work_of(a) > work_of(b); });
+  int32_t* d_ord = mem.alloc<int32_t>(std::max(N, 1));
+  CK(cudaMemcpyAsync(d_ord, ord.data(), 4 * (size_t)N, cudaMemcpyHostToDevice, s));
   auto launch = [&](auto kern) {
     CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    EigOut eo{co.zld, nev, nullptr, nullptr, 0, (sizeof(T) == 8 && spd && h.delta == 1) ? 1 : 0};
+    EigOut eo{co.zld, nev, nullptr, nullptr, 0, (sizeof(T) == 8 && spd && h.delta == 1) ? 1 : 0, d_ord};
     kern<<<N, NT, smem, s>>>((const T*)dn.XpT, dn.xs_off, (const T*)dn.S, dn.s_off, (const T*)dn.work, dn.work_off,
                              dn.np, h.dev_n, h.dev_m, h.dev_p, h.ov.sub_off, h.ov.ent_off, h.ov.lcol, h.ov.omega,
                              h.row_ptr, h.col_idx, h.val, h.dscale, aval, (T*)co.scratch, co.scr_off, nev, over, maxsw,
@@ -1210,7 +1221,7 @@ void run_eigen(Handle& h, cudaStream_t s) {
     T* lscr = mem.alloc<T>(std::max<int64_t>(totl, 1));
     int64_t* lscr_off = mem.alloc<int64_t>(N);
     CK(cudaMemcpyAsync(lscr_off, scl.data(), 8 * N, cudaMemcpyHostToDevice, s));
-    EigOut eo{co.zld, nlift, co.count_g, h.delta == 1 ? co.count_g : nullptr, 1, sizeof(T) == 8 ? 1 : 0};
+    EigOut eo{co.zld, nlift, co.count_g, h.delta == 1 ? co.count_g : nullptr, 1, sizeof(T) == 8 ? 1 : 0, d_ord};
     auto kern = k_subspace<T, true>;
     CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<N, NT, smem, s>>>((const T*)dn.XpT, dn.xs_off, (const T*)dn.S, dn.s_off, (const T*)dn.work, dn.work_off,

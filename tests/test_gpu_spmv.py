@@ -97,3 +97,4 @@ def test_pcg_spmv_timing_helper(P):
     ref = A @ p.cpu().numpy()
     np.testing.assert_allclose(q.cpu().numpy(), ref, rtol=0, atol=1e-14 * np.abs(ref).max() * 10)
     pre.close()
+
