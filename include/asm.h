@@ -172,7 +172,7 @@ typedef struct {
 } asm_setup_info;
 
 /* Fill *o with defaults: spd 1, FP64, oversample 8, max_sweeps 0 (= 40 in
- * FP64, 12 in FP32), eig_tol 0 (= 1e-8 in FP64, 1e-3 in FP32), nu off, coarse
+ * FP64, 12 in FP32), eig_tol 0 (= 1e-8 in FP64, 4e-3 in FP32), nu off, coarse
  * on, seed 0, filter degree 0 (= 4 in FP64, 3 in FP32), no warm start, nothing
  * recorded. */
 void asm_default_options(asm_options* o);

@@ -103,7 +103,7 @@ void asm_default_options(asm_options* o) {
   o->local_precision = ASM_PREC_FP64;
   o->oversample = 8;
   o->max_sweeps = 0;  // 0: 40
-  o->eig_tol = 0;     // 0: 1e-8 (FP64) / 1e-3 (FP32)
+  o->eig_tol = 0;     // 0: 1e-8 (FP64) / 4e-3 (FP32)
   o->nu = 0;
   o->nev_lift = 0;
   o->coarse = 1;

@@ -7,9 +7,9 @@ against tests/golden/c3_oracle_reference.json / c4_oracle_reference.json
 oracle) the kept local values of EVERY subdomain, their counts, n_C and the
 Krylov iteration count; plus the true residual of the solve.
 
-Tolerance of the values: the single-precision subspace iteration stops when
-every kept Ritz pair has a relative eigen-residual ||K z - mu z|| / mu below
-1e-3; for a symmetric operator some eigenvalue then lies within 1e-3 mu of
+Tolerance of the values: with eig_tol = 1e-3 (set here; the library's
+single-precision default is 4e-3) the subspace iteration stops when every kept
+Ritz pair has a relative eigen-residual ||K z - mu z|| / mu below 1e-3; for a symmetric operator some eigenvalue then lies within 1e-3 mu of
 mu (Bauer-Fike for normal matrices), so the sorted values agree to a relative
 1e-3 where the kept values are separated.  The iteration count is within 10%
 of the FP64 oracle's (the target for the single-precision local work)."""
@@ -77,7 +77,7 @@ def test_c3_elasticity_full_size(P):
     prob = config("c3")
     ref = _golden("c3")
     A = prob.csr()
-    pre = _setup(P, prob, precision="fp32")
+    pre = _setup(P, prob, precision="fp32", eig_tol=1e-3)
     ovs = O.overlap(A, prob.part, prob.N, prob.delta)
     sample = [0, prob.N // 2, prob.N - 1]
     _check_overlap_sampled(P, pre.h, ovs, sample)
@@ -95,7 +95,7 @@ def test_c4_convdiff_full_size(P):
     prob = config("c4")
     ref = _golden("c4")
     A = prob.csr()
-    pre = _setup(P, prob, spd=False, precision="fp32")
+    pre = _setup(P, prob, spd=False, precision="fp32", eig_tol=1e-3)
     ovs = O.overlap(A, prob.part, prob.N, prob.delta)
     sample = [0, 517, prob.N - 1]
     _check_overlap_sampled(P, pre.h, ovs, sample)
