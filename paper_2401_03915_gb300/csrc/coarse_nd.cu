@@ -79,7 +79,12 @@ __global__ void __launch_bounds__(NT) k_front_pivot(const FrontDev* __restrict__
                                                     int k, double* __restrict__ M, double* __restrict__ piv,
                                                     int spd, int32_t* err) {
   COUNT_LAUNCH();
-  __shared__ double P[FB][FB + 1];
+  // Gauss-Jordan inversion of the FB x FB pivot block, ping-ponging between
+  // two copies so that each elimination step needs one block barrier: step q
+  // reads row q, column q and the pivot of the current copy and writes every
+  // entry of the other (the same operations, in the same order per entry, as
+  // in place).
+  __shared__ double P[2][FB][FB + 1];
   __shared__ int bad;
   const int t = list[blockIdx.x];
   const FrontDev f = fr[t];
@@ -87,37 +92,38 @@ __global__ void __launch_bounds__(NT) k_front_pivot(const FrontDev* __restrict__
   const int k0 = k * FB;
   for (int idx = threadIdx.x; idx < FB * FB; idx += NT) {
     int r = idx / FB, c = idx % FB;
-    P[r][c] = F[(int64_t)(k0 + r) * f.m + k0 + c];
+    P[0][r][c] = F[(int64_t)(k0 + r) * f.m + k0 + c];
   }
   if (threadIdx.x == 0) bad = 0;
   __syncthreads();
+  int cur = 0;
   for (int q = 0; q < FB; ++q) {
-    double pv = P[q][q];
+    const double (*Pc)[FB + 1] = P[cur];
+    double (*Pn)[FB + 1] = P[cur ^ 1];
+    const double pv = Pc[q][q];
     if (threadIdx.x == 0 && (!isfinite(pv) || (spd ? !(pv > 0) : pv == 0.0))) bad = 1;
-    __syncthreads();
-    if (bad) break;
-    double inv = 1.0 / pv;
+    const double inv = 1.0 / pv;
     for (int idx = threadIdx.x; idx < FB * FB; idx += NT) {
-      int r = idx / FB, c = idx % FB;
-      if (r != q && c != q) P[r][c] -= P[r][q] * P[q][c] * inv;
+      const int r = idx / FB, c = idx % FB;
+      double v;
+      if (r == q) v = c == q ? inv : Pc[q][c] * inv;
+      else if (c == q) v = Pc[r][q] * -inv;
+      else v = Pc[r][c] - Pc[r][q] * Pc[q][c] * inv;
+      Pn[r][c] = v;
     }
-    __syncthreads();
-    if (threadIdx.x < FB && threadIdx.x != q) P[q][threadIdx.x] *= inv;
-    if (threadIdx.x >= FB && threadIdx.x < 2 * FB && threadIdx.x - FB != q) P[threadIdx.x - FB][q] *= -inv;
-    __syncthreads();
-    if (threadIdx.x == 0) P[q][q] = inv;
+    cur ^= 1;
     __syncthreads();
   }
   if (bad) {
     if (threadIdx.x == 0) atomicOr(err, DERR_COARSE);
     for (int idx = threadIdx.x; idx < FB * FB; idx += NT) {
       int r = idx / FB, c = idx % FB;
-      P[r][c] = r == c ? 1.0 : 0.0;
+      P[cur][r][c] = r == c ? 1.0 : 0.0;
     }
     __syncthreads();
   }
   double* out = piv + (int64_t)t * FB * FB;
-  for (int idx = threadIdx.x; idx < FB * FB; idx += NT) out[idx] = P[idx / FB][idx % FB];
+  for (int idx = threadIdx.x; idx < FB * FB; idx += NT) out[idx] = P[cur][idx / FB][idx % FB];
 }
 
 // Row panel: M[K][C] <- P M[K][C] for column tiles C != K.
