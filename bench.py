@@ -71,6 +71,8 @@ def parse():
     ap.add_argument("--instances", type=int, default=200, help="stream mode: instances in the stream")
     ap.add_argument("--no-stream", action="store_true",
                     help="step mode: skip the batched stream of 200 instances (learned vs randomized start)")
+    ap.add_argument("--stream-oracle-sample", type=int, default=2,
+                    help="stream mode: instances the CPU oracle is timed on (0: none)")
     ap.add_argument("--stream-batch", type=int, default=20,
                     help="stream mode: instances per batched setup (block-diagonal system); 0 skips the batched pass")
     ap.add_argument("--sample-subdomains", type=int, default=16,
@@ -429,10 +431,33 @@ def run_stream(args, P, torch, dev, stream):
         out[name] = {"s_total": e0.elapsed_time(e1) / 1e3, "iterations_total": int(np.sum(its)),
                      "mean_sweeps": float(np.mean(sweeps)), "subdomains": subs, "unknowns": rows}
     batched = run_stream_batched(args, P, torch, dev, stream, insts, net) if args.stream_batch > 0 else None
+    oracle = stream_oracle_sample(insts, args.stream_oracle_sample) if args.stream_oracle_sample > 0 else None
     print(json.dumps({"mode": "stream", "instances": args.instances, "warm_start": warm_info, **out,
                       "learned_vs_random": out["random"]["s_total"] / out["learned"]["s_total"],
-                      "batched": batched}), flush=True)
+                      "batched": batched, "cpu_oracle": oracle}), flush=True)
     net.close()
+
+
+def stream_oracle_sample(insts, k):
+    """The CPU oracle (FP64 dense local eigensolves, PCG to 1e-8) on the first
+    k instances of the stream, timed on the host cores, and the whole stream
+    extrapolated from their mean time per unknown (labelled as such)."""
+    import oracle as O
+    t_all, n_all, per = 0.0, 0, []
+    for p, *_ in insts[:k]:
+        A = p.csr()
+        t0 = time.perf_counter()
+        st = O.setup(A, p.part, p.N, p.delta, p.nev)
+        res = O.solve(st, p.b)
+        dt = time.perf_counter() - t0
+        per.append({"n": p.n, "N": p.N, "s": round(dt, 2), "iterations": res.iterations})
+        t_all += dt
+        n_all += p.n
+    total_n = sum(p.n for p, *_ in insts)
+    threads = int(os.environ.get("OPENBLAS_NUM_THREADS", os.environ.get("OMP_NUM_THREADS", os.cpu_count())))
+    return {"kind": "oracle", "cores": threads, "sample": f"first {k} of {len(insts)} instances",
+            "instances": per, "extrapolated_s": t_all / n_all * total_n,
+            "note": "extrapolated to the whole stream by the sample's time per unknown"}
 
 
 def run_stream_batched(args, P, torch, dev, stream, insts, net):
