@@ -71,6 +71,9 @@ def parse():
     ap.add_argument("--instances", type=int, default=200, help="stream mode: instances in the stream")
     ap.add_argument("--no-stream", action="store_true",
                     help="step mode: skip the batched stream of 200 instances (learned vs randomized start)")
+    ap.add_argument("--weak-side", type=int, default=8, help="weak mode: subdomain side (unknowns per axis)")
+    ap.add_argument("--weak-counts", default="4,6,8,10,12", help="weak mode: subdomains per axis, comma-separated")
+    ap.add_argument("--weak-rtol", type=float, default=1e-8, help="weak mode: PCG tolerance")
     ap.add_argument("--stream-oracle-sample", type=int, default=2,
                     help="stream mode: instances the CPU oracle is timed on (0: none)")
     ap.add_argument("--stream-batch", type=int, default=20,
@@ -582,21 +585,26 @@ def run_sweep(args, P, torch, dev, stream):
 
 
 def run_weak(args, P, torch, dev, stream):
-    """One-GPU weak scaling (the paper's Section 6 Poisson sweep, at a fixed
-    8^3 unknowns per subdomain): 3D 7-point Poisson (unit coefficient) on
-    m^3 grids, m = 32 .. 96, boxes of 8^3, overlap 1, nev 16, FP32 local
-    work, PCG to 1e-8.  Iteration counts should stay flat as N grows."""
+    """One-GPU weak scaling (the paper's Section 6 Poisson sweep): 3D 7-point
+    Poisson (unit coefficient) on m^3 grids split into c^3 cubic subdomains of
+    side `--weak-side` (m = c * side for c in `--weak-counts`), overlap 1,
+    nev 16, FP32 local work, PCG to `--weak-rtol`.  Iteration counts should
+    stay flat as N grows.  With side 22 each subdomain has 10,648 interior
+    unknowns (13,552 with its overlap), near the paper's ~15k."""
     from asm_inputs import diffusion3d
-    sopt = P.default_solve_opts(rtol=1e-8, max_it=5000)
+    sopt = P.default_solve_opts(rtol=args.weak_rtol, max_it=5000)
     opt = P.default_options(local_precision=P.PREC_FP32)
     rows = []
-    for m in (32, 48, 64, 80, 96):
-        prob = diffusion3d(m, (m // 8,) * 3, contrast=1.0, frac=0.0, delta=1, nev=16)
+    side = args.weak_side
+    for c in [int(v) for v in args.weak_counts.split(",")]:
+        m = c * side
+        prob = diffusion3d(m, (c,) * 3, contrast=1.0, frac=0.0, delta=1, nev=16)
         rp = torch.as_tensor(prob.indptr, device=dev); ci = torch.as_tensor(prob.indices, device=dev)
         va = torch.as_tensor(prob.data, device=dev); pa = torch.as_tensor(prob.part, device=dev)
         b = torch.as_tensor(prob.b, device=dev)
-        h = P.asm_setup(rp, ci, va, pa, prob.N, 1, 16, opt, stream, True)  # warm-up of this shape
-        P.asm_destroy(h)
+        if side <= 8:
+            h = P.asm_setup(rp, ci, va, pa, prob.N, 1, 16, opt, stream, True)  # warm-up of this shape
+            P.asm_destroy(h)
         x = torch.zeros_like(b)
         e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
         e2 = torch.cuda.Event(enable_timing=True)
@@ -607,12 +615,14 @@ def run_weak(args, P, torch, dev, stream):
         e2.record(stream)
         torch.cuda.synchronize()
         si = P.asm_get_info(h)
-        rows.append({"m": m, "n": prob.n, "N": prob.N, "n_C": si.n_C, "gc": si.gc, "oc": si.oc,
-                     "pcg_iterations": info.iterations, "true_relres": info.true_relres,
-                     "setup_ms": e0.elapsed_time(e1), "solve_ms": e1.elapsed_time(e2)})
+        rows.append({"m": m, "n": prob.n, "N": prob.N, "max_n_i": si.max_ni, "n_C": si.n_C, "gc": si.gc,
+                     "oc": si.oc, "pcg_iterations": info.iterations, "true_relres": info.true_relres,
+                     "setup_ms": e0.elapsed_time(e1), "solve_ms": e1.elapsed_time(e2),
+                     "stages_ms": [round(v, 2) for v in list(si.stage_ms)[:8]]})
         P.asm_destroy(h)
-    print(json.dumps({"mode": "weak", "workload": "3D 7-point Poisson, unit coefficient, 8^3 per subdomain, "
-                      "overlap 1, nev 16, FP32 local work, PCG 1e-8", "rows": rows}), flush=True)
+        print(json.dumps(rows[-1]), flush=True)
+    print(json.dumps({"mode": "weak", "workload": f"3D 7-point Poisson, unit coefficient, {side}^3 per subdomain, "
+                      f"overlap 1, nev 16, FP32 local work, PCG {args.weak_rtol:g}", "rows": rows}), flush=True)
 
 
 def laplacian3d(m: int):
