@@ -36,6 +36,7 @@
 #include <cuda_bf16.h>
 
 #include "handle.cuh"
+#include "tcgemm.cuh"
 
 namespace asmgpu {
 namespace {
@@ -345,6 +346,44 @@ __device__ void mul_AII(int p, int pos0, const int64_t* __restrict__ ent_off, co
   __syncthreads();
 }
 
+// The single-precision eq. gevpsvd operator K = U A^_II U^T of each subdomain
+// (g x g, U = W[Gamma_delta, I_i]) is formed once at setup: the zero-padded
+// copy Up of U and T = U A^_II (from the sparse local rows; A^_II is
+// symmetric, so column c of T takes row c of A^_II) here, then K = T Up^T as
+// 64 x 64 tile jobs on the tensor cores.  Each application of the operator in
+// the iteration is then one g x g block product instead of two g x p ones.
+__global__ void __launch_bounds__(NT) k_u_padded(const float* __restrict__ work, const int64_t* __restrict__ work_off,
+                                                 const int32_t* __restrict__ np_arr, const int32_t* __restrict__ n_arr,
+                                                 const int32_t* __restrict__ m_arr, const int32_t* __restrict__ p_arr,
+                                                 const int64_t* __restrict__ uoff, const int32_t* __restrict__ uld,
+                                                 const int32_t* __restrict__ urows, float* __restrict__ Up,
+                                                 float* __restrict__ Tm, const int32_t* __restrict__ sub_off,
+                                                 const int64_t* __restrict__ ent_off, const int32_t* __restrict__ lcol,
+                                                 const float* __restrict__ aval) {
+  COUNT_LAUNCH();
+  const int i = blockIdx.y;
+  const int n = n_arr[i], m = m_arr[i], p = p_arr[i], g = n - m, ld = np_arr[i];
+  const int pp = uld[i], gp = urows[i], pos0 = sub_off[i];
+  const float* U = work + work_off[i] + (int64_t)m * ld;
+  float* up = Up + uoff[i];
+  float* tm = Tm + uoff[i];
+  const int64_t total = (int64_t)gp * pp;
+  for (int64_t idx = blockIdx.x * (int64_t)NT + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * NT) {
+    const int r = (int)(idx / pp), c = (int)(idx % pp);
+    float u = 0.f, t = 0.f;
+    if (r < g && c < p) {
+      const float* Ur = U + (int64_t)r * ld;
+      u = Ur[c];
+      for (int64_t e = ent_off[pos0 + c]; e < ent_off[pos0 + c + 1]; ++e) {
+        const int lc = lcol[e];
+        if (lc >= 0 && lc < p) t = fmaf(Ur[lc], aval[e], t);
+      }
+    }
+    up[idx] = u;
+    tm[idx] = t;
+  }
+}
+
 // Scaled values of every local row (all positions of all Omega_i), in the
 // working precision: aval[e] = a_vu ds_v ds_u with ds = |diag A|^{-1/2}.
 template <typename T>
@@ -487,6 +526,9 @@ struct EigOut {
   int lift;                 // 1: report 1 + mu and scale the vectors by sqrt((1 + mu) / mu)
   int refine;               // FP64, lifting or overlap 1: report the variational Rayleigh quotient
   const int32_t* order;     // block b works on subdomain order[b] (largest first; null: b)
+  const float* K;           // single precision, eq. gevpsvd run: the explicit operator U A^_II U^T per
+  const int64_t* koff;      // subdomain (row-major, leading dimension kld[i]); null: products with U
+  const int32_t* kld;
 };
 
 // B16 (single precision, SPD): the operator applications K Y = U (A^_II (U^T Y))
@@ -562,6 +604,13 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 4 : 1) k_subspace(
   // Column c0.. c0+nc-1 of the blocks (stride sp).
   auto applyK = [&](const T* Yin, T* out, int c0, int nc) {
     if (SPD) {
+      if constexpr (sizeof(T) == 4) {
+        if (eo.K != nullptr && eo.koff[i] >= 0) {  // K Y with the operator formed at setup
+          cta_gemm<T, false, false, false, B16>(g, nc, g, eo.K + eo.koff[i], eo.kld[i], Yin + c0, sp, out + c0, sp,
+                                                gsm);
+          return;
+        }
+      }
       cta_gemm<T, true, false, false, B16>(p, nc, g, U, ld, Yin + c0, sp, V + c0, sp, gsm);    // V = U^T Y
       mul_AII(p, pos0, ent_off, lcol, aval, V + c0, AV + c0, nc, sp);
       cta_gemm<T, false, false, false, B16>(g, nc, p, U, ld, AV + c0, sp, out + c0, sp, gsm);  // U (A^_II V)
@@ -1151,6 +1200,69 @@ void run_eigen(Handle& h, cudaStream_t s) {
                                                            h.col_idx, h.val, h.dscale, aval);
     CK_LAUNCH("scaled local values");
   }
+  // single precision, SPD: the explicit operator K = U A^_II U^T per subdomain
+  const float* Kexp = nullptr;
+  const int64_t* d_koff = nullptr;
+  const int32_t* d_kld = nullptr;
+  if constexpr (sizeof(T) == 4) {
+    if (spd && nev > 0) {
+      std::vector<int64_t> ko(N), uo(N);
+      std::vector<int32_t> kl(N), ul(N), ur(N);
+      int64_t kt = 0, ut = 0;
+      std::vector<TcJob> jobs;
+      // only where |Gamma| <= |I_i|: one g x g product per application then
+      // beats the two g x p ones by at least half, building K included
+      // (elasticity's wide overlap layers keep the products with U)
+      for (int i = 0; i < N; ++i) {
+        const int g = h.h_n[i] - h.h_m[i], p = h.h_p[i];
+        const int gp = (int)round_up(std::max(g, 1), TILE), pp = (int)round_up(std::max(p, 1), TILE);
+        if (g > p) {
+          ko[i] = -1; kl[i] = 0; uo[i] = ut; ul[i] = pp; ur[i] = 0;
+          continue;
+        }
+        ko[i] = kt; kl[i] = gp; kt += (int64_t)gp * gp;
+        uo[i] = ut; ul[i] = pp; ur[i] = gp; ut += (int64_t)gp * pp;
+        for (int I = 0; I < gp / TILE; ++I)
+          for (int J = 0; J < gp / TILE; ++J) {
+            TcJob Jb{};
+            Jb.a0 = uo[i] + (int64_t)I * TILE * pp; Jb.a_step = TILE; Jb.lda = pp;   // T(I, k)
+            Jb.b0 = uo[i] + (int64_t)J * TILE * pp; Jb.b_step = TILE; Jb.ldb = pp;   // Up(J, k)
+            Jb.c_out = ko[i] + (int64_t)I * TILE * gp + J * TILE; Jb.ldc_out = gp; Jb.ldc_in = gp;
+            Jb.nprod = pp / TILE; Jb.flags = 0; Jb.sub = i;
+            jobs.push_back(Jb);
+          }
+      }
+      if (!jobs.empty()) {
+        float* Kb = mem.alloc<float>(kt);
+        float* Up = mem.alloc<float>(ut);
+        float* Tm = mem.alloc<float>(ut);
+        int64_t* koff = mem.alloc<int64_t>(N);
+        int32_t* kld = mem.alloc<int32_t>(N);
+        int64_t* uoff = mem.alloc<int64_t>(N);
+        int32_t* uld = mem.alloc<int32_t>(N);
+        int32_t* urows = mem.alloc<int32_t>(N);
+        TcJob* d_jobs = mem.alloc<TcJob>(jobs.size());
+        // pageable sources: each copy is staged before the call returns
+        CK(cudaMemcpyAsync(koff, ko.data(), 8 * (size_t)N, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(kld, kl.data(), 4 * (size_t)N, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(uoff, uo.data(), 8 * (size_t)N, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(uld, ul.data(), 4 * (size_t)N, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(urows, ur.data(), 4 * (size_t)N, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(d_jobs, jobs.data(), sizeof(TcJob) * jobs.size(), cudaMemcpyHostToDevice, s));
+        CK(cudaStreamSynchronize(s));
+        k_u_padded<<<dim3(64, N), NT, 0, s>>>((const float*)dn.work, dn.work_off, dn.np, h.dev_n, h.dev_m, h.dev_p, uoff,
+                                             uld, urows, Up, Tm, h.ov.sub_off, h.ov.ent_off, h.ov.lcol,
+                                             (const float*)aval);
+        CK_LAUNCH("padded U and U A^_II");
+        tc_tiles(d_jobs, (int64_t)jobs.size(), Tm, Up, nullptr, Kb, nullptr, dn.err, h.num_sms, s);
+        mem.free(Up);  // stream-ordered behind the tile jobs
+        mem.free(Tm);
+        Kexp = Kb;
+        d_koff = koff;
+        d_kld = kld;
+      }
+    }
+  }
   // learned warm start (SPD path): features per Gamma_delta node, the
   // network's start blocks, and (when recorded) the converged blocks
   const bool want_warm = spd && (h.opt.warm_start || h.opt.record_warm);
@@ -1190,7 +1302,8 @@ void run_eigen(Handle& h, cudaStream_t s) {
   CK(cudaMemcpyAsync(d_ord, ord.data(), 4 * (size_t)N, cudaMemcpyHostToDevice, s));
   auto launch = [&](auto kern) {
     CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    EigOut eo{co.zld, nev, nullptr, nullptr, 0, (sizeof(T) == 8 && spd && h.delta == 1) ? 1 : 0, d_ord};
+    EigOut eo{co.zld, nev, nullptr, nullptr, 0, (sizeof(T) == 8 && spd && h.delta == 1) ? 1 : 0, d_ord,
+              Kexp, d_koff, d_kld};
     kern<<<N, NT, smem, s>>>((const T*)dn.XpT, dn.xs_off, (const T*)dn.S, dn.s_off, (const T*)dn.work, dn.work_off,
                              dn.np, h.dev_n, h.dev_m, h.dev_p, h.ov.sub_off, h.ov.ent_off, h.ov.lcol, h.ov.omega,
                              h.row_ptr, h.col_idx, h.val, h.dscale, aval, (T*)co.scratch, co.scr_off, nev, over, maxsw,
@@ -1225,7 +1338,8 @@ void run_eigen(Handle& h, cudaStream_t s) {
     T* lscr = mem.alloc<T>(std::max<int64_t>(totl, 1));
     int64_t* lscr_off = mem.alloc<int64_t>(N);
     CK(cudaMemcpyAsync(lscr_off, scl.data(), 8 * N, cudaMemcpyHostToDevice, s));
-    EigOut eo{co.zld, nlift, co.count_g, h.delta == 1 ? co.count_g : nullptr, 1, sizeof(T) == 8 ? 1 : 0, d_ord};
+    EigOut eo{co.zld, nlift, co.count_g, h.delta == 1 ? co.count_g : nullptr, 1, sizeof(T) == 8 ? 1 : 0, d_ord,
+              nullptr, nullptr, nullptr};
     auto kern = k_subspace<T, true>;
     CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<N, NT, smem, s>>>((const T*)dn.XpT, dn.xs_off, (const T*)dn.S, dn.s_off, (const T*)dn.work, dn.work_off,
