@@ -69,3 +69,43 @@ def test_invalid_arguments_are_rejected_before_any_device_work(lib):
         assert e.value.name == "INVALID_ARG", kw
     assert L.asm_apply(None, None, None, None) == 1
     assert b"null" in L.asm_last_error()
+
+
+def test_tile_products_arguments_checked_on_the_host(lib):
+    """asm_tile_products rejects a bad job list before any device work (the
+    pointers below are never dereferenced)."""
+    P, L = lib
+    dummy = C.c_void_p(16)
+    def call(**kw):
+        jobs = np.zeros(1, dtype=P.TILE_JOB_DTYPE)
+        jobs[0]["lda"] = jobs[0]["ldb"] = jobs[0]["ldc_out"] = jobs[0]["ldc_in"] = 64
+        jobs[0]["nprod"] = 1
+        for k, v in kw.items():
+            jobs[0][k] = v
+        cin = kw.pop("_cin", None)
+        return L.asm_tile_products(jobs.ctypes.data, 1, dummy, dummy, cin, dummy, None)
+    INVALID = 1
+    assert call(nprod=0) == INVALID
+    assert call(a0=2) == INVALID           # row starts must be 16-byte aligned
+    assert call(lda=66) == INVALID
+    assert call(flags=32) == INVALID       # unknown flag
+    assert call(flags=4) == INVALID        # C_in asked for, none given
+    assert call(lda=32) == INVALID         # row stride below the tile edge
+    assert L.asm_tile_products(None, 1, dummy, dummy, None, dummy, None) == INVALID
+    assert L.asm_tile_products(None, -1, dummy, dummy, None, dummy, None) == INVALID
+    assert L.asm_tile_products(None, 0, None, None, None, None, None) == 0  # empty batch
+
+
+def test_segmented_solve_arguments_checked_on_the_host(lib):
+    """asm_solve_segments rejects null arguments and segment counts out of
+    range before touching the handle's device data."""
+    P, L = lib
+    INVALID = 1
+    infos = (P.asm_solve_info * 2)()
+    off = np.array([0, 1, 2], dtype=np.int32)
+    assert L.asm_solve_segments(None, C.c_void_p(16), C.c_void_p(16), 2, off.ctypes.data, None, infos, None) == INVALID
+    assert L.asm_solve_segments(C.c_void_p(16), None, C.c_void_p(16), 2, off.ctypes.data, None, infos, None) == INVALID
+    assert L.asm_solve_segments(C.c_void_p(16), C.c_void_p(16), C.c_void_p(16), 0, off.ctypes.data, None, infos,
+                                None) == INVALID
+    assert L.asm_solve_segments(C.c_void_p(16), C.c_void_p(16), C.c_void_p(16), 70000, off.ctypes.data, None, infos,
+                                None) == INVALID
